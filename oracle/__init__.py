@@ -1,0 +1,203 @@
+"""CPU oracle for the charges-in-a-disk hot path (TEST INFRASTRUCTURE ONLY).
+
+Thin ctypes wrapper over oracle/tco.c, a plain single-thread FP64 program with
+Neumaier-compensated sums.  Only tests, the smoke check and the benchmark's
+CPU-baseline arm use it; the GPU library never imports, links or calls it, and
+it shares nothing with the GPU library.
+
+Paper passages followed (Lavrov & Nikonov, Thomson problem in a disk):
+  energy          Eq. (hamiltonian) with the hard wall of Eq. (potential)
+  grad            its analytic Cartesian gradient (Sec. II C step 4: analytic gradients)
+  local energy    Sec. II C step 1
+  subdomain_grad  the subdomain objective E_sub of Sec. II D
+  delta_energy    E_sub(new) - E_sub(old), summed as pair differences
+  project         the hard wall as a projection; pinned boundary charges of Sec. II B
+  lbfgs / bb / pgd  projected descent on E (the paper's local optimiser is
+                  L-BFGS-B, Sec. II C step 4; see the function docs for the
+                  variant written here)
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_ERR = {1: "invalid argument", 3: "non-finite (coincident charges or NaN)",
+        4: "charge outside the disk", 7: "out of memory"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what}: {_ERR.get(code, code)} (status {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        d, i64, vp = C.c_double, C.c_int64, C.c_void_p
+        sig = {
+            "tco_energy": [vp, i64, vp, vp],
+            "tco_grad": [vp, i64, vp],
+            "tco_rows_grad": [vp, i64, vp, i64, vp, vp],
+            "tco_subdomain_grad": [vp, i64, vp, i64, vp, vp, vp, vp],
+            "tco_delta_energy": [vp, i64, vp, i64, vp, vp],
+            "tco_project": [vp, i64, d, vp],
+            "tco_projected_grad": [vp, vp, i64, d, vp, vp, vp, vp],
+            "tco_pgd": [vp, i64, d, i64, d, vp, vp],
+            "tco_subdomain_bb": [vp, i64, vp, i64, d, d, d, i64, d, vp],
+            "tco_accept_sequential": [vp, i64, vp, vp, i64, vp, vp, vp],
+            "tco_lbfgs": [vp, i64, i64, i64, d, d, d, d, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _pos(pos) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
+    if a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("positions must have shape (n, 2)")
+    return a
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check(code: int, what: str) -> None:
+    if code != 0:
+        raise OracleError(code, what)
+
+
+def energy(pos, local: bool = False):
+    """E = sum_{i<j} 1/r_ij; with local=True also e_i = 1/2 sum_{j != i} 1/r_ij."""
+    p = _pos(pos)
+    e = np.zeros(1)
+    le = np.zeros(p.shape[0]) if local else None
+    _check(lib().tco_energy(_p(p), p.shape[0], _p(e), _p(le)), "energy")
+    return (float(e[0]), le) if local else float(e[0])
+
+
+def grad(pos) -> np.ndarray:
+    """g_i = dE/dr_i = sum_{j != i} -(r_i - r_j)/r_ij^3, shape (n, 2)."""
+    p = _pos(pos)
+    g = np.zeros_like(p)
+    _check(lib().tco_grad(_p(p), p.shape[0], _p(g)), "grad")
+    return g
+
+
+def rows_grad(pos, rows):
+    """Gradient rows (and sum_{j != i} 1/r_ij) of the charges `rows` against all n."""
+    p = _pos(pos)
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
+    g = np.zeros((r.size, 2))
+    e = np.zeros(r.size)
+    _check(lib().tco_rows_grad(_p(p), p.shape[0], _p(r), r.size, _p(g), _p(e)), "rows_grad")
+    return g, e
+
+
+def subdomain_grad(snap, idx, act):
+    """Gradient, local energies e_k and E_sub of the subdomain objective (Sec. II D)."""
+    s = _pos(snap)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    a = _pos(act)
+    g = np.zeros_like(a)
+    e = np.zeros(ix.size)
+    es = np.zeros(1)
+    _check(lib().tco_subdomain_grad(_p(s), s.shape[0], _p(ix), ix.size, _p(a), _p(g), _p(e), _p(es)),
+           "subdomain_grad")
+    return g, e, float(es[0])
+
+
+def delta_energy(pos, idx, new_act) -> float:
+    """Energy change of moving charges idx to new_act, summed as pair differences."""
+    p = _pos(pos)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    na = _pos(new_act)
+    d = np.zeros(1)
+    _check(lib().tco_delta_energy(_p(p), p.shape[0], _p(ix), ix.size, _p(na), _p(d)), "delta_energy")
+    return float(d[0])
+
+
+def project(pos, radius: float = 1.0, flags=None) -> np.ndarray:
+    """Hard-wall projection r <- r min(1, radius/|r|); pinned charges to the unit circle."""
+    p = _pos(pos).copy()
+    f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+    _check(lib().tco_project(_p(p), p.shape[0], float(radius), _p(f)), "project")
+    return p
+
+
+def projected_grad(pos, g, radius: float = 1.0, flags=None):
+    """Gradient with wall-blocked components removed; returns (pg, rms, max)."""
+    p = _pos(pos)
+    gg = _pos(g)
+    f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+    pg = np.zeros_like(p)
+    rms = np.zeros(1)
+    mx = np.zeros(1)
+    _check(lib().tco_projected_grad(_p(p), _p(gg), p.shape[0], float(radius), _p(f), _p(pg), _p(rms), _p(mx)),
+           "projected_grad")
+    return pg, float(rms[0]), float(mx[0])
+
+
+def pgd(pos, eta: float, steps: int, radius: float = 1.0, flags=None):
+    """Projected gradient descent x <- P(x - eta g); returns (x, energy trace[steps+1])."""
+    p = _pos(pos).copy()
+    f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+    tr = np.zeros(steps + 1)
+    _check(lib().tco_pgd(_p(p), p.shape[0], float(eta), int(steps), float(radius), _p(f), _p(tr)), "pgd")
+    return p, tr
+
+
+def subdomain_bb(snap, idx, step0: float, alpha_min: float, alpha_max: float, steps: int,
+                 radius: float = 1.0) -> np.ndarray:
+    """Projected BB gradient descent of one subdomain against the snapshot; returns x (m, 2)."""
+    s = _pos(snap)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    out = np.zeros((ix.size, 2))
+    _check(lib().tco_subdomain_bb(_p(s), s.shape[0], _p(ix), ix.size, float(step0), float(alpha_min),
+                                  float(alpha_max), int(steps), float(radius), _p(out)), "subdomain_bb")
+    return out
+
+
+def accept_sequential(pos, idx, offsets, new_act):
+    """Sequential FP64 accept/reject; returns (new pos, delta[n_sub], accepted[n_sub] in {0,1,2})."""
+    p = _pos(pos).copy()
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    na = _pos(new_act)
+    ns = off.size - 1
+    d = np.zeros(ns)
+    acc = np.zeros(ns, dtype=np.uint8)
+    _check(lib().tco_accept_sequential(_p(p), p.shape[0], _p(ix), _p(off), ns, _p(na), _p(d), _p(acc)),
+           "accept_sequential")
+    return p, d, acc
+
+
+def lbfgs(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: float = 1e-4,
+          maxstep: float = 1e-2, radius: float = 1.0, flags=None):
+    """Projected L-BFGS with a max-displacement cap; returns (x, iterations, final RMS |pg|)."""
+    p = _pos(pos).copy()
+    f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+    it = np.zeros(1, dtype=np.int64)
+    rms = np.zeros(1)
+    _check(lib().tco_lbfgs(_p(p), p.shape[0], int(memory), int(max_iter), float(gtol), float(step0),
+                           float(maxstep), float(radius), _p(f), _p(it), _p(rms)), "lbfgs")
+    return p, int(it[0]), float(rms[0])
+
+
+def library_path() -> str:
+    return os.path.abspath(lib()._name)

@@ -1,0 +1,604 @@
+/*
+ * tco.c -- CPU oracle for the Coulomb-charges-in-a-disk hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously correct
+ * single-thread FP64 statement of what the GPU library computes.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline arm may load
+ * it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Every sum over pairs uses Neumaier-compensated accumulation; 1/r is
+ * 1.0 / sqrt(r^2) with IEEE correctly rounded sqrt and divide.  Build with
+ * -ffp-contract=off so no fused multiply-add changes the rounding.
+ *
+ * Paper: Thomson problem in a disk, N = 100 000 (Lavrov & Nikonov).
+ *   Eq. (hamiltonian) + Eq. (potential), Sec. II A: E = sum_{i<j} 1/|r_i - r_j|,
+ *       wall term 0 for |r| <= R = 1, infinite outside.
+ *   Sec. II C, step 1: local energy e_i = 1/2 sum_{j != i} 1/|r_i - r_j|.
+ *   Sec. II D: subdomain objective E_sub = sum_{i in A} e_i with
+ *       e_i = 1/2 sum_{j in A, j != i} 1/r_ij + sum_{j in F} 1/r_ij,
+ *       optimised by a box-constrained quasi-Newton method with analytic
+ *       gradients (Sec. II C step 4).
+ *   Sec. II E: each subproblem's gradient is n_act rows against all N charges.
+ *
+ * Parity status: every function here is pinned by tests against closed forms,
+ * brute force in extended precision, invariants or the paper's asymptotic
+ * expansion (Eq. asym); see tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TCO_OK 0
+#define TCO_ERR_INVALID_ARG 1
+#define TCO_ERR_NONFINITE 3
+#define TCO_ERR_OUTSIDE_DISK 4
+#define TCO_ERR_NO_MEMORY 7
+
+/* A charge with |r| above this radius is outside the hard wall of Eq. (potential);
+ * the slack admits positions a projection left one rounding above R = 1. */
+#define TCO_WALL_SLACK 1e-12
+
+/* ---------------------------------------------------------------- sums --- */
+
+typedef struct {
+    double s; /* running sum */
+    double c; /* running compensation */
+} acc_t;
+
+static void acc_add(acc_t* a, double v)
+{
+    /* Neumaier's improvement of Kahan summation */
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v))
+        a->c += (a->s - t) + v;
+    else
+        a->c += (v - t) + a->s;
+    a->s = t;
+}
+
+static double acc_get(const acc_t* a) { return a->s + a->c; }
+
+static double inv_dist(double xi, double yi, double xj, double yj)
+{
+    double dx = xi - xj;
+    double dy = yi - yj;
+    double r2 = dx * dx + dy * dy;
+    return 1.0 / sqrt(r2);
+}
+
+static int check_inside(const double* pos, int64_t n)
+{
+    double lim = 1.0 + TCO_WALL_SLACK;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[2 * i], y = pos[2 * i + 1];
+        if (!(isfinite(x) && isfinite(y))) return TCO_ERR_NONFINITE;
+        if (sqrt(x * x + y * y) > lim) return TCO_ERR_OUTSIDE_DISK;
+    }
+    return TCO_OK;
+}
+
+/* ------------------------------------------------------------ energies --- */
+
+/* E = sum_{i<j} 1/|r_i - r_j| (Eq. hamiltonian; V = 0 inside the disk).
+ * local_e (nullable, n): e_i = 1/2 sum_{j != i} 1/r_ij (Sec. II C step 1). */
+int tco_energy(const double* pos, int64_t n, double* energy, double* local_e)
+{
+    if (n < 0 || (n > 0 && !pos) || !energy) return TCO_ERR_INVALID_ARG;
+    int st = check_inside(pos, n);
+    if (st) return st;
+    acc_t E = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            acc_add(&E, inv_dist(pos[2 * i], pos[2 * i + 1], pos[2 * j], pos[2 * j + 1]));
+    *energy = acc_get(&E);
+    if (local_e) {
+        for (int64_t i = 0; i < n; ++i) {
+            acc_t e = {0.0, 0.0};
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                acc_add(&e, inv_dist(pos[2 * i], pos[2 * i + 1], pos[2 * j], pos[2 * j + 1]));
+            }
+            local_e[i] = 0.5 * acc_get(&e);
+        }
+    }
+    return isfinite(*energy) ? TCO_OK : TCO_ERR_NONFINITE;
+}
+
+/* One gradient row: g = sum over sources j (j != skip) of -(r - r_j)/|r - r_j|^3,
+ * and the row's sum of 1/|r - r_j| (both compensated). */
+static void grad_row(double x, double y, const double* src, int64_t ns, int64_t skip,
+                     const unsigned char* exclude, acc_t* gx, acc_t* gy, acc_t* e)
+{
+    for (int64_t j = 0; j < ns; ++j) {
+        if (j == skip) continue;
+        if (exclude && exclude[j]) continue;
+        double dx = x - src[2 * j];
+        double dy = y - src[2 * j + 1];
+        double r2 = dx * dx + dy * dy;
+        double inv = 1.0 / sqrt(r2);
+        double inv3 = inv * inv * inv;
+        acc_add(gx, -dx * inv3);
+        acc_add(gy, -dy * inv3);
+        if (e) acc_add(e, inv);
+    }
+}
+
+/* g_i = dE/dr_i = sum_{j != i} -(r_i - r_j)/|r_i - r_j|^3 (analytic gradient of
+ * Eq. hamiltonian; the force is -g).  grad: 2n doubles, interleaved. */
+int tco_grad(const double* pos, int64_t n, double* grad)
+{
+    if (n < 0 || (n > 0 && (!pos || !grad))) return TCO_ERR_INVALID_ARG;
+    int st = check_inside(pos, n);
+    if (st) return st;
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        acc_t gx = {0.0, 0.0}, gy = {0.0, 0.0};
+        grad_row(pos[2 * i], pos[2 * i + 1], pos, n, i, NULL, &gx, &gy, NULL);
+        grad[2 * i] = acc_get(&gx);
+        grad[2 * i + 1] = acc_get(&gy);
+        if (!isfinite(grad[2 * i]) || !isfinite(grad[2 * i + 1])) bad = 1;
+    }
+    return bad ? TCO_ERR_NONFINITE : TCO_OK;
+}
+
+/* Gradient rows of selected charges against all n (Sec. II E: n_act rows x N).
+ * rows: m indices; grad_rows: 2m; e_rows (nullable, m): sum_{j != i} 1/r_ij. */
+int tco_rows_grad(const double* pos, int64_t n, const int32_t* rows, int64_t m,
+                  double* grad_rows, double* e_rows)
+{
+    if (n < 0 || m < 0 || (m > 0 && (!rows || !grad_rows || !pos))) return TCO_ERR_INVALID_ARG;
+    int bad = 0;
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t i = rows[k];
+        if (i < 0 || i >= n) return TCO_ERR_INVALID_ARG;
+        acc_t gx = {0.0, 0.0}, gy = {0.0, 0.0}, e = {0.0, 0.0};
+        grad_row(pos[2 * i], pos[2 * i + 1], pos, n, i, NULL, &gx, &gy, &e);
+        grad_rows[2 * k] = acc_get(&gx);
+        grad_rows[2 * k + 1] = acc_get(&gy);
+        if (e_rows) e_rows[k] = acc_get(&e);
+        if (!isfinite(grad_rows[2 * k]) || !isfinite(grad_rows[2 * k + 1])) bad = 1;
+    }
+    return bad ? TCO_ERR_NONFINITE : TCO_OK;
+}
+
+static unsigned char* membership(int64_t n, const int32_t* idx, int64_t m, int* st)
+{
+    unsigned char* in_a = (unsigned char*)calloc((size_t)(n > 0 ? n : 1), 1);
+    *st = TCO_OK;
+    if (!in_a) { *st = TCO_ERR_NO_MEMORY; return NULL; }
+    for (int64_t k = 0; k < m; ++k) {
+        if (idx[k] < 0 || idx[k] >= n || in_a[idx[k]]) {
+            free(in_a);
+            *st = TCO_ERR_INVALID_ARG;
+            return NULL;
+        }
+        in_a[idx[k]] = 1;
+    }
+    return in_a;
+}
+
+/* Subdomain objective of Sec. II D for active set A (idx, m) whose charges sit
+ * at act (2m) while every other charge j in F sits at snap[j]:
+ *   e_k = 1/2 sum_{k' in A, k' != k} 1/|a_k - a_k'| + sum_{j in F} 1/|a_k - s_j|,
+ *   E_sub = sum_k e_k,  grad_k = dE_sub/da_k
+ *         = sum_{k' != k} -(a_k - a_k')/|.|^3 + sum_{j in F} -(a_k - s_j)/|.|^3.
+ * (The A-A pair enters E_sub once via the two halves, and each half-term's
+ * derivative appears in both rows, so the row gradient carries the full A-A
+ * term.)  grad (2m), e (nullable, m), e_sub (nullable). */
+int tco_subdomain_grad(const double* snap, int64_t n, const int32_t* idx, int64_t m,
+                       const double* act, double* grad, double* e, double* e_sub)
+{
+    if (n < 0 || m < 0 || (m > 0 && (!idx || !act || !grad || !snap))) return TCO_ERR_INVALID_ARG;
+    int st;
+    unsigned char* in_a = membership(n, idx, m, &st);
+    if (!in_a) return st;
+    acc_t tot = {0.0, 0.0};
+    int bad = 0;
+    for (int64_t k = 0; k < m; ++k) {
+        acc_t gx = {0.0, 0.0}, gy = {0.0, 0.0}, ef = {0.0, 0.0}, ea = {0.0, 0.0};
+        double x = act[2 * k], y = act[2 * k + 1];
+        grad_row(x, y, snap, n, -1, in_a, &gx, &gy, &ef);
+        grad_row(x, y, act, m, k, NULL, &gx, &gy, &ea);
+        grad[2 * k] = acc_get(&gx);
+        grad[2 * k + 1] = acc_get(&gy);
+        double ek = 0.5 * acc_get(&ea) + acc_get(&ef);
+        if (e) e[k] = ek;
+        acc_add(&tot, ek);
+        if (!isfinite(grad[2 * k]) || !isfinite(grad[2 * k + 1]) || !isfinite(ek)) bad = 1;
+    }
+    if (e_sub) *e_sub = acc_get(&tot);
+    free(in_a);
+    return bad ? TCO_ERR_NONFINITE : TCO_OK;
+}
+
+/* Energy change of moving the charges of A (idx, m) from pos[idx] to new_act (2m),
+ * summed directly as pair differences (never as a difference of totals):
+ *   dE = sum_{i in A} sum_{j not in A} (1/|n_i - p_j| - 1/|p_i - p_j|)
+ *      + sum_{i<k in A} (1/|n_i - n_k| - 1/|p_i - p_k|).
+ * This equals E_sub(new) - E_sub(old) of Sec. II D and E(new) - E(old) of
+ * Eq. hamiltonian. */
+int tco_delta_energy(const double* pos, int64_t n, const int32_t* idx, int64_t m,
+                     const double* new_act, double* delta)
+{
+    if (n < 0 || m < 0 || !delta || (m > 0 && (!idx || !new_act || !pos))) return TCO_ERR_INVALID_ARG;
+    int st;
+    unsigned char* in_a = membership(n, idx, m, &st);
+    if (!in_a) return st;
+    acc_t d = {0.0, 0.0};
+    for (int64_t a = 0; a < m; ++a) {
+        int64_t i = idx[a];
+        double nx = new_act[2 * a], ny = new_act[2 * a + 1];
+        double px = pos[2 * i], py = pos[2 * i + 1];
+        for (int64_t j = 0; j < n; ++j) {
+            if (in_a[j]) continue;
+            double qx = pos[2 * j], qy = pos[2 * j + 1];
+            acc_add(&d, inv_dist(nx, ny, qx, qy) - inv_dist(px, py, qx, qy));
+        }
+        for (int64_t b = a + 1; b < m; ++b) {
+            int64_t k = idx[b];
+            acc_add(&d, inv_dist(nx, ny, new_act[2 * b], new_act[2 * b + 1]) -
+                            inv_dist(px, py, pos[2 * k], pos[2 * k + 1]));
+        }
+    }
+    *delta = acc_get(&d);
+    free(in_a);
+    return isfinite(*delta) ? TCO_OK : TCO_ERR_NONFINITE;
+}
+
+/* ---------------------------------------------------------- constraint --- */
+
+/* Hard wall of Eq. (potential) as a projection: r <- r * min(1, radius/|r|).
+ * A charge with flags[i] != 0 is pinned to the unit circle (the boundary
+ * population of Sec. II B): r <- r/|r| (left unchanged at the origin). */
+int tco_project(double* pos, int64_t n, double radius, const unsigned char* flags)
+{
+    if (n < 0 || (n > 0 && !pos) || !(radius > 0.0)) return TCO_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[2 * i], y = pos[2 * i + 1];
+        double r = sqrt(x * x + y * y);
+        if (flags && flags[i]) {
+            if (r > 0.0) {
+                pos[2 * i] = x / r;
+                pos[2 * i + 1] = y / r;
+            }
+        } else if (r > radius) {
+            double s = radius / r;
+            pos[2 * i] = x * s;
+            pos[2 * i + 1] = y * s;
+        }
+    }
+    return TCO_OK;
+}
+
+/* Gradient with the components the wall blocks removed ("tangential" gradient):
+ * pinned charges keep only the component along the circle; a free charge at the
+ * wall (|r| >= radius (1 - 1e-12)) whose force -g points outward keeps only the
+ * tangential part; every other charge keeps g.  Returns RMS and max of |pg_i|. */
+int tco_projected_grad(const double* pos, const double* grad, int64_t n, double radius,
+                       const unsigned char* flags, double* pg, double* rms, double* gmax)
+{
+    if (n < 0 || (n > 0 && (!pos || !grad || !pg))) return TCO_ERR_INVALID_ARG;
+    acc_t ss = {0.0, 0.0};
+    double mx = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[2 * i], y = pos[2 * i + 1];
+        double gx = grad[2 * i], gy = grad[2 * i + 1];
+        double r = sqrt(x * x + y * y);
+        int pinned = flags && flags[i];
+        if (r > 0.0 && (pinned || r >= radius * (1.0 - 1e-12))) {
+            double ux = x / r, uy = y / r;
+            double gr = gx * ux + gy * uy;
+            if (pinned || gr < 0.0) {
+                gx -= gr * ux;
+                gy -= gr * uy;
+            }
+        }
+        pg[2 * i] = gx;
+        pg[2 * i + 1] = gy;
+        double a2 = gx * gx + gy * gy;
+        acc_add(&ss, a2);
+        if (sqrt(a2) > mx) mx = sqrt(a2);
+    }
+    if (rms) *rms = n > 0 ? sqrt(acc_get(&ss) / (double)n) : 0.0;
+    if (gmax) *gmax = mx;
+    return TCO_OK;
+}
+
+/* -------------------------------------------------------------- descent --- */
+
+/* Projected gradient descent x <- P(x - eta g(x)), `steps` times, over all n
+ * charges.  trace (nullable, steps+1): E before each step and after the last. */
+int tco_pgd(double* pos, int64_t n, double eta, int64_t steps, double radius,
+            const unsigned char* flags, double* trace)
+{
+    if (n < 0 || steps < 0 || (n > 0 && !pos)) return TCO_ERR_INVALID_ARG;
+    double* g = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    if (!g) return TCO_ERR_NO_MEMORY;
+    int st = TCO_OK;
+    for (int64_t k = 0; k <= steps; ++k) {
+        if (trace) {
+            st = tco_energy(pos, n, &trace[k], NULL);
+            if (st) break;
+        }
+        if (k == steps) break;
+        st = tco_grad(pos, n, g);
+        if (st) break;
+        for (int64_t i = 0; i < 2 * n; ++i) pos[i] = pos[i] - eta * g[i];
+        tco_project(pos, n, radius, flags);
+    }
+    free(g);
+    return st;
+}
+
+/* Dot product of two length-len vectors, compensated. */
+static double dot(const double* a, const double* b, int64_t len)
+{
+    acc_t s = {0.0, 0.0};
+    for (int64_t i = 0; i < len; ++i) acc_add(&s, a[i] * b[i]);
+    return acc_get(&s);
+}
+
+/* Projected gradient descent on one subdomain with Barzilai-Borwein steps.
+ * Charges of A (idx, m) start at snap[idx] and move; every other charge stays
+ * at snap.  Step k: g_k = grad E_sub(x_k) (tco_subdomain_grad),
+ *   alpha_0 = step0;  alpha_k = s^T y / y^T y (BB2, s = x_k - x_{k-1},
+ *   y = g_k - g_{k-1}) when s^T y > 0, else alpha_max; clamped to
+ *   [alpha_min, alpha_max];  x_{k+1} = P(x_k - alpha_k g_k).
+ * act_out (2m): x after `steps` steps. */
+int tco_subdomain_bb(const double* snap, int64_t n, const int32_t* idx, int64_t m,
+                     double step0, double alpha_min, double alpha_max, int64_t steps,
+                     double radius, double* act_out)
+{
+    if (n < 0 || m < 0 || steps < 0 || (m > 0 && (!snap || !idx || !act_out))) return TCO_ERR_INVALID_ARG;
+    size_t sz = sizeof(double) * 2 * (size_t)(m > 0 ? m : 1);
+    double *x = act_out, *g = (double*)malloc(sz), *xp = (double*)malloc(sz), *gp = (double*)malloc(sz);
+    double *s = (double*)malloc(sz), *y = (double*)malloc(sz);
+    if (!g || !xp || !gp || !s || !y) { free(g); free(xp); free(gp); free(s); free(y); return TCO_ERR_NO_MEMORY; }
+    for (int64_t k = 0; k < m; ++k) {
+        x[2 * k] = snap[2 * idx[k]];
+        x[2 * k + 1] = snap[2 * idx[k] + 1];
+    }
+    int st = TCO_OK;
+    for (int64_t it = 0; it < steps; ++it) {
+        st = tco_subdomain_grad(snap, n, idx, m, x, g, NULL, NULL);
+        if (st) break;
+        double alpha = step0;
+        if (it > 0) {
+            for (int64_t i = 0; i < 2 * m; ++i) { s[i] = x[i] - xp[i]; y[i] = g[i] - gp[i]; }
+            double sy = dot(s, y, 2 * m), yy = dot(y, y, 2 * m);
+            alpha = (sy > 0.0 && yy > 0.0) ? sy / yy : alpha_max;
+            if (alpha < alpha_min) alpha = alpha_min;
+            if (alpha > alpha_max) alpha = alpha_max;
+        }
+        memcpy(xp, x, sz);
+        memcpy(gp, g, sz);
+        for (int64_t i = 0; i < 2 * m; ++i) x[i] = x[i] - alpha * g[i];
+        tco_project(x, m, radius, NULL);
+    }
+    free(g); free(xp); free(gp); free(s); free(y);
+    return st;
+}
+
+/* Sequential FP64 accept/reject of relaxed subdomains against the current
+ * configuration pos (in/out).  For s = 0 .. n_sub-1 in order: a subdomain that
+ * shares a charge with an already accepted one is skipped (accepted = 2);
+ * otherwise dE_s = tco_delta_energy(current pos, A_s -> new_act_s) and the move
+ * is applied iff dE_s < 0 (accepted = 1, else 0).  delta (n_sub), accepted (n_sub). */
+int tco_accept_sequential(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
+                          int64_t n_sub, const double* new_act, double* delta, unsigned char* accepted)
+{
+    if (n < 0 || n_sub < 0 || (n_sub > 0 && (!idx || !offsets || !new_act || !delta || !accepted)))
+        return TCO_ERR_INVALID_ARG;
+    unsigned char* taken = (unsigned char*)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!taken) return TCO_ERR_NO_MEMORY;
+    int st = TCO_OK;
+    for (int64_t s = 0; s < n_sub; ++s) {
+        int64_t b = offsets[s], e = offsets[s + 1];
+        int clash = 0;
+        for (int64_t k = b; k < e; ++k) if (taken[idx[k]]) clash = 1;
+        if (clash) { delta[s] = 0.0; accepted[s] = 2; continue; }
+        st = tco_delta_energy(pos, n, idx + b, e - b, new_act + 2 * b, &delta[s]);
+        if (st) break;
+        if (delta[s] < 0.0) {
+            accepted[s] = 1;
+            for (int64_t k = b; k < e; ++k) {
+                taken[idx[k]] = 1;
+                pos[2 * idx[k]] = new_act[2 * k];
+                pos[2 * idx[k] + 1] = new_act[2 * k + 1];
+            }
+        } else {
+            accepted[s] = 0;
+        }
+    }
+    free(taken);
+    return st;
+}
+
+/* Smooth wall parameterisation used by the quasi-Newton solver.
+ *
+ * The paper writes interior charges as r = sigma sin^2 t (Sec. II D), which makes
+ * the wall r = sigma a smooth maximum of r(t), so the wall needs no projection.
+ * The map used here has the same property in Cartesian form and no polar
+ * singularity at the centre: a free charge is z in R^2 with
+ *     x = sigma sin(|z|) z/|z|     (x = sigma z in the limit z -> 0),
+ * and a pinned charge (the boundary population of Sec. II B) is x = z/|z|.
+ * Chain rule (cf. the paper's dE/dt, dE/du): with g = dE/dx, u = z/|z|,
+ * g_r = g.u, g_t = g - g_r u,
+ *     free:   dE/dz = sigma ( sin|z|/|z| g_t + cos|z| g_r u )   (sigma g at z = 0)
+ *     pinned: dE/dz = g_t / |z|.                                           */
+static void z_to_x(const double* z, int64_t n, double sigma, const unsigned char* flags, double* x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double zx = z[2 * i], zy = z[2 * i + 1];
+        double rho = sqrt(zx * zx + zy * zy);
+        if (flags && flags[i]) {
+            x[2 * i] = zx / rho;
+            x[2 * i + 1] = zy / rho;
+        } else if (rho > 0.0) {
+            double f = sigma * sin(rho) / rho;
+            x[2 * i] = zx * f;
+            x[2 * i + 1] = zy * f;
+        } else {
+            x[2 * i] = 0.0;
+            x[2 * i + 1] = 0.0;
+        }
+    }
+}
+
+static void x_to_z(const double* x, int64_t n, double sigma, const unsigned char* flags, double* z)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double px = x[2 * i], py = x[2 * i + 1];
+        double r = sqrt(px * px + py * py);
+        if (flags && flags[i]) {
+            z[2 * i] = r > 0.0 ? px / r : 1.0;
+            z[2 * i + 1] = r > 0.0 ? py / r : 0.0;
+        } else if (r > 0.0) {
+            double q = r / sigma;
+            if (q > 1.0) q = 1.0;
+            double f = asin(q) / r;
+            z[2 * i] = px * f;
+            z[2 * i + 1] = py * f;
+        } else {
+            z[2 * i] = 0.0;
+            z[2 * i + 1] = 0.0;
+        }
+    }
+}
+
+static void grad_z(const double* z, const double* g, int64_t n, double sigma, const unsigned char* flags,
+                   double* gz)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double zx = z[2 * i], zy = z[2 * i + 1];
+        double gx = g[2 * i], gy = g[2 * i + 1];
+        double rho = sqrt(zx * zx + zy * zy);
+        if (rho == 0.0) {
+            gz[2 * i] = (flags && flags[i]) ? 0.0 : sigma * gx;
+            gz[2 * i + 1] = (flags && flags[i]) ? 0.0 : sigma * gy;
+            continue;
+        }
+        double ux = zx / rho, uy = zy / rho;
+        double gr = gx * ux + gy * uy;
+        double tx = gx - gr * ux, ty = gy - gr * uy;
+        if (flags && flags[i]) {
+            gz[2 * i] = tx / rho;
+            gz[2 * i + 1] = ty / rho;
+        } else {
+            double a = sin(rho) / rho, c = cos(rho);
+            gz[2 * i] = sigma * (a * tx + c * gr * ux);
+            gz[2 * i + 1] = sigma * (a * ty + c * gr * uy);
+        }
+    }
+}
+
+/* Limited-memory BFGS on the smooth wall parameterisation, with a maximum
+ * displacement cap and no line search, over all n charges of one configuration.
+ *
+ * State z (2n), gradient gz = dE/dz.  Iteration, memory M pairs (s_j, y_j) with
+ * rho_j = 1/(s_j^T y_j):
+ *   stop when RMS_i |gz_i| < gtol;
+ *   two-loop recursion (Nocedal & Wright, Alg. 7.4) on q = gz with H0 = gamma I,
+ *   gamma = s^T y / y^T y of the newest pair (step0 without history): d = -H gz;
+ *   if gz^T d >= 0 the history is cleared and d = -step0 gz;
+ *   alpha = min(1, maxstep / max_i |d_i|) (each charge moves at most maxstep in z,
+ *   hence at most sigma maxstep in x);  z <- z + alpha d;
+ *   the pair s = z_new - z, y = gz_new - gz is kept iff s^T y > 1e-12 |s||y|
+ *   (the oldest drops out beyond M).
+ * pos (in/out, 2n): x of the final z.  Reports iterations and final RMS |gz|. */
+int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+              double step0, double maxstep, double sigma, const unsigned char* flags,
+              int64_t* iters_out, double* rms_out)
+{
+    if (n < 0 || memory < 1 || max_iter < 0 || (n > 0 && !pos) || !(sigma > 0.0)) return TCO_ERR_INVALID_ARG;
+    int64_t L = 2 * n;
+    size_t sz = sizeof(double) * (size_t)(L > 0 ? L : 1);
+    double* z = (double*)malloc(sz);
+    double* zn = (double*)malloc(sz);
+    double* g = (double*)malloc(sz);
+    double* gz = (double*)malloc(sz);
+    double* gzn = (double*)malloc(sz);
+    double* d = (double*)malloc(sz);
+    double* S = (double*)malloc(sz * (size_t)memory);
+    double* Y = (double*)malloc(sz * (size_t)memory);
+    double* rho = (double*)malloc(sizeof(double) * (size_t)memory);
+    double* al = (double*)malloc(sizeof(double) * (size_t)memory);
+    if (!z || !zn || !g || !gz || !gzn || !d || !S || !Y || !rho || !al) {
+        free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
+        return TCO_ERR_NO_MEMORY;
+    }
+    memset(z, 0, sz);
+    int64_t hist = 0, head = 0; /* ring buffer: newest pair at (head - 1) mod M */
+    int64_t it = 0;
+    double rms = 0.0;
+    x_to_z(pos, n, sigma, flags, z);
+    z_to_x(z, n, sigma, flags, pos);
+    int st = tco_grad(pos, n, g);
+    if (!st) {
+        grad_z(z, g, n, sigma, flags, gz);
+        rms = n > 0 ? sqrt(dot(gz, gz, L) / (double)n) : 0.0;
+    }
+    for (; !st && it < max_iter; ++it) {
+        if (rms < gtol) break;
+        for (int64_t i = 0; i < L; ++i) d[i] = gz[i];
+        for (int64_t q = 0; q < hist; ++q) {
+            int64_t j = ((head - 1 - q) % memory + memory) % memory;
+            al[j] = rho[j] * dot(S + j * L, d, L);
+            for (int64_t i = 0; i < L; ++i) d[i] -= al[j] * Y[j * L + i];
+        }
+        double gamma = step0;
+        if (hist > 0) {
+            int64_t j = ((head - 1) % memory + memory) % memory;
+            gamma = dot(S + j * L, Y + j * L, L) / dot(Y + j * L, Y + j * L, L);
+        }
+        for (int64_t i = 0; i < L; ++i) d[i] *= gamma;
+        for (int64_t q = hist - 1; q >= 0; --q) {
+            int64_t j = ((head - 1 - q) % memory + memory) % memory;
+            double b = rho[j] * dot(Y + j * L, d, L);
+            for (int64_t i = 0; i < L; ++i) d[i] += S[j * L + i] * (al[j] - b);
+        }
+        for (int64_t i = 0; i < L; ++i) d[i] = -d[i];
+        if (dot(gz, d, L) >= 0.0) {
+            hist = 0;
+            head = 0;
+            for (int64_t i = 0; i < L; ++i) d[i] = -step0 * gz[i];
+        }
+        double dmax = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double a = sqrt(d[2 * i] * d[2 * i] + d[2 * i + 1] * d[2 * i + 1]);
+            if (a > dmax) dmax = a;
+        }
+        double alpha = (dmax > maxstep) ? maxstep / dmax : 1.0;
+        for (int64_t i = 0; i < L; ++i) zn[i] = z[i] + alpha * d[i];
+        z_to_x(zn, n, sigma, flags, pos);
+        st = tco_grad(pos, n, g);
+        if (st) break;
+        grad_z(zn, g, n, sigma, flags, gzn);
+        rms = n > 0 ? sqrt(dot(gzn, gzn, L) / (double)n) : 0.0;
+        /* the candidate pair is tested first and stored only if kept, so a
+         * rejected pair never overwrites the oldest stored one */
+        acc_t sy_a = {0.0, 0.0}, ss_a = {0.0, 0.0}, yy_a = {0.0, 0.0};
+        for (int64_t i = 0; i < L; ++i) {
+            double si = zn[i] - z[i], yi = gzn[i] - gz[i];
+            acc_add(&sy_a, si * yi);
+            acc_add(&ss_a, si * si);
+            acc_add(&yy_a, yi * yi);
+        }
+        double sy = acc_get(&sy_a);
+        if (sy > 1e-12 * sqrt(acc_get(&ss_a)) * sqrt(acc_get(&yy_a))) {
+            double* Sj = S + head * L;
+            double* Yj = Y + head * L;
+            for (int64_t i = 0; i < L; ++i) { Sj[i] = zn[i] - z[i]; Yj[i] = gzn[i] - gz[i]; }
+            rho[head] = 1.0 / sy;
+            head = (head + 1) % memory;
+            if (hist < memory) ++hist;
+        }
+        memcpy(z, zn, sz);
+        memcpy(gz, gzn, sz);
+    }
+    if (iters_out) *iters_out = it;
+    if (rms_out) *rms_out = rms;
+    free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
+    return st;
+}

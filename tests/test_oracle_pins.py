@@ -1,0 +1,390 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties an oracle function to something other than itself: a closed
+form, an extended-precision brute force, an exact invariant, a derivative
+relation between two different oracle functions, a known minimum, or a number
+the paper prints.  A dropped term, a wrong sign, a swapped index or a
+transposed operand in tests/../oracle/tco.c fails at least one of them.
+"""
+
+from __future__ import annotations
+
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.txt")
+
+
+def golden() -> dict:
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if "=" in line:
+                k, v = line.split("=", 1)
+                out[k.strip()] = float(v)
+    return out
+
+
+def gross(pos):
+    """G_i = sum_{j != i} 1/r_ij^2, the scale of the gradient row before cancellation."""
+    d = pos[:, None, :] - pos[None, :, :]
+    r2 = (d ** 2).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    return (1.0 / r2).sum(1)
+
+
+def cubic(pos):
+    """C_i = sum_{j != i} 2/r_ij^3: how much row i's gradient moves per unit position error."""
+    d = pos[:, None, :] - pos[None, :, :]
+    r = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    return (2.0 / r ** 3).sum(1)
+
+
+# ------------------------------------------------------------ closed forms ---
+
+def ngon_energy_mp(n):
+    """Regular n-gon on the unit circle: E = (n/2) sum_{k=1}^{n-1} 1/(2 sin(pi k/n)) (chord lengths)."""
+    mp.mp.dps = 40
+    return mp.mpf(n) / 2 * mp.fsum(1 / (2 * mp.sin(mp.pi * k / n)) for k in range(1, n))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 10, 100, 1000])
+def test_ngon_closed_form(n):
+    pos = synth.ngon(n, phase=0.37)
+    e = oracle.energy(pos)
+    ref = float(ngon_energy_mp(n))
+    assert abs(e - ref) <= 4e-16 * ref * max(1.0, math.log2(n))
+    g = oracle.grad(pos)
+    u = pos / np.linalg.norm(pos, axis=1)[:, None]
+    gr = (g * u).sum(1)
+    gt = g - gr[:, None] * u
+    G = gross(pos)
+    # symmetry: no tangential force, equal inward radial gradient (outward force) on all charges;
+    # the vertices' own rounding (~1 ulp of cos, sin, each) moves a row by up to ~1e-15 C_i
+    tol = 1e-13 * G + 2e-15 * cubic(pos)
+    assert np.all(np.linalg.norm(gt, axis=1) <= tol)
+    assert np.all(gr < 0)
+    assert np.ptp(gr) <= 2 * tol.max()
+
+
+def test_small_hand_cases():
+    e2 = oracle.energy(np.array([[1.0, 0.0], [-1.0, 0.0]]))
+    assert e2 == 0.5
+    g2 = oracle.grad(np.array([[1.0, 0.0], [-1.0, 0.0]]))
+    # dE/dr_1 = -(r_1 - r_2)/|r_1 - r_2|^3 = -(2,0)/8: points inward; the force -g points outward
+    np.testing.assert_array_equal(g2, [[-0.25, 0.0], [0.25, 0.0]])
+    tri = synth.ngon(3)
+    assert abs(oracle.energy(tri) - math.sqrt(3.0)) <= 2e-16 * math.sqrt(3.0)
+    assert oracle.energy(np.zeros((0, 2))) == 0.0
+    assert oracle.energy(np.array([[0.3, 0.1]])) == 0.0
+    np.testing.assert_array_equal(oracle.grad(np.array([[0.3, 0.1]])), [[0.0, 0.0]])
+
+
+def brute_mp(pos):
+    mp.mp.dps = 40
+    n = pos.shape[0]
+    P = [(mp.mpf(float(x)), mp.mpf(float(y))) for x, y in pos]
+    E = mp.mpf(0)
+    g = [[mp.mpf(0), mp.mpf(0)] for _ in range(n)]
+    le = [mp.mpf(0) for _ in range(n)]
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            dx, dy = P[i][0] - P[j][0], P[i][1] - P[j][1]
+            r = mp.sqrt(dx * dx + dy * dy)
+            if i < j:
+                E += 1 / r
+            le[i] += 1 / (2 * r)
+            g[i][0] -= dx / r ** 3
+            g[i][1] -= dy / r ** 3
+    return E, np.array([[float(a), float(b)] for a, b in g]), np.array([float(v) for v in le])
+
+
+@pytest.mark.parametrize("n,seed", [(3, 0), (7, 1), (12, 2), (20, 3)])
+def test_brute_force_extended_precision(n, seed):
+    pos = synth.arcsine_disk(n, seed)
+    E, g, le = brute_mp(pos)
+    e, loc = oracle.energy(pos, local=True)
+    assert abs(e - float(E)) <= 2e-16 * float(E)
+    np.testing.assert_allclose(loc, le, rtol=4e-16, atol=0)
+    G = gross(pos)
+    go = oracle.grad(pos)
+    assert np.all(np.abs(go - g) <= 4e-16 * G[:, None])
+    rows = np.array([n - 1, 0, n // 2], dtype=np.int32)
+    gr, er = oracle.rows_grad(pos, rows)
+    np.testing.assert_array_equal(gr, go[rows])
+    np.testing.assert_allclose(er, 2 * le[rows], rtol=4e-16)
+
+
+# ------------------------------------------------------------- invariants ---
+
+def test_invariances_and_identities():
+    n = 300
+    pos = synth.arcsine_disk(n, 5)
+    e, loc = oracle.energy(pos, local=True)
+    g = oracle.grad(pos)
+    G = gross(pos)
+    th = 1.234
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    pr = pos @ R.T
+    assert abs(oracle.energy(pr) - e) <= 1e-14 * e
+    gr = oracle.grad(pr)
+    assert np.all(np.linalg.norm(gr - g @ R.T, axis=1) <= 1e-13 * G)
+    refl = pos * np.array([1.0, -1.0])
+    assert abs(oracle.energy(refl) - e) <= 1e-14 * e
+    np.testing.assert_allclose(oracle.grad(refl), g * np.array([1.0, -1.0]), atol=1e-13 * G.max(), rtol=0)
+    perm = np.random.default_rng(0).permutation(n)
+    assert abs(oracle.energy(pos[perm]) - e) <= 1e-14 * e
+    assert np.all(np.abs(oracle.grad(pos[perm]) - g[perm]) <= 1e-13 * G[perm, None])
+    # Newton's third law: the gradient rows sum to zero
+    assert np.all(np.abs(g.sum(0)) <= 1e-13 * G.sum())
+    # Euler's theorem for the degree -1 homogeneous E: sum_i r_i . g_i = -E
+    assert abs((pos * g).sum() + e) <= 1e-12 * e
+    # local energies add up to the total (Sec. II C step 1)
+    assert abs(loc.sum() - e) <= 1e-14 * e
+
+
+def test_scaling_law_degree_minus_one():
+    pos = synth.arcsine_disk(200, 9) * 0.5
+    e = oracle.energy(pos)
+    assert abs(oracle.energy(pos * 0.5) - 2.0 * e) <= 1e-14 * e
+
+
+# ------------------------------------------------- derivative relations ---
+
+def test_gradient_matches_central_differences_of_delta_energy():
+    """dE/dx_i from tco_grad equals the central difference of the pairwise dE (a different function)."""
+    n = 2000
+    pos = synth.arcsine_disk(n, 11)
+    g = oracle.grad(pos)
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for i in rng.choice(n, 6, replace=False):
+        for c in range(2):
+            plus = pos[i].copy()
+            minus = pos[i].copy()
+            plus[c] += h
+            minus[c] -= h
+            if np.linalg.norm(plus) > 1 or np.linalg.norm(minus) > 1:
+                continue
+            dp = oracle.delta_energy(pos, [i], plus[None])
+            dm = oracle.delta_energy(pos, [i], minus[None])
+            fd = (dp - dm) / (2 * h)
+            # truncation h^2/6 |d3E| plus rounding eps |e_i| / h
+            d = np.linalg.norm(pos - pos[i], axis=1)
+            d[i] = np.inf
+            tol = h * h * (6.0 / d ** 4).sum() + 1e-16 * (1.0 / d).sum() / h * 4
+            assert abs(fd - g[i, c]) <= tol + 1e-9 * abs(g[i, c])
+
+
+def test_subdomain_objective_definition_and_gradient():
+    n = 400
+    pos = synth.arcsine_disk(n, 3)
+    idx = np.array(sorted(np.random.default_rng(2).choice(n, 40, replace=False)), dtype=np.int32)
+    act = pos[idx].copy()
+    g, e, esub = oracle.subdomain_grad(pos, idx, act)
+    # E = E_sub + E(F alone): the subdomain objective is E minus the constant F-F energy
+    F = np.setdiff1d(np.arange(n), idx)
+    etot = oracle.energy(pos)
+    assert abs(esub + oracle.energy(pos[F]) - etot) <= 1e-13 * etot
+    # with A at the snapshot, the subdomain gradient rows equal the full gradient rows
+    gf = oracle.grad(pos)
+    np.testing.assert_allclose(g, gf[idx], rtol=0, atol=1e-13 * np.abs(gf).max())
+    # move A, then: E_sub(new) - E_sub(old) == pairwise dE, and the gradient at the moved
+    # configuration matches central differences of E_sub
+    rng = np.random.default_rng(4)
+    act2 = act + rng.normal(0, 1e-3, act.shape)
+    act2 = oracle.project(act2)
+    g2, _, esub2 = oracle.subdomain_grad(pos, idx, act2)
+    de = oracle.delta_energy(pos, idx, act2)
+    assert abs((esub2 - esub) - de) <= 1e-11 * esub
+    h = 1e-6
+    for k in [0, 7, 39]:
+        for c in range(2):
+            ap = act2.copy()
+            am = act2.copy()
+            ap[k, c] += h
+            am[k, c] -= h
+            dp = oracle.delta_energy(pos, idx, ap)
+            dm = oracle.delta_energy(pos, idx, am)
+            fd = (dp - dm) / (2 * h)
+            assert abs(fd - g2[k, c]) <= 1e-5 * (1 + abs(g2[k, c]))
+
+
+def test_delta_energy_against_extended_precision():
+    n = 25
+    pos = synth.arcsine_disk(n, 21)
+    idx = np.array([2, 5, 6, 11, 24], dtype=np.int32)
+    new = pos[idx] * 0.97 + 0.01
+    E0, _, _ = brute_mp(pos)
+    p1 = pos.copy()
+    p1[idx] = new
+    E1, _, _ = brute_mp(p1)
+    de = oracle.delta_energy(pos, idx, new)
+    assert abs(de - float(E1 - E0)) <= 1e-15 * float(E0)
+
+
+def test_delta_energy_difference_of_totals_small_n():
+    n = 1500
+    pos = synth.arcsine_disk(n, 8)
+    idx = np.arange(100, 400, 3, dtype=np.int32)
+    new = oracle.project(pos[idx] + np.random.default_rng(6).normal(0, 2e-3, (idx.size, 2)))
+    p1 = pos.copy()
+    p1[idx] = new
+    e0, e1 = oracle.energy(pos), oracle.energy(p1)
+    de = oracle.delta_energy(pos, idx, new)
+    assert abs(de - (e1 - e0)) <= 1e-13 * e0
+
+
+# ----------------------------------------------------------- constraint ---
+
+def test_project():
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-1.5, 1.5, (500, 2))
+    out = oracle.project(pts, radius=0.9)
+    r_in = np.linalg.norm(pts, axis=1)
+    inside = r_in <= 0.9
+    np.testing.assert_array_equal(out[inside], pts[inside])
+    r_out = np.linalg.norm(out[~inside], axis=1)
+    assert np.all(np.abs(r_out - 0.9) <= 4e-16)
+    cross = pts[~inside, 0] * out[~inside, 1] - pts[~inside, 1] * out[~inside, 0]
+    assert np.all(np.abs(cross) <= 1e-15 * r_in[~inside])
+    assert np.all((pts[~inside] * out[~inside]).sum(1) > 0)
+    flags = np.zeros(500, np.uint8)
+    flags[::3] = 1
+    outp = oracle.project(pts, radius=0.9, flags=flags)
+    assert np.all(np.abs(np.linalg.norm(outp[::3], axis=1) - 1.0) <= 4e-16)
+
+
+def test_projected_grad():
+    pos = synth.ngon(12)
+    g = oracle.grad(pos)
+    pg, rms, mx = oracle.projected_grad(pos, g)
+    # on the circle the outward force is blocked; the n-gon is stationary
+    assert mx <= 1e-12 * np.abs(g).max()
+    inner = pos * 0.5
+    g2 = oracle.grad(inner)
+    pg2, _, _ = oracle.projected_grad(inner, g2)
+    np.testing.assert_array_equal(pg2, g2)
+
+
+# --------------------------------------------------------------- descent ---
+
+def test_pgd_step_and_descent():
+    n = 300
+    pos = synth.arcsine_disk(n, 13)
+    eta = 1e-4 / n
+    x1, tr = oracle.pgd(pos, eta, 1)
+    manual = oracle.project(pos - eta * oracle.grad(pos))
+    np.testing.assert_array_equal(x1, manual)
+    _, tr = oracle.pgd(pos, eta, 30)
+    assert np.all(np.diff(tr) < 0)
+    # the regular polygon on the wall is a fixed point of projected descent
+    ng = synth.ngon(9)
+    x, _ = oracle.pgd(ng, 1e-3, 5)
+    np.testing.assert_allclose(x, ng, atol=1e-15)
+
+
+def test_subdomain_bb_reduces_energy_and_fixed_step_is_pgd():
+    n = 600
+    pos = synth.arcsine_disk(n, 17)
+    idx = np.arange(0, n, 7, dtype=np.int32)
+    eta = 1e-4 / n
+    # alpha_min = alpha_max = step0 turns BB off: plain projected descent on E_sub
+    x = oracle.subdomain_bb(pos, idx, eta, eta, eta, 3)
+    a = pos[idx].copy()
+    for _ in range(3):
+        g, _, _ = oracle.subdomain_grad(pos, idx, a)
+        a = oracle.project(a - eta * g)
+    np.testing.assert_allclose(x, a, rtol=0, atol=1e-15)
+    xb = oracle.subdomain_bb(pos, idx, eta, 0.0, 10 * eta, 40)
+    assert oracle.delta_energy(pos, idx, xb) < oracle.delta_energy(pos, idx, x) < 0
+
+
+def test_accept_sequential():
+    n = 800
+    pos = synth.lattice_disk(n, 1, 0.05)
+    subs = [np.arange(0, 60, dtype=np.int32), np.arange(50, 120, dtype=np.int32),
+            np.arange(200, 260, dtype=np.int32)]
+    idx, off = synth.to_csr(subs)
+    eta = 1e-4 / n
+    new = np.concatenate([oracle.subdomain_bb(pos, s, eta, 0.0, 10 * eta, 20) for s in subs])
+    new[off[2]:off[3]] = pos[subs[2]] + 0.01  # an uphill move
+    new[off[2]:off[3]] = oracle.project(new[off[2]:off[3]])
+    p1, d, acc = oracle.accept_sequential(pos, idx, off, new)
+    assert acc[0] == 1 and d[0] < 0
+    assert acc[1] == 2  # shares charges 50..59 with an accepted subdomain
+    assert acc[2] == 0 and d[2] > 0
+    e0, e1 = oracle.energy(pos), oracle.energy(p1)
+    assert abs((e1 - e0) - d[0]) <= 1e-12 * e0
+    np.testing.assert_array_equal(p1[subs[0]], new[:60])
+    np.testing.assert_array_equal(p1[subs[2]], pos[subs[2]])
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 8])
+def test_lbfgs_reaches_ring_minimum(n):
+    """For these small N the lowest-energy state of charges in a disk is the ring (regular N-gon)."""
+    x, it, rms = oracle.lbfgs(synth.arcsine_disk(n, 2), max_iter=500, gtol=1e-12, step0=1e-3, maxstep=0.05)
+    assert rms < 1e-12
+    ref = float(ngon_energy_mp(n))
+    assert abs(oracle.energy(x) - ref) <= 1e-14 * ref
+    assert np.all(np.abs(np.linalg.norm(x, axis=1) - 1.0) <= 1e-12)
+
+
+def test_lbfgs_relaxed_energy_against_asymptotic_expansion():
+    """Relaxed minima at N = 100, 150 lie just above the fit of Eq. (asym) with the paper's coefficients."""
+    gd = golden()
+    for n, seed in [(100, 12), (150, 4)]:
+        x, it, rms = oracle.lbfgs(synth.arcsine_disk(n, seed), max_iter=2000, gtol=1e-9, step0=1e-5,
+                                  maxstep=0.03)
+        assert rms < 1e-9
+        e = oracle.energy(x)
+        easym = math.pi / 4 * n ** 2 + gd["k2"] * n ** 1.5 + gd["k3"] * n + gd["k4"] * n ** 0.5 + gd["k5"]
+        assert easym < e < easym * 1.006
+        # stationarity in Cartesian form: tangential force on wall charges, full force inside
+        pg, rms_c, mx = oracle.projected_grad(x, oracle.grad(x))
+        assert mx < 1e-6
+
+
+# ------------------------------------------------------ paper's numbers ---
+
+def test_paper_numbers_recomputed():
+    gd = golden()
+    n = 1e5
+    easym = math.pi / 4 * n ** 2 + gd["k2"] * n ** 1.5 + gd["k3"] * n + gd["k4"] * n ** 0.5 + gd["k5"]
+    assert abs(easym - gd["E_asym_1e5"]) <= 1e-12 * easym
+    dev = abs(gd["E_min_1e5"] - easym) / easym
+    assert abs(dev - gd["deviation_1e5"]) <= 5e-4 * gd["deviation_1e5"]
+    nb = gd["Nb_a"] * n ** (2 / 3) + gd["Nb_b"] * n ** (1 / 3) + gd["Nb_c"]
+    assert round(nb) == gd["N_b_best"]
+
+
+def test_arcsine_energy_trend():
+    """E/N^2 -> pi/4 (Sec. I): arcsine-random charges have E[1/|X-Y|] = pi/2, so E ~ (pi/4) N(N-1)."""
+    n = 1500
+    vals = [oracle.energy(synth.arcsine_disk(n, s)) / (n * (n - 1) / 2) for s in range(6)]
+    m = float(np.mean(vals))
+    se = float(np.std(vals, ddof=1)) / math.sqrt(len(vals))
+    assert abs(m - math.pi / 2) <= 4 * se + 2e-3
+
+
+def test_error_statuses():
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.energy(np.array([[0.2, 0.1], [0.2, 0.1]]))
+    assert e.value.code == 3
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.grad(np.array([[1.2, 0.0], [0.0, 0.0]]))
+    assert e.value.code == 4
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.delta_energy(synth.arcsine_disk(10, 0), [3, 3], np.zeros((2, 2)))
+    assert e.value.code == 1

@@ -1,0 +1,63 @@
+"""Seeded synthetic inputs: shape, determinism and distribution checks."""
+
+import math
+
+import numpy as np
+from scipy import stats
+
+import synth
+
+
+def test_arcsine_radii_follow_the_arcsine_cdf():
+    pos = synth.arcsine_disk(20000, 0)
+    r = np.linalg.norm(pos, axis=1)
+    assert r.max() <= 1.0
+    # radial CDF of rho ~ 1/sqrt(1 - r^2) over the disk: F(r) = 1 - sqrt(1 - r^2)
+    d, p = stats.kstest(r, lambda x: 1.0 - np.sqrt(1.0 - np.clip(x, 0, 1) ** 2))
+    assert p > 1e-3
+    th = np.arctan2(pos[:, 1], pos[:, 0])
+    assert stats.kstest((th + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-3
+
+
+def test_determinism():
+    np.testing.assert_array_equal(synth.arcsine_disk(1000, 3), synth.arcsine_disk(1000, 3))
+    assert not np.array_equal(synth.arcsine_disk(1000, 3), synth.arcsine_disk(1000, 4))
+    a = synth.lattice_disk(5000, 2)
+    np.testing.assert_array_equal(a, synth.lattice_disk(5000, 2))
+
+
+def test_lattice_background():
+    n = 20000
+    pos = synth.lattice_disk(n, 0)
+    assert pos.shape == (n, 2)
+    assert np.linalg.norm(pos, axis=1).max() <= 1.0
+    assert synth.min_pair_distance(pos) > 0.0
+    r = np.linalg.norm(pos, axis=1)
+    # the radial map carries the lattice onto the arcsine CDF (up to lattice discreteness)
+    d, _ = stats.kstest(r, lambda x: 1.0 - np.sqrt(1.0 - np.clip(x, 0, 1) ** 2))
+    assert d < 0.01
+
+
+def test_jitter_stays_inside_and_keeps_shape():
+    pos = synth.ngon(64)
+    out = synth.jitter_inside(pos, 1e-3, 5)
+    assert np.linalg.norm(out, axis=1).max() <= 1.0
+    assert np.abs(out - pos).max() < 1e-2
+
+
+def test_subdomains_and_csr():
+    pos = synth.lattice_disk(10000, 1)
+    subs = synth.subdomains(pos, 20, 200, 500, 2)
+    for s in subs:
+        assert 200 <= s.size <= 500
+        assert np.all(np.diff(s) > 0) and s[0] >= 0 and s[-1] < 10000
+    idx, off = synth.to_csr(subs)
+    assert off[0] == 0 and off[-1] == idx.size and idx.dtype == np.int32
+
+
+def test_instances():
+    pos, off = synth.instances(16, 100, 500, 3)
+    sizes = np.diff(off)
+    assert sizes.min() >= 100 and sizes.max() <= 500
+    assert pos.shape == (off[-1], 2)
+    np.testing.assert_array_equal(pos[off[2]:off[3]], synth.arcsine_disk(int(sizes[2]), 3 + 1 + 2))
