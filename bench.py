@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: Coulomb pair interactions per second at N = 100 000 (one adaptive-cycle step).
+
+One step is one pass of the whole hot path over one batch of synthetic input:
+  1. float64 local energies e_i of all N charges (Sec. II C step 1: N(N-1)
+     ordered pair interactions),
+  2. 256 subdomains (m ~ U{200..5000}, the m nearest charges to a centre)
+     relaxed together against all N for 200 mixed-precision projected
+     Barzilai-Borwein steps (Sec. II C step 4, Sec. II E: m(N-1) pair
+     interactions per subdomain per step),
+  3. sequential float64 pairwise accept/reject of the relaxed subdomains.
+The value is the ordered pair interactions of 1 and 2 divided by the whole
+step's time (the accept passes of 3 are timed but not counted).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank relaxes its own
+independently seeded configuration (weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 100_000
+N_SUB = 256
+M_LO, M_HI = 200, 5000
+RELAX_STEPS = 200
+METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
+UNIT = "pair-interactions/s"
+WORKLOAD = ("adaptive-cycle step at N=1e5: fp64 local energies of all charges + 256 subdomains "
+            "(m~U[200,5000], nearest charges to a centre) x 200 mixed BB steps against all N + fp64 "
+            "sequential accept; triangular-lattice background mapped to the arcsine density, 0.5% jitter, "
+            "charges stored in Hilbert-curve order")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    # a single small kernel case (used for profiler captures): no JSON bench line
+    ap.add_argument("--case", choices=["allpairs", "relax"], default=None)
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--n", type=int, default=20000)
+    ap.add_argument("--nsub", type=int, default=16)
+    ap.add_argument("--reps", type=int, default=3)
+    return ap.parse_args()
+
+
+def run_case(args):
+    """One small workload of one kernel family, timed with CUDA events (for profiler runs)."""
+    import torch
+
+    import synth
+    import paper_2609_24722_b300 as tc
+
+    dev = torch.device("cuda", 0)
+    if args.case == "allpairs":
+        pa = synth.arcsine_disk(args.n, 0)
+        p = torch.tensor(pa[synth.zorder(pa)], device=dev)
+        work = lambda: tc.grad(p, args.prec, with_energy=True)  # noqa: E731
+        pairs = args.n * (args.n - 1)
+    else:
+        pos = synth.lattice_disk(args.n, 0)
+        pos = pos[synth.zorder(pos)]
+        subs = synth.subdomains(pos, args.nsub, 200, 2000, 2)
+        idx, off = synth.to_csr(subs)
+        p0 = torch.tensor(pos, device=dev)
+        p = p0.clone()
+        it, of = torch.tensor(idx, device=dev), torch.tensor(off, device=dev)
+        eta = 1e-4 / args.n
+
+        def work():
+            p.copy_(p0)
+            return tc.relax_subdomains(p, it, of, precision=args.prec, optimizer="bb", n_steps=10, step0=eta,
+                                       alpha_min=0.0, alpha_max=10 * eta, accept=False)
+        pairs = 10 * sum(len(s) for s in subs) * (args.n - 1)
+    work()
+    ts = []
+    for _ in range(args.reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        work()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    tc.sync_status()
+    ms = min(ts)
+    print(json.dumps({"case": args.case, "prec": args.prec, "n": args.n, "ms": ms, "pairs_per_s": pairs / (ms / 1e3)}))
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(seed: int):
+    import synth
+
+    pos = synth.lattice_disk(N, seed)
+    # charges are identical: store the configuration along a Hilbert curve so
+    # nearby charges have nearby indices (compact row blocks and source tiles)
+    pos = pos[synth.zorder(pos)]
+    subs = synth.subdomains(pos, N_SUB, M_LO, M_HI, seed + 2)
+    idx, off = synth.to_csr(subs)
+    return pos, idx, off
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(pos, idx, off, seconds: float = 12.0) -> dict:
+    """The CPU oracle, as it stands, on a bounded sample: subdomain rows against all N."""
+    import numpy as np
+    import oracle
+
+    rows_all = idx[: off[min(N_SUB, len(off) - 1)]]
+    # size the sample from a short calibration run
+    t0 = time.perf_counter()
+    oracle.rows_grad(pos, rows_all[:50])
+    per_row = (time.perf_counter() - t0) / 50
+    n_rows = int(max(50, min(len(rows_all), seconds / max(per_row, 1e-9))))
+    rows = np.ascontiguousarray(rows_all[:n_rows])
+    t0 = time.perf_counter()
+    oracle.rows_grad(pos, rows)
+    dt = time.perf_counter() - t0
+    pairs = n_rows * (N - 1)
+    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"float64 gradient + energy rows of the first {n_rows} subdomain charges against all "
+                      f"{N} charges (tco_rows_grad, single thread, Neumaier sums), {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+
+    pos, idx, off = make_inputs(0)
+    per_step_rows = 3000
+    times = []
+    for k in range(args.warmup + args.steps):
+        rows = np.ascontiguousarray(idx[(k * per_step_rows) % (len(idx) - per_step_rows):][:per_step_rows])
+        t0 = time.perf_counter()
+        oracle.rows_grad(pos, rows)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = per_step_rows * (N - 1) / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "n_sub": N_SUB, "relax_steps": RELAX_STEPS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step_rows} subdomain rows x {N} charges per step (tco_rows_grad)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.case:
+        return run_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2609_24722_b300 as tc
+    from paper_2609_24722_b300 import build as tc_build
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    tc_build.build()
+
+    pos_np, idx_np, off_np = make_inputs(rank)
+    pos0 = torch.tensor(pos_np, device=dev)
+    pos = pos0.clone()
+    idx = torch.tensor(idx_np, device=dev)
+    off = torch.tensor(off_np, device=dev)
+    eta = 1e-4 / N
+    relax_kw = dict(precision="mixed", optimizer="bb", n_steps=RELAX_STEPS, step0=eta, alpha_min=0.0,
+                    alpha_max=10 * eta, accept=True, profile=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(p):
+        e, loc = tc.local_energy(p, "fp64")
+        r = tc.relax_subdomains(p, idx, off, **relax_kw)
+        return e, r
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        pos.copy_(pos0)
+        step(pos)
+    tc.sync_status()
+
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    ms, profs, accepted = [], [], []
+    clocks.start()
+    for _ in range(args.steps):
+        pos.copy_(pos0)
+        flush.zero_()
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        e, r = step(pos)
+        t1.record(stream)
+        barrier()
+        ms.append(t0.elapsed_time(t1))
+        profs.append(tc.relax_last_profile())
+        accepted.append(int((r.status == 1).sum().item()))
+    clk = clocks.stop()
+    tc.sync_status()
+    ms_step = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = t.item()
+    prof = profs[-1]
+    pairs_step = N * (N - 1) + RELAX_STEPS * prof["pass_pairs"]
+    value = world * pairs_step / (ms_step / 1e3)
+
+    # end to end through the public API: pinned host buffers in, results out, every step
+    pos_h = torch.tensor(pos_np).pin_memory()
+    idx_h = torch.tensor(idx_np).pin_memory()
+    off_h = torch.tensor(off_np).pin_memory()
+    out_h = torch.empty_like(pos_h).pin_memory()
+    res_h = torch.empty((N_SUB, 4), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(2):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        p_d = pos_h.to(dev, non_blocking=True)
+        i_d = idx_h.to(dev, non_blocking=True)
+        o_d = off_h.to(dev, non_blocking=True)
+        e_d, _ = tc.local_energy(p_d, "fp64")
+        r = tc.relax_subdomains(p_d, i_d, o_d, **{**relax_kw, "profile": False})
+        out_h.copy_(p_d, non_blocking=True)
+        res_h[:, 0].copy_(r.delta_e, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_step = statistics.mean(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = t.item()
+    h2d = pos_h.numel() * 8 + idx_h.numel() * 4 + off_h.numel() * 8
+    d2h = out_h.numel() * 8 + N_SUB * 8
+
+    # side by side: one full E+grad at N = 1e5, mixed and float64 (all-pairs kernel)
+    def time_allpairs(prec, reps):
+        p = pos0.clone()
+        tc.grad(p, prec, with_energy=True)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tc.grad(p, prec, with_energy=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    ms_mixed = time_allpairs("mixed", 5)
+    ms_f64 = time_allpairs("fp64", 3)
+    pipes = tc.probe_pipes()
+    tc.sync_status()
+
+    # roofline of the dominant kernel: the mixed relaxation pass (gradient only).
+    # Algorithmic work per ordered pair: 8 float32 FMA-pipe operations
+    # (dx, dy, r^2 as mul + fma, r^-3 as two muls, two gradient fmas) and 1 MUFU.RSQ.
+    pass_ms = prof["pass_ms"] / max(prof["n_pass"], 1)
+    achieved = prof["pass_pairs"] / (pass_ms / 1e3)
+    peak = min(pipes["ffma_per_s"] / 8.0, pipes["mufu_per_s"])
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_pass<mixed, grad> (relaxation pair pass)",
+                "peak_source": "measured: tc_probe_pipes FFMA lane-ops/s / 8 and MUFU.RSQ/s, this run",
+                "pipe_peaks": pipes}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(pos_np, idx_np, off_np)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulation (mixed); f64 energies/accept",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "n_sub": N_SUB, "m_range": [M_LO, M_HI],
+                   "relax_steps": RELAX_STEPS, "optimizer": "projected BB, step0 1e-4/N, alpha_max 1e-3/N",
+                   "accept": "fp64 pairwise, sequential", "pairs_per_step": pairs_step,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replica x{world}"},
+        "relax_time_s": ms_step / 1e3,
+        "breakdown_ms": {"relax_pass": prof["pass_ms"], "relax_update": prof["update_ms"],
+                         "relax_loop": prof["relax_ms"], "accept": prof["accept_ms"], "setup": prof["setup_ms"]},
+        "accepted_subdomains": accepted[-1],
+        "allpairs_n1e5": {"mixed_pairs_per_s": N * (N - 1) / (ms_mixed / 1e3), "mixed_ms": ms_mixed,
+                          "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64},
+        "e2e": {"value": world * pairs_step / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "gpu_launches": args.steps * (prof["launches"] + 3),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

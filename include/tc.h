@@ -1,0 +1,207 @@
+/*
+ * tc.h -- C ABI of libtc: Coulomb charges in the unit disk on one B300 GPU.
+ *
+ * The library computes, with hand-written CUDA kernels for sm_103a, the hot
+ * path of the adaptive subdomain method for the Thomson problem in a disk
+ * (Lavrov & Nikonov, "Lowest-known energy configuration of N = 100 000
+ * Coulomb charges in a disk"):
+ *   - the direct-sum energy of Eq. (hamiltonian), E = sum_{i<j} 1/|r_i - r_j|,
+ *     with the hard wall of Eq. (potential) (V = 0 for |r| <= R = 1),
+ *   - its analytic gradient and the local energies e_i of Sec. II C step 1,
+ *   - the subdomain objective E_sub of Sec. II D and the projected local
+ *     relaxation of many active sets against all N charges (Sec. II C step 4,
+ *     Sec. II E: n_act rows against the full configuration).
+ *
+ * Conventions for every call:
+ *   - Positions are interleaved (x, y) float64 pairs: pos[2i], pos[2i+1].
+ *   - Every array pointer is a DEVICE pointer owned by the caller, 16-byte
+ *     aligned for position/gradient arrays, 8-byte aligned otherwise.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  Argument errors are returned synchronously; errors
+ *     found on the device (coincident charges, non-finite values, charges
+ *     outside the disk, invalid index sets) are recorded in a per-device
+ *     status word that tc_sync_status() returns and clears.
+ *   - The library keeps one scratch workspace per (device, stream), grown on
+ *     demand with cudaMalloc and released by tc_shutdown().  The first call on
+ *     a stream with a given size allocates; later calls of that size or
+ *     smaller do not.
+ *   - Gradients are dE/dr (the force is -grad).
+ *   - n <= 1 gives E = 0 and zero gradients.
+ *   - Charges closer than about 1e-19 are reported as coincident.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object type as cudaStream_t, without requiring the CUDA headers. */
+typedef struct CUstream_st* tc_stream;
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_INVALID_ARG = 1,   /* bad size, null or misaligned pointer, bad index set */
+    TC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    TC_ERR_NONFINITE = 3,     /* coincident charges or NaN/Inf in the result */
+    TC_ERR_OUTSIDE_DISK = 4,  /* a charge with |r| > 1 + 1e-12 (Eq. potential) */
+    TC_ERR_TIMEOUT = 5,       /* a bounded device wait expired */
+    TC_ERR_NOT_CONVERGED = 6, /* reserved: relaxation did not reach its tolerance */
+    TC_ERR_NO_MEMORY = 7      /* workspace allocation failed */
+} tc_status;
+
+typedef enum {
+    TC_FP64 = 0,  /* every pair term and sum in float64 */
+    TC_MIXED = 1  /* pair terms in float32 from hi/lo-split positions, tile sums
+                     in float32, cross-tile sums double-float, rows combined in float64 */
+} tc_precision;
+
+/* Human-readable name of a status code (static storage). */
+const char* tc_status_string(tc_status s);
+
+/* Text of the last CUDA runtime failure that a call from this host thread
+ * reported as TC_ERR_CUDA: the failing step and CUDA's error name/string
+ * ("" if none).  Static thread-local storage, valid until the next call. */
+const char* tc_last_error(void);
+
+/* Waits for `stream`, then returns and clears the current device's status word. */
+tc_status tc_sync_status(tc_stream stream);
+
+/* Frees every workspace of every device this process used. */
+void tc_shutdown(void);
+
+/* Total energy, Eq. (hamiltonian):  E = sum_{i<j} 1/|r_i - r_j|.
+ *   pos      [2n]  positions (read)
+ *   n              number of charges, n >= 0
+ *   prec           TC_FP64 or TC_MIXED
+ *   energy   [1]   E (written)
+ *   local_e  [n]   nullable; e_i = 1/2 sum_{j != i} 1/|r_i - r_j|
+ *                  (Sec. II C step 1), so sum_i e_i = E
+ * Device errors: TC_ERR_NONFINITE, TC_ERR_OUTSIDE_DISK. */
+tc_status tc_energy(const double* pos, int64_t n, tc_precision prec, double* energy,
+                    double* local_e, tc_stream stream);
+
+/* Gradient of Eq. (hamiltonian):  grad_i = dE/dr_i = sum_{j != i} -(r_i - r_j)/|r_i - r_j|^3.
+ *   pos    [2n]  positions (read)
+ *   grad   [2n]  dE/dr (written, interleaved like pos)
+ *   energy [1]   nullable; E computed in the same pass
+ * Device errors: TC_ERR_NONFINITE, TC_ERR_OUTSIDE_DISK. */
+tc_status tc_grad(const double* pos, int64_t n, tc_precision prec, double* grad, double* energy,
+                  tc_stream stream);
+
+/* Energy change of moving each subdomain's active set, summed directly as pair
+ * differences in float64 (never as a difference of totals).  For subdomain s
+ * with active set A = idx[offsets[s] .. offsets[s+1]) and new positions
+ * a_k = new_active[2 offsets[s] + 2k ..]:
+ *   delta[s] = sum_{i in A, j not in A} (1/|a_i - p_j| - 1/|p_i - p_j|)
+ *            + sum_{i<k in A} (1/|a_i - a_k| - 1/|p_i - p_k|)
+ *            = E_sub(new) - E_sub(old)   (Sec. II D)
+ * Each subdomain is evaluated against `pos` independently.
+ *   pos        [2n]             configuration p (read)
+ *   idx        [offsets[n_sub]] active indices, strictly ascending within a subdomain
+ *   offsets    [n_sub + 1]      int64 CSR offsets, offsets[0] = 0, non-decreasing
+ *   new_active [2 offsets[n_sub]] new positions of the active charges
+ *   delta      [n_sub]          written
+ * Device errors: TC_ERR_INVALID_ARG (index set), TC_ERR_NONFINITE. */
+tc_status tc_subdomain_delta_energy(const double* pos, int64_t n, const int32_t* idx,
+                                    const int64_t* offsets, int32_t n_sub, const double* new_active,
+                                    double* delta, tc_stream stream);
+
+/* Hard wall of Eq. (potential) as a projection, in place:
+ *   r <- r min(1, radius/|r|);  a charge with flags[i] != 0 is pinned to the
+ *   unit circle (the boundary population of Sec. II B): r <- r/|r| (unchanged
+ *   at the origin).
+ *   pos   [2n] in/out;  radius > 0;  flags [n] nullable. */
+tc_status tc_project_disk(double* pos, int64_t n, double radius, const uint8_t* flags, tc_stream stream);
+
+typedef enum {
+    TC_OPT_GD = 0,    /* projected gradient descent x <- P(x - step0 g) */
+    TC_OPT_BB = 1,    /* projected descent with Barzilai-Borwein (s^T y / y^T y) steps */
+    TC_OPT_LBFGS = 2  /* L-BFGS on the smooth wall map x = radius sin|z| z/|z| (no projection) */
+} tc_optimizer;
+
+typedef struct {
+    int32_t precision;   /* tc_precision of the bulk steps */
+    int32_t optimizer;   /* tc_optimizer */
+    int32_t n_steps;     /* bulk steps per problem (>= 0) */
+    int32_t memory;      /* L-BFGS history pairs, 1..16 */
+    double step0;        /* GD step; BB first step; L-BFGS scale without history */
+    double alpha_min;    /* BB step clamp */
+    double alpha_max;
+    double maxstep;      /* L-BFGS: largest move of one charge in z per step */
+    double gtol;         /* a problem stops once its RMS stationarity < gtol (0: never) */
+    double radius;       /* wall radius for free charges (1 = the unit disk) */
+    int32_t polish_steps;/* float64 L-BFGS steps after the bulk phase (0: none) */
+    int32_t accept;      /* subdomain mode: 1 = sequential float64 accept/reject;
+                            instance mode: 1 = write back only if E drops */
+    double polish_gtol;  /* stopping tolerance of the float64 polish */
+    int32_t want_energy; /* 1: also report each problem's final float64 E_sub / E */
+    int32_t profile;     /* 1: launch the step loop directly (no CUDA graph) and time each
+                            launch with CUDA events (see tc_relax_last_profile) */
+} tc_relax_params;
+
+typedef struct {
+    double delta_e;  /* float64 pairwise energy change of the relaxed move */
+    double energy;   /* final float64 E_sub (subdomain) or E (instance), if requested */
+    double rms;      /* final RMS stationarity measure */
+    int32_t steps;   /* steps taken (bulk + polish) */
+    int32_t status;  /* 0 rejected, 1 accepted/written, 2 skipped (overlap) */
+} tc_subdomain_result;
+
+/* Relax many problems in one batched call (Sec. II C step 4; Sec. II E).
+ *
+ * Subdomain mode (idx != NULL): problem s moves the charges
+ * idx[offsets[s] .. offsets[s+1]) (strictly ascending, inside the world range)
+ * while every other charge of its world range stays at its value on entry;
+ * the objective is E_sub of Sec. II D.  Problems run concurrently and may
+ * overlap.  With accept = 1 they are then visited in order: a problem sharing
+ * a charge with an accepted one is skipped; otherwise its float64 pairwise
+ * energy change against the current configuration is computed and the move
+ * is applied iff it is negative.  With accept = 0 nothing is written to pos.
+ *
+ * Instance mode (idx == NULL): problem s is the independent configuration
+ * pos[world[2s] .. world[2s+1]), all of whose charges move.
+ *
+ *   pos     [2n]        in/out configuration
+ *   world   [2 n_sub]   int64 [begin, end) charge range per problem; nullable
+ *                       in subdomain mode (= [0, n)), required in instance mode
+ *   flags   [n]         nullable; nonzero = pinned to the unit circle
+ *   prm                 HOST pointer to the parameters
+ *   out     [n_sub]     DEVICE results
+ * Device errors: TC_ERR_INVALID_ARG (index set), TC_ERR_NONFINITE, TC_ERR_OUTSIDE_DISK. */
+tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
+                              int32_t n_sub, const int64_t* world, const uint8_t* flags,
+                              const tc_relax_params* prm, tc_subdomain_result* out, tc_stream stream);
+
+/* Launch timings of the calling thread's last tc_relax_subdomains call made
+ * with prm->profile = 1 (measurement utility; the paper has no counterpart).
+ * Times are CUDA-event intervals on the launching stream, in milliseconds. */
+typedef struct {
+    double pass_ms;     /* sum over the relaxation pair passes (bulk + polish) */
+    double update_ms;   /* sum over the optimiser update launches */
+    double relax_ms;    /* whole step loop(s) */
+    double accept_ms;   /* energy-change passes and accept/apply launches */
+    double setup_ms;    /* set-up launches before the first step */
+    int32_t n_pass;     /* relaxation pair-pass launches */
+    int32_t launches;   /* every kernel launch of the call */
+    int64_t pass_pairs; /* ordered pair interactions of one bulk pass over all problems */
+} tc_relax_profile;
+
+tc_status tc_relax_last_profile(tc_relax_profile* out);
+
+/* Measurement utility (the paper has no counterpart): achieved throughput of
+ * the instruction pipes that bound the pair kernels, measured with long
+ * chains of independent instructions on every SM of the current device.
+ *   rates [3] HOST array, written: float32 FFMA lane operations/s,
+ *             float64 DFMA operations/s, MUFU.RSQ operations/s.
+ * Synchronous; allocates and frees a 64-byte scratch buffer. */
+tc_status tc_probe_pipes(double* rates, tc_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

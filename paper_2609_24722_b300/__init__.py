@@ -1,0 +1,192 @@
+"""Coulomb charges in the unit disk on one B300: Python binding of libtc.
+
+Thin wrappers over the C ABI in include/tc.h.  Tensors are CUDA float64
+(positions (n, 2)), int32 index sets and int64 offsets; every step of the
+computation runs in libtc's CUDA kernels on the current torch stream.  There is
+no CPU path: on a machine without a GPU or without libtc.so every call raises.
+
+    energy(pos)            E = sum_{i<j} 1/r_ij            (Eq. hamiltonian)
+    grad(pos)              dE/dr                            (its analytic gradient)
+    local_energy(pos)      e_i = 1/2 sum_{j != i} 1/r_ij    (Sec. II C step 1)
+    project_disk(pos)      hard wall of Eq. (potential) as a projection
+    subdomain_delta_energy pairwise E_sub(new) - E_sub(old) (Sec. II D)
+    relax_subdomains       batched local relaxation of subdomains / instances
+    coulomb_energy         torch.autograd.Function: energy forward, gradient backward
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+from ._lib import TCError, RelaxParams
+
+__all__ = [
+    "energy", "grad", "local_energy", "project_disk", "subdomain_delta_energy", "relax_subdomains",
+    "coulomb_energy", "CoulombEnergy", "sync_status", "probe_pipes", "relax_last_profile", "TCError", "RelaxParams",
+    "library_path",
+]
+
+_PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED}
+_OPT = {"gd": L.TC_OPT_GD, "bb": L.TC_OPT_BB, "lbfgs": L.TC_OPT_LBFGS}
+
+
+def library_path() -> str:
+    return L.LIB_PATH
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _p(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _pos(t: torch.Tensor, name: str = "pos") -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if t.dim() != 2 or t.shape[1] != 2 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (n, 2) tensor")
+    return t
+
+
+def _prec(p) -> int:
+    if isinstance(p, int):
+        return p
+    return _PREC[p]
+
+
+def sync_status() -> None:
+    """Wait for the current stream and raise if a kernel recorded a device error."""
+    L.check(L.lib().tc_sync_status(_stream()), "device status")
+
+
+def energy(pos: torch.Tensor, precision="fp64") -> torch.Tensor:
+    """Total energy E (0-d CUDA float64 tensor)."""
+    _pos(pos)
+    out = torch.empty((), dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_energy(_p(pos), pos.shape[0], _prec(precision), _p(out), None, _stream()), "tc_energy")
+    return out
+
+
+def local_energy(pos: torch.Tensor, precision="fp64") -> tuple[torch.Tensor, torch.Tensor]:
+    """(E, e) with e_i = 1/2 sum_{j != i} 1/r_ij."""
+    _pos(pos)
+    out = torch.empty((), dtype=torch.float64, device=pos.device)
+    e = torch.empty(pos.shape[0], dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_energy(_p(pos), pos.shape[0], _prec(precision), _p(out), _p(e), _stream()), "tc_energy")
+    return out, e
+
+
+def grad(pos: torch.Tensor, precision="fp64", with_energy: bool = False):
+    """dE/dr (n, 2); with with_energy=True also E from the same pass."""
+    _pos(pos)
+    g = torch.empty_like(pos)
+    e = torch.empty((), dtype=torch.float64, device=pos.device) if with_energy else None
+    L.check(L.lib().tc_grad(_p(pos), pos.shape[0], _prec(precision), _p(g), _p(e), _stream()), "tc_grad")
+    return (g, e) if with_energy else g
+
+
+def project_disk(pos: torch.Tensor, radius: float = 1.0, flags: torch.Tensor | None = None) -> torch.Tensor:
+    """In place: r <- r min(1, radius/|r|); charges with flags != 0 go to the unit circle."""
+    _pos(pos)
+    if flags is not None and (flags.dtype != torch.uint8 or not flags.is_cuda or flags.numel() != pos.shape[0]):
+        raise TypeError("flags must be a CUDA uint8 tensor with one entry per charge")
+    L.check(L.lib().tc_project_disk(_p(pos), pos.shape[0], float(radius), _p(flags), _stream()), "tc_project_disk")
+    return pos
+
+
+def _csr(idx, offsets):
+    if idx.dtype != torch.int32 or not idx.is_cuda or not idx.is_contiguous():
+        raise TypeError("idx must be a contiguous CUDA int32 tensor")
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise TypeError("offsets must be a contiguous CUDA int64 tensor")
+
+
+def subdomain_delta_energy(pos, idx, offsets, new_active) -> torch.Tensor:
+    """Pairwise float64 energy change of moving each subdomain's charges to new_active."""
+    _pos(pos)
+    _csr(idx, offsets)
+    _pos(new_active, "new_active")
+    n_sub = offsets.numel() - 1
+    out = torch.empty(max(n_sub, 0), dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_subdomain_delta_energy(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub,
+                                              _p(new_active), _p(out), _stream()), "tc_subdomain_delta_energy")
+    return out
+
+
+@dataclass
+class RelaxResult:
+    delta_e: torch.Tensor   # float64 pairwise energy change (NaN when not computed)
+    energy: torch.Tensor    # float64 final E_sub / E (NaN when not requested)
+    rms: torch.Tensor       # final RMS stationarity
+    steps: torch.Tensor     # int32 steps taken
+    status: torch.Tensor    # int32: 0 rejected, 1 accepted/written, 2 skipped
+
+
+def relax_subdomains(pos, idx=None, offsets=None, world=None, flags=None, *, precision="mixed", optimizer="bb",
+                     n_steps=200, memory=8, step0=1e-9, alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0,
+                     radius=1.0, polish_steps=0, polish_gtol=0.0, accept=True, want_energy=False,
+                     profile=False) -> RelaxResult:
+    """Relax subdomains (idx/offsets given) or independent instances (idx None, world given)."""
+    _pos(pos)
+    if idx is not None:
+        _csr(idx, offsets)
+        n_sub = offsets.numel() - 1
+    else:
+        if world is None:
+            raise ValueError("instance mode needs world ranges")
+        n_sub = world.shape[0]
+    if world is not None and (world.dtype != torch.int64 or not world.is_cuda or not world.is_contiguous()):
+        raise TypeError("world must be a contiguous CUDA int64 tensor of shape (n_sub, 2)")
+    prm = RelaxParams(precision=_prec(precision), optimizer=_OPT[optimizer] if isinstance(optimizer, str) else optimizer,
+                      n_steps=int(n_steps), memory=int(memory), step0=float(step0), alpha_min=float(alpha_min),
+                      alpha_max=float(alpha_max), maxstep=float(maxstep), gtol=float(gtol), radius=float(radius),
+                      polish_steps=int(polish_steps), accept=int(bool(accept)), polish_gtol=float(polish_gtol),
+                      want_energy=int(bool(want_energy)), profile=int(bool(profile)))
+    raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_relax_subdomains(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub, _p(world), _p(flags),
+                                        C.byref(prm), _p(raw), _stream()), "tc_relax_subdomains")
+    raw = raw[:n_sub]
+    # the two int32 fields share the fourth 8-byte column of each 32-byte record
+    ints = raw.view(torch.int32).view(n_sub, 8)[:, 6:8]
+    return RelaxResult(raw[:, 0], raw[:, 1], raw[:, 2], ints[:, 0].clone(), ints[:, 1].clone())
+
+
+def relax_last_profile() -> dict:
+    """Launch timings of this thread's last relax_subdomains(..., profile=True) call."""
+    prof = L.RelaxProfile()
+    L.check(L.lib().tc_relax_last_profile(C.byref(prof)), "tc_relax_last_profile")
+    return {f: getattr(prof, f) for f, _ in L.RelaxProfile._fields_}
+
+
+def probe_pipes() -> dict:
+    """Measured FFMA lane-ops/s, DFMA ops/s and MUFU.RSQ ops/s of the current device."""
+    rates = (C.c_double * 3)()
+    L.check(L.lib().tc_probe_pipes(C.cast(rates, C.c_void_p), _stream()), "tc_probe_pipes")
+    return {"ffma_per_s": rates[0], "dfma_per_s": rates[1], "mufu_per_s": rates[2]}
+
+
+class CoulombEnergy(torch.autograd.Function):
+    """E(pos) forward; backward recomputes dE/dr with tc_grad (no N x N storage)."""
+
+    @staticmethod
+    def forward(ctx, pos, precision="fp64"):
+        ctx.save_for_backward(pos)
+        ctx.precision = precision
+        return energy(pos.contiguous(), precision)
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(ctx, gout):
+        (pos,) = ctx.saved_tensors
+        g = grad(pos.contiguous(), ctx.precision)
+        return gout * g, None
+
+
+def coulomb_energy(pos: torch.Tensor, precision="fp64") -> torch.Tensor:
+    return CoulombEnergy.apply(pos, precision)

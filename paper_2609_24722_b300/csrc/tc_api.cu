@@ -1,0 +1,181 @@
+// tc_api.cu -- status codes, per-device status word, per-stream workspace.
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "tc_internal.h"
+
+namespace tc {
+namespace {
+
+struct Block {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Block> g_ws;
+std::map<int, int*> g_status;
+std::map<int, cudaStream_t> g_cap;
+
+thread_local std::string g_last_error;
+
+}  // namespace
+
+tc_status cuda_fail(cudaError_t e, const char* where)
+{
+    if (e == cudaSuccess) return TC_OK;
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    g_last_error = buf;
+    return TC_ERR_CUDA;
+}
+
+void* workspace(cudaStream_t s, size_t bytes, tc_status* err)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        *err = TC_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    Block& b = g_ws[{dev, s}];
+    if (b.bytes >= bytes && b.ptr) return b.ptr;
+    size_t want = align_up(bytes + bytes / 4, size_t(2) << 20);
+    if (b.ptr) {
+        // no kernel of this stream may still use the old block
+        if (cudaStreamSynchronize(s) != cudaSuccess || cudaFree(b.ptr) != cudaSuccess) {
+            *err = TC_ERR_CUDA;
+            return nullptr;
+        }
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        *err = TC_ERR_NO_MEMORY;
+        return nullptr;
+    }
+    // counters used by the last-block reductions must start at zero
+    if (cudaMemsetAsync(p, 0, want, s) != cudaSuccess) {
+        cudaFree(p);
+        *err = TC_ERR_CUDA;
+        return nullptr;
+    }
+    b.ptr = p;
+    b.bytes = want;
+    return p;
+}
+
+int* device_status(tc_status* err)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        *err = TC_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_status.find(dev);
+    if (it != g_status.end()) return it->second;
+    int* p = nullptr;
+    if (cudaMalloc(&p, 256) != cudaSuccess || cudaMemset(p, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        *err = TC_ERR_NO_MEMORY;
+        return nullptr;
+    }
+    g_status[dev] = p;
+    return p;
+}
+
+cudaStream_t capture_stream(tc_status* err)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        *err = TC_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cap.find(dev);
+    if (it != g_cap.end()) return it->second;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        *err = TC_ERR_CUDA;
+        return nullptr;
+    }
+    g_cap[dev] = cs;
+    return cs;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace tc
+
+extern "C" {
+
+const char* tc_status_string(tc_status s)
+{
+    switch (s) {
+        case TC_OK: return "ok";
+        case TC_ERR_INVALID_ARG: return "invalid argument";
+        case TC_ERR_CUDA: return "CUDA runtime error";
+        case TC_ERR_NONFINITE: return "non-finite result (coincident charges or NaN)";
+        case TC_ERR_OUTSIDE_DISK: return "charge outside the disk";
+        case TC_ERR_TIMEOUT: return "bounded device wait expired";
+        case TC_ERR_NOT_CONVERGED: return "not converged";
+        case TC_ERR_NO_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char* tc_last_error(void)
+{
+    return tc::g_last_error.c_str();
+}
+
+tc_status tc_sync_status(tc_stream stream)
+{
+    tc_status err = TC_OK;
+    int* st = tc::device_status(&err);
+    if (!st) return err;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaError_t e_ = cudaStreamSynchronize(s); e_ != cudaSuccess) return tc::cuda_fail(e_, "cudaStreamSynchronize");
+    int h = 0;
+    if (cudaError_t e_ = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost); e_ != cudaSuccess) return tc::cuda_fail(e_, "cudaMemcpy");
+    if (h != 0 && cudaMemset(st, 0, sizeof(int)) != cudaSuccess) return TC_ERR_CUDA;
+    return static_cast<tc_status>(h);
+}
+
+void tc_shutdown(void)
+{
+    std::lock_guard<std::mutex> lk(tc::g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : tc::g_ws) {
+        cudaSetDevice(kv.first.first);
+        cudaStreamSynchronize(kv.first.second);
+        cudaFree(kv.second.ptr);
+    }
+    tc::g_ws.clear();
+    for (auto& kv : tc::g_status) {
+        cudaSetDevice(kv.first);
+        cudaFree(kv.second);
+    }
+    tc::g_status.clear();
+    for (auto& kv : tc::g_cap) {
+        cudaSetDevice(kv.first);
+        cudaStreamDestroy(kv.second);
+    }
+    tc::g_cap.clear();
+    cudaSetDevice(cur);
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// tc_device.cuh -- device arithmetic and the generic pair pass of libtc.
+//
+// Everything the kernels compute is a sum over (target row, source charge)
+// pairs of the 1/r Coulomb interaction of Eq. (hamiltonian):
+//     e-term  1/|r_i - r_j|,   gradient term  -(r_i - r_j)/|r_i - r_j|^3,
+// or, for the pairwise energy change of Sec. II D, the difference of two such
+// e-terms.  Rows are the moving charges of a problem; sources are tiles of
+// either the fixed configuration (the "snapshot", with the problem's own
+// charges masked out) or the problem's own moving charges.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tc {
+
+// Device status codes (same numbering as tc_status).
+enum : int { ST_OK = 0, ST_INVALID = 1, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_TIMEOUT = 5 };
+
+// A masked-out or padding source sits this far away: its 1/r term is below
+// 1e-30 (float64) or 1e-18 (float32) and its gradient term underflows, so it
+// vanishes below one rounding of any real row sum.
+constexpr double kFar64 = 1.0e30;
+constexpr float kFar32 = 1.0e18f;
+// Rows past the end of a problem sit at the opposite far corner, so they
+// never coincide with a far source.
+constexpr double kFarRow64 = -1.0e30;
+constexpr float kFarRow32 = -1.0e18f;
+
+// Slack above the wall radius that still counts as inside (Eq. potential).
+constexpr double kWallSlack = 1e-12;
+
+__device__ __forceinline__ void set_status(int* st, int code)
+{
+    if (st) atomicCAS(st, 0, code);
+}
+
+// One MUFU.RSQ: approximate 1/sqrt(x) in float32 (denormal inputs flush to 0).
+__device__ __forceinline__ float rsqrt_mufu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// float64 1/sqrt(r2): a float32 seed y0, then one correction step of the
+// binomial series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3) with
+// e = 1 - r2 y0^2.  With |e| < 2^-21 the truncation is below 2^-63, so the
+// result is within a few rounding errors of the correctly rounded value.
+// r2 = 0 gives NaN (coincident charges are caught by the finiteness checks).
+__device__ __forceinline__ double rsqrt64(double r2)
+{
+    double y0 = (double)rsqrt_mufu((float)r2);
+    double t = r2 * y0;
+    double e = fma(-t, y0, 1.0);
+    double p = fma(0.375, e, 0.5);
+    double q = e * p;
+    return fma(y0, q, y0);
+}
+
+// Error-free transformation of a float32 sum (Knuth's TwoSum): hi + v is
+// split into its rounded value and the exact rounding error, which is kept in
+// lo.  Used to carry float32 tile sums across tiles without float64 work.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v)
+{
+    float s = hi + v;
+    float bp = s - hi;
+    float err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+}
+
+// Same transformation in float64, used for the energy row sums.
+__device__ __forceinline__ void dd_add(double& hi, double& lo, double v)
+{
+    double s = hi + v;
+    double bp = s - hi;
+    double err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+}
+
+// hi/lo split of a float64 coordinate: hi = rn(x), lo = rn(x - hi).
+__device__ __forceinline__ float4 split4(double x, double y)
+{
+    float xh = (float)x, yh = (float)y;
+    return make_float4(xh, yh, (float)(x - (double)xh), (float)(y - (double)yh));
+}
+
+// ------------------------------------------------------------ stream-K ---
+// The pass work is a list of W equal units (one row block x one source tile),
+// cut into G contiguous ranges [b_k, b_{k+1}), b_k = floor(W k / G), one per
+// persistent CTA (the stream-K decomposition of Osama et al., PPoPP 2023).
+// owner(u) is the CTA whose range holds unit u: the largest k with
+// floor(W k / G) <= u, i.e. k = ceil(G (u + 1) / W) - 1.
+__host__ __device__ __forceinline__ int64_t sk_begin(int64_t W, int64_t G, int64_t k)
+{
+    return (W * k) / G;
+}
+
+__host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t W, int64_t G)
+{
+    return (G * (u + 1) + W - 1) / W - 1;
+}
+
+// One problem of a pass: rows [row_base, row_base + m) of the row arrays move;
+// sources are the snapshot range [snap_b, snap_e) of the configuration (with
+// the problem's own charges masked by mask words [mask_off, ...)) followed by
+// the problem's own rows.
+struct Prob {
+    int64_t row_base;
+    int64_t snap_b, snap_e;
+    int64_t unit_off;   // first pass unit of this problem
+    int64_t mask_off;   // first mask word, -1 without a mask
+    int32_t m;          // rows
+    int32_t n_rb;       // row blocks
+    int32_t n_t_snap;   // snapshot tiles
+    int32_t n_t_priv;   // own-row tiles
+};
+
+__device__ __forceinline__ int find_prob(const Prob* __restrict__ P, int S, int64_t u)
+{
+    // largest s with P[s].unit_off <= u (problems are ordered by unit_off)
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P[mid].unit_off <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// (x_old, y_old, x_new, y_new) of one moving charge, 32-byte aligned.
+struct alignas(32) d4 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ d4 make_d4(double x, double y, double z, double w)
+{
+    d4 r;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+    r.w = w;
+    return r;
+}
+
+// Pass flavours.
+enum PassKind { PASS_MIXED = 0, PASS_F64 = 1, PASS_DELTA = 2 };
+
+template <int KIND> struct SrcT;
+template <> struct SrcT<PASS_MIXED> { using type = float4; };   // (x_hi, y_hi, x_lo, y_lo)
+template <> struct SrcT<PASS_F64> { using type = double2; };    // (x, y)
+template <> struct SrcT<PASS_DELTA> { using type = d4; };  // (x_old, y_old, x_new, y_new)
+
+// Arguments of one pass launch.
+struct PassArgs {
+    const Prob* prob;   // device table of S problems; nullptr: the single problem below
+    Prob single;
+    int S;              // problems
+    int64_t W;          // total units
+    int64_t M;          // total rows (row arrays and partial-slot stride)
+    const void* rows;   // row positions: float4 split (mixed), double2 (f64), d4 old/new (delta)
+    const void* snap;   // snapshot: float4 split (mixed), double2 (f64, delta)
+    const uint32_t* mask;
+    const int* active;  // nullable; problems with active[s] == 0 are skipped
+    double* part_e;     // [slots x M] row partial energies (or energy changes)
+    double2* part_g;    // [slots x M] row partial gradients (nullable)
+};
+
+}  // namespace tc

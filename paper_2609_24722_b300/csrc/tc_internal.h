@@ -1,0 +1,54 @@
+// tc_internal.h -- host-side helpers shared by the libtc translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+// Per-(device, stream) scratch workspace.  Grows with cudaMalloc (after a
+// stream synchronisation, so no in-flight kernel uses the old block) and is
+// freed by tc_shutdown().  Returns nullptr and sets *err on failure.
+void* workspace(cudaStream_t s, size_t bytes, tc_status* err);
+
+// Per-device status word (device int), allocated on first use.
+int* device_status(tc_status* err);
+
+// Per-device private non-blocking stream used only to capture CUDA graphs
+// (the legacy default stream cannot be captured).
+cudaStream_t capture_stream(tc_status* err);
+
+// SM count and current device.
+int sm_count();
+
+// Record a failed CUDA runtime call (name and error text, per host thread)
+// for tc_last_error() and return TC_ERR_CUDA; TC_OK for cudaSuccess.
+tc_status cuda_fail(cudaError_t e, const char* where);
+
+inline tc_status cuda_status(cudaError_t e, const char* where = "CUDA call") { return cuda_fail(e, where); }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The first kCounterBytes of every workspace hold zero-initialised counters
+// for last-block reductions (each user resets its counter to zero); the rest
+// is carved per call.
+constexpr size_t kCounterBytes = 256;
+
+// Bump allocator over a workspace block: take<T>(n) returns the next 256-byte
+// aligned region of n elements, after the counter area.
+struct Carver {
+    char* base = nullptr;
+    size_t off = kCounterBytes;
+    template <class T> T* take(size_t count)
+    {
+        off = align_up(off, 256);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace tc

@@ -1,0 +1,283 @@
+// tc_pass.cuh -- the generic pair pass: persistent CTAs, stream-K unit split,
+// source tiles staged in shared memory, per-row partial sums out.
+//
+// Unit = (one row block of RB = THREADS*R moving charges) x (one tile of
+// T = THREADS sources).  A CTA walks its contiguous unit range; every time it
+// leaves a row block it writes that block's partial row sums to the slot
+// (its CTA index minus the index of the first CTA touching the block), so the
+// reducer can add the slots of a row in a fixed order (deterministic).
+#pragma once
+
+#include "tc_device.cuh"
+
+namespace tc {
+
+// Rows of one thread and their accumulators, per pass flavour.
+template <int KIND, int R> struct RowState;
+
+// ---- mixed: float32 pair terms from hi/lo-split positions -------------------
+template <int R> struct RowState<PASS_MIXED, R> {
+    float xh[R], yh[R], xl[R], yl[R];
+    float eh[R], el[R], gxh[R], gxl[R], gyh[R], gyl[R];
+
+    __device__ void load(const float4* rows, int64_t base, int64_t rl0, int stride, int m)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t rl = rl0 + (int64_t)r * stride;
+            float4 q = (rl < m) ? rows[base + rl] : make_float4(kFarRow32, kFarRow32, 0.f, 0.f);
+            xh[r] = q.x; yh[r] = q.y; xl[r] = q.z; yl[r] = q.w;
+            eh[r] = el[r] = gxh[r] = gxl[r] = gyh[r] = gyl[r] = 0.f;
+        }
+    }
+
+    // One tile: s[0..T) against the R rows; jself[r] is the tile position of
+    // row r's own charge (only checked when SELF).
+    template <int T, bool SELF, bool WANT_E, bool WANT_G>
+    __device__ __forceinline__ void tile(const float4* __restrict__ s, const int (&jself)[R], float escale)
+    {
+        float et[R], gxt[R], gyt[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) et[r] = gxt[r] = gyt[r] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < T; ++j) {
+            const float4 q = s[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float dx = (xh[r] - q.x) + (xl[r] - q.z);
+                float dy = (yh[r] - q.y) + (yl[r] - q.w);
+                float r2 = fmaf(dx, dx, dy * dy);
+                float inv = rsqrt_mufu(r2);
+                if (SELF) inv = (j == jself[r]) ? 0.f : inv;
+                if (WANT_E) et[r] += inv;
+                if (WANT_G) {
+                    float inv3 = inv * inv * inv;
+                    gxt[r] = fmaf(-dx, inv3, gxt[r]);
+                    gyt[r] = fmaf(-dy, inv3, gyt[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (WANT_E) df_add(eh[r], el[r], et[r] * escale);
+            if (WANT_G) {
+                df_add(gxh[r], gxl[r], gxt[r]);
+                df_add(gyh[r], gyl[r], gyt[r]);
+            }
+        }
+    }
+
+    __device__ double e(int r) const { return (double)eh[r] + (double)el[r]; }
+    __device__ double2 g(int r) const
+    {
+        return make_double2((double)gxh[r] + (double)gxl[r], (double)gyh[r] + (double)gyl[r]);
+    }
+};
+
+// ---- float64 pair terms --------------------------------------------------------
+template <int R> struct RowState<PASS_F64, R> {
+    double x[R], y[R];
+    double eh[R], el[R], gx[R], gy[R];
+
+    __device__ void load(const double2* rows, int64_t base, int64_t rl0, int stride, int m)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t rl = rl0 + (int64_t)r * stride;
+            double2 q = (rl < m) ? rows[base + rl] : make_double2(kFarRow64, kFarRow64);
+            x[r] = q.x; y[r] = q.y;
+            eh[r] = el[r] = gx[r] = gy[r] = 0.0;
+        }
+    }
+
+    template <int T, bool SELF, bool WANT_E, bool WANT_G>
+    __device__ __forceinline__ void tile(const double2* __restrict__ s, const int (&jself)[R], double escale)
+    {
+        double et[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) et[r] = 0.0;
+#pragma unroll 2
+        for (int j = 0; j < T; ++j) {
+            const double2 q = s[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double dx = x[r] - q.x;
+                double dy = y[r] - q.y;
+                double r2 = fma(dx, dx, dy * dy);
+                double inv = rsqrt64(r2);
+                if (SELF) inv = (j == jself[r]) ? 0.0 : inv;
+                if (WANT_E) et[r] += inv;
+                if (WANT_G) {
+                    double inv3 = inv * inv * inv;
+                    gx[r] = fma(-dx, inv3, gx[r]);
+                    gy[r] = fma(-dy, inv3, gy[r]);
+                }
+            }
+        }
+        if (WANT_E) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) dd_add(eh[r], el[r], et[r] * escale);
+        }
+    }
+
+    __device__ double e(int r) const { return eh[r] + el[r]; }
+    __device__ double2 g(int r) const { return make_double2(gx[r], gy[r]); }
+};
+
+// ---- float64 pairwise energy change: rows and own-row sources carry (old, new) -----
+template <int R> struct RowState<PASS_DELTA, R> {
+    double ox[R], oy[R], nx[R], ny[R];
+    double dh[R], dl[R];
+
+    __device__ void load(const d4* rows, int64_t base, int64_t rl0, int stride, int m)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t rl = rl0 + (int64_t)r * stride;
+            d4 q = (rl < m) ? rows[base + rl] : make_d4(kFarRow64, kFarRow64, kFarRow64, kFarRow64);
+            ox[r] = q.x; oy[r] = q.y; nx[r] = q.z; ny[r] = q.w;
+            dh[r] = dl[r] = 0.0;
+        }
+    }
+
+    // OWN = false: snapshot sources (x, y in .x, .y): term 1/|new - c| - 1/|old - c|.
+    // OWN = true: own rows (old, new): term 1/|new - new'| - 1/|old - old'|.
+    template <int T, bool SELF, bool OWN>
+    __device__ __forceinline__ void tile(const d4* __restrict__ s, const int (&jself)[R], double escale)
+    {
+        double dt[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) dt[r] = 0.0;
+#pragma unroll 2
+        for (int j = 0; j < T; ++j) {
+            const d4 q = s[j];
+            const double sx1 = OWN ? q.z : q.x, sy1 = OWN ? q.w : q.y;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double ax = nx[r] - sx1, ay = ny[r] - sy1;
+                double bx = ox[r] - q.x, by = oy[r] - q.y;
+                double inv1 = rsqrt64(fma(ax, ax, ay * ay));
+                double inv0 = rsqrt64(fma(bx, bx, by * by));
+                double d = inv1 - inv0;
+                if (SELF) d = (j == jself[r]) ? 0.0 : d;
+                dt[r] += d;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) dd_add(dh[r], dl[r], dt[r] * escale);
+    }
+
+    __device__ double e(int r) const { return dh[r] + dl[r]; }
+};
+
+// Source entry t*T + tid of a problem's tile list, with masking and padding.
+template <int KIND, int T>
+__device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a, const Prob& p, int t, int tid)
+{
+    using src_t = typename SrcT<KIND>::type;
+    if (t < p.n_t_snap) {
+        int64_t j = (int64_t)t * T + tid;
+        bool ok = j < p.snap_e - p.snap_b;
+        if (ok && p.mask_off >= 0) {
+            uint32_t w = a.mask[p.mask_off + (j >> 5)];
+            ok = ((w >> (j & 31)) & 1u) == 0u;
+        }
+        if constexpr (KIND == PASS_MIXED) {
+            return ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
+        } else if constexpr (KIND == PASS_F64) {
+            return ok ? static_cast<const double2*>(a.snap)[p.snap_b + j] : make_double2(kFar64, kFar64);
+        } else {
+            double2 c = ok ? static_cast<const double2*>(a.snap)[p.snap_b + j] : make_double2(kFar64, kFar64);
+            return make_d4(c.x, c.y, c.x, c.y);
+        }
+    } else {
+        int64_t j = (int64_t)(t - p.n_t_snap) * T + tid;
+        bool ok = j < p.m;
+        if constexpr (KIND == PASS_MIXED) {
+            return ok ? static_cast<const float4*>(a.rows)[p.row_base + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
+        } else if constexpr (KIND == PASS_F64) {
+            return ok ? static_cast<const double2*>(a.rows)[p.row_base + j] : make_double2(kFar64, kFar64);
+        } else {
+            return ok ? static_cast<const d4*>(a.rows)[p.row_base + j]
+                      : make_d4(kFar64, kFar64, kFar64, kFar64);
+        }
+    }
+}
+
+// The pass.  Grid: persistent CTAs (any count); each takes units
+// [u_base + b_k, u_base + b_{k+1}) of the W units starting at u_base.
+// Row partials go to part_e/part_g[slot * M + row - row_sub].
+template <int KIND, int R, int THREADS, bool WANT_E, bool WANT_G>
+__global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, int64_t row_sub)
+{
+    constexpr int T = THREADS;
+    constexpr int RB = THREADS * R;
+    using src_t = typename SrcT<KIND>::type;  // rows use the same entry type as sources
+    __shared__ src_t tile[2][T];
+
+    const int tid = threadIdx.x;
+    const int64_t G = gridDim.x;
+    const int64_t k = blockIdx.x;
+    int64_t u = sk_begin(a.W, G, k);
+    const int64_t u_end = sk_begin(a.W, G, k + 1);
+
+    RowState<KIND, R> rs;
+    while (u < u_end) {
+        const int s = a.prob ? find_prob(a.prob, a.S, u_base + u) : 0;
+        const Prob p = a.prob ? a.prob[s] : a.single;
+        const int n_t = p.n_t_snap + p.n_t_priv;
+        const int64_t local = u_base + u - p.unit_off;
+        const int rb = (int)(local / n_t);
+        const int t0 = (int)(local % n_t);
+        const int t1 = (int)min((int64_t)n_t, (int64_t)t0 + (u_end - u));
+        const bool act = (a.active == nullptr) || (a.active[s] != 0);
+        if (act) {
+            const int64_t rl0 = (int64_t)rb * RB + tid;
+            rs.load(static_cast<const src_t*>(a.rows), p.row_base, rl0, THREADS, p.m);
+            src_t pre = load_src<KIND, T>(a, p, t0, tid);
+            tile[0][tid] = pre;
+            __syncthreads();
+            for (int t = t0; t < t1; ++t) {
+                const int buf = (t - t0) & 1;
+                if (t + 1 < t1) pre = load_src<KIND, T>(a, p, t + 1, tid);
+                const bool own = t >= p.n_t_snap;
+                const int tp = t - p.n_t_snap;
+                const bool self = own && (rb * RB < tp * T + T) && (tp * T < rb * RB + RB);
+                int jself[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) jself[r] = (int)(rl0 + r * THREADS) - tp * T;
+                const double sc = own ? 0.5 : 1.0;
+                if constexpr (KIND == PASS_DELTA) {
+                    if (!own)
+                        rs.template tile<T, false, false>(tile[buf], jself, sc);
+                    else if (self)
+                        rs.template tile<T, true, true>(tile[buf], jself, sc);
+                    else
+                        rs.template tile<T, false, true>(tile[buf], jself, sc);
+                } else {
+                    if (self)
+                        rs.template tile<T, true, WANT_E, WANT_G>(tile[buf], jself, (float)sc);
+                    else
+                        rs.template tile<T, false, WANT_E, WANT_G>(tile[buf], jself, (float)sc);
+                }
+                if (t + 1 < t1) tile[buf ^ 1][tid] = pre;
+                __syncthreads();
+            }
+            const int64_t slot = k - sk_owner(p.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int64_t rl = rl0 + (int64_t)r * THREADS;
+                if (rl < p.m) {
+                    const int64_t o = slot * a.M + p.row_base + rl - row_sub;
+                    if (WANT_E || KIND == PASS_DELTA) a.part_e[o] = rs.e(r);
+                    if constexpr (KIND != PASS_DELTA) {
+                        if (WANT_G) a.part_g[o] = rs.g(r);
+                    }
+                }
+            }
+        }
+        u += t1 - t0;
+    }
+}
+
+}  // namespace tc

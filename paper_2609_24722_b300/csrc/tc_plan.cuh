@@ -1,0 +1,154 @@
+// tc_plan.cuh -- host planning of pair passes and device helpers shared by
+// the libtc translation units.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "tc_internal.h"
+#include "tc_pass.cuh"
+#include "tc_pass_mixed.cuh"
+
+namespace tc {
+
+constexpr int kThreads = 256;       // pass CTA size = source tile length T
+constexpr int kR = 2;               // rows per thread
+constexpr int kRB = kThreads * kR;  // rows per row block
+constexpr int kT = kThreads;
+
+// ------------------------------------------------------------ planning ---
+
+struct Plan {
+    std::vector<Prob> prob;
+    int64_t W = 0;   // total units
+    int64_t G = 1;   // CTAs
+    int64_t slots = 1;
+    int64_t M = 0;   // total rows
+};
+
+// Fill unit offsets, row blocks and tile counts; W = sum of units.
+inline void plan_units(Plan& P)
+{
+    int64_t u = 0;
+    for (auto& p : P.prob) {
+        p.n_rb = (int32_t)((p.m + kRB - 1) / kRB);
+        p.n_t_snap = (int32_t)((p.snap_e - p.snap_b + kT - 1) / kT);
+        p.n_t_priv = (int32_t)((p.m + kT - 1) / kT);
+        p.unit_off = u;
+        u += (int64_t)p.n_rb * (p.n_t_snap + p.n_t_priv);
+    }
+    P.W = u;
+}
+
+// Largest number of CTAs that touch one row block, for G CTAs over units
+// [u_base, u_base + W) of problems `ps`.
+inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last, int64_t u_base, int64_t W,
+                          int64_t G)
+{
+    int64_t best = 1;
+    for (size_t s = first; s < last; ++s) {
+        const Prob& p = ps[s];
+        int64_t n_t = p.n_t_snap + p.n_t_priv;
+        for (int64_t rb = 0; rb < p.n_rb; ++rb) {
+            int64_t U0 = p.unit_off + rb * n_t - u_base;
+            int64_t c = sk_owner(U0 + n_t - 1, W, G) - sk_owner(U0, W, G) + 1;
+            best = std::max(best, c);
+        }
+    }
+    return best;
+}
+
+template <class K> inline int64_t grid_for(K kernel, int64_t W)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess || occ < 1) occ = 1;
+    int64_t g = (int64_t)sm_count() * occ;
+    return std::max<int64_t>(1, std::min<int64_t>(g, W));
+}
+
+// ------------------------------------------------------- small kernels ---
+
+__device__ __forceinline__ bool inside(double x, double y)
+{
+    double r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+    return r <= 1.0 + kWallSlack;
+}
+
+// Deterministic block sum of one double per thread (fixed tree).
+template <int THREADS> __device__ double block_sum(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int w = THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Number of slots holding partials of row block rb of problem p.
+__device__ __forceinline__ int64_t slot_count(const Prob& p, int rb, int64_t u_base, int64_t W, int64_t G)
+{
+    int64_t n_t = p.n_t_snap + p.n_t_priv;
+    int64_t U0 = p.unit_off + rb * n_t - u_base;
+    return sk_owner(U0 + n_t - 1, W, G) - sk_owner(U0, W, G) + 1;
+}
+
+__device__ __forceinline__ double2 project1(double2 p, double radius, bool pinned)
+{
+    double r = sqrt(__dadd_rn(__dmul_rn(p.x, p.x), __dmul_rn(p.y, p.y)));
+    if (pinned) {
+        if (r > 0.0) return make_double2(p.x / r, p.y / r);
+    } else if (r > radius) {
+        double s = radius / r;
+        return make_double2(__dmul_rn(p.x, s), __dmul_rn(p.y, s));
+    }
+    return p;
+}
+
+// Gradient with the wall-blocked components removed (pinned charges keep the
+// component along the circle; a free charge at the wall whose force -g points
+// outward keeps the tangential part).
+__device__ __forceinline__ double2 wall_grad(double2 x, double2 g, double radius, bool pinned)
+{
+    double r = sqrt(__dadd_rn(__dmul_rn(x.x, x.x), __dmul_rn(x.y, x.y)));
+    if (r > 0.0 && (pinned || r >= radius * (1.0 - 1e-12))) {
+        double ux = x.x / r, uy = x.y / r;
+        double gr = __dadd_rn(__dmul_rn(g.x, ux), __dmul_rn(g.y, uy));
+        if (pinned || gr < 0.0) {
+            g.x = __dsub_rn(g.x, __dmul_rn(gr, ux));
+            g.y = __dsub_rn(g.y, __dmul_rn(gr, uy));
+        }
+    }
+    return g;
+}
+
+// ------------------------------------------------------ pass launching ---
+
+// The float32 pass has its own kernel (packed FP32x2, near/far tiles); the
+// float64 and energy-change passes share k_pass.
+template <int KIND, bool WANT_E, bool WANT_G> inline auto pass_kernel()
+{
+    if constexpr (KIND == PASS_MIXED)
+        return k_pass_mixed<kR, kThreads, WANT_E, WANT_G>;
+    else
+        return k_pass<KIND, kR, kThreads, WANT_E, WANT_G>;
+}
+
+template <int KIND, bool WANT_E, bool WANT_G>
+inline cudaError_t launch_pass(const PassArgs& a, int64_t G, int64_t u_base, int64_t row_sub, cudaStream_t s)
+{
+    if (a.W <= 0) return cudaSuccess;
+    pass_kernel<KIND, WANT_E, WANT_G>()<<<(unsigned)G, kThreads, 0, s>>>(a, u_base, row_sub);
+    return cudaGetLastError();
+}
+
+template <int KIND, bool WANT_E, bool WANT_G> inline int64_t pass_grid(int64_t W)
+{
+    return grid_for(pass_kernel<KIND, WANT_E, WANT_G>(), W);
+}
+
+}  // namespace tc

@@ -1,0 +1,1074 @@
+// tc_relax.cu -- batched relaxation of subdomains / instances and the
+// pairwise energy change of Sec. II D.
+//
+// A relaxation step of every problem is one pair pass (all problems' units in
+// one persistent launch, tc_pass.cuh) followed by one update launch (one CTA
+// per problem: reduce the row partials in a fixed order, take the optimiser
+// step, re-split the moved rows).  The step loop is captured once into a CUDA
+// graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tc_plan.cuh"
+
+namespace tc {
+
+constexpr int kUpd = 256;   // update / reduction CTA size
+constexpr int kMaxMem = 16; // largest L-BFGS memory
+
+struct RelaxDev {
+    const Prob* prob;
+    int S;
+    int64_t M;
+    const int64_t* wbeg;   // per problem: first charge of the world range
+    const int32_t* idx;    // nullable (instance mode)
+    const uint8_t* flags;  // nullable
+    double2* pos;          // the caller's configuration
+    int32_t* gidx;         // per row: charge index
+    double2* x;            // per row: position (float64 master copy)
+    float4* xs;            // per row: hi/lo split of x
+    double2* g;            // per row: reduced dE/dx
+    double2* xp;           // per row: previous x (BB) / previous z (L-BFGS)
+    double2* gp;           // per row: previous g (BB) / current dE/dz (L-BFGS)
+    double2* z;            // per row: L-BFGS variable
+    double2* q;            // per row: L-BFGS work vector
+    double2* Sh;           // [mem][M] L-BFGS s history
+    double2* Yh;           // [mem][M] L-BFGS y history
+    d4* rows4;             // per row: (old, new) for the float64 energy change
+    uint32_t* mask;        // per problem: own-charge bit mask over its world range
+    uint32_t* taken;       // over all n charges: charges moved by an accepted problem
+    int* active;           // per problem: still stepping
+    int* ok;               // per problem: take part in the energy-change pass
+    int* steps;            // per problem
+    int* hist;             // per problem: L-BFGS pairs stored
+    int* head;             // per problem: L-BFGS ring position
+    double* rho;           // [S][mem]
+    double* rms;           // per problem
+    double* delta;         // per problem
+    double* energy;        // per problem
+    int* status;           // per problem
+    int* st;               // device status word
+};
+
+__device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, int64_t row)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P[mid].row_base <= row)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Row partial of one pass: sum of its slots in order (float64, compensated for e).
+struct SlotView {
+    int64_t W, G, u_base, stride, row_sub;
+};
+
+__device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double2* part_g, const SlotView& v)
+{
+    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
+    double gx = 0.0, gy = 0.0;
+    int64_t o = p.row_base + rl - v.row_sub;
+    for (int64_t k = 0; k < c; ++k) {
+        double2 q = part_g[k * v.stride + o];
+        gx += q.x;
+        gy += q.y;
+    }
+    return make_double2(gx, gy);
+}
+
+__device__ __forceinline__ double sum_e(const Prob& p, int64_t rl, const double* part_e, const SlotView& v)
+{
+    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
+    double hi = 0.0, lo = 0.0;
+    int64_t o = p.row_base + rl - v.row_sub;
+    for (int64_t k = 0; k < c; ++k) dd_add(hi, lo, part_e[k * v.stride + o]);
+    return hi + lo;
+}
+
+// Deterministic block reductions of several doubles at once.
+template <int N> __device__ void block_sums(double (&v)[N], double* sh)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = block_sum<kUpd>(v[i], sh);
+}
+
+__device__ double block_max(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kUpd / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------ wall parameterisation ---
+// Free charge: x = radius sin|z| z/|z| (x = radius z as z -> 0).  Pinned charge:
+// x = z/|z|.  The wall is a smooth maximum of |x|, as for the paper's
+// r = sigma sin^2 t of Sec. II D, so L-BFGS needs no projection.
+
+__device__ __forceinline__ double2 z_to_x(double2 z, double radius, bool pinned)
+{
+    double rho = sqrt(z.x * z.x + z.y * z.y);
+    if (pinned) return make_double2(z.x / rho, z.y / rho);
+    if (rho > 0.0) {
+        double f = radius * sin(rho) / rho;
+        return make_double2(z.x * f, z.y * f);
+    }
+    return make_double2(0.0, 0.0);
+}
+
+__device__ __forceinline__ double2 x_to_z(double2 x, double radius, bool pinned)
+{
+    double r = sqrt(x.x * x.x + x.y * x.y);
+    if (pinned) return r > 0.0 ? make_double2(x.x / r, x.y / r) : make_double2(1.0, 0.0);
+    if (r > 0.0) {
+        double q = fmin(r / radius, 1.0);
+        double f = asin(q) / r;
+        return make_double2(x.x * f, x.y * f);
+    }
+    return make_double2(0.0, 0.0);
+}
+
+// dE/dz from dE/dx (chain rule of the map above; cf. the paper's dE/dt, dE/du).
+__device__ __forceinline__ double2 grad_z(double2 z, double2 g, double radius, bool pinned)
+{
+    double rho = sqrt(z.x * z.x + z.y * z.y);
+    if (rho == 0.0) return pinned ? make_double2(0.0, 0.0) : make_double2(radius * g.x, radius * g.y);
+    double ux = z.x / rho, uy = z.y / rho;
+    double gr = g.x * ux + g.y * uy;
+    double tx = g.x - gr * ux, ty = g.y - gr * uy;
+    if (pinned) return make_double2(tx / rho, ty / rho);
+    double a = sin(rho) / rho, c = cos(rho);
+    return make_double2(radius * (a * tx + c * gr * ux), radius * (a * ty + c * gr * uy));
+}
+
+// ------------------------------------------------------------- set-up ---
+
+__global__ void k_rows_init(RelaxDev d, int64_t n, double radius, int lbfgs)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_row_prob(d.prob, d.S, rr);
+        const Prob p = d.prob[s];
+        const int64_t rl = rr - p.row_base;
+        int64_t j;
+        bool bad = false;
+        if (d.idx) {
+            j = d.idx[rr];
+            bad = j < p.snap_b || j >= p.snap_e || (rl > 0 && d.idx[rr - 1] >= j);
+        } else {
+            j = d.wbeg[s] + rl;
+        }
+        if (bad || j < 0 || j >= n) {
+            set_status(d.st, ST_INVALID);
+            j = 0;
+        }
+        d.gidx[rr] = (int32_t)j;
+        double2 x = d.pos[j];
+        if (!isfinite(x.x) || !isfinite(x.y)) set_status(d.st, ST_NONFINITE);
+        else if (!inside(x.x, x.y)) set_status(d.st, ST_OUTSIDE);
+        if (lbfgs) {
+            const bool pinned = d.flags && d.flags[j];
+            double2 z = x_to_z(x, radius, pinned);
+            x = z_to_x(z, radius, pinned);
+            d.z[rr] = z;
+        }
+        if (d.x) d.x[rr] = x;
+        if (d.xs) d.xs[rr] = split4(x.x, x.y);
+    }
+}
+
+__global__ void k_mask_build(RelaxDev d)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_row_prob(d.prob, d.S, rr);
+        const Prob p = d.prob[s];
+        if (p.mask_off < 0) continue;
+        int64_t j = (int64_t)d.gidx[rr] - p.snap_b;
+        if (j < 0 || j >= p.snap_e - p.snap_b) continue;
+        atomicOr(&d.mask[p.mask_off + (j >> 5)], 1u << (j & 31));
+    }
+}
+
+__global__ void k_split_pos(const double2* __restrict__ pos, int64_t n, float4* __restrict__ out, int* st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 p = pos[i];
+        if (!isfinite(p.x) || !isfinite(p.y))
+            set_status(st, ST_NONFINITE);
+        else if (!inside(p.x, p.y))
+            set_status(st, ST_OUTSIDE);
+        out[i] = split4(p.x, p.y);
+    }
+}
+
+// ------------------------------------------------------------ updates ---
+
+struct StepParams {
+    int opt;
+    int memory;
+    double step0, alpha_min, alpha_max, maxstep, gtol, radius;
+};
+
+// Projected gradient descent (fixed or Barzilai-Borwein step), one CTA per problem.
+__global__ void __launch_bounds__(kUpd) k_update_gdbb(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
+                                                       StepParams sp)
+{
+    __shared__ double sh[kUpd];
+    const int s = blockIdx.x;
+    if (!d.active[s]) return;
+    const Prob p = d.prob[s];
+    const int k = d.steps[s];
+    double acc[3] = {0.0, 0.0, 0.0};  // |pg|^2, s.y, y.y
+    bool bad = false;
+    for (int64_t rl = threadIdx.x; rl < p.m; rl += kUpd) {
+        const int64_t row = p.row_base + rl;
+        double2 g = sum_g(p, rl, part_g, v);
+        if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
+        d.g[row] = g;
+        const double2 x = d.x[row];
+        const bool pinned = d.flags && d.flags[d.gidx[row]];
+        double2 pg = wall_grad(x, g, sp.radius, pinned);
+        acc[0] += pg.x * pg.x + pg.y * pg.y;
+        if (sp.opt == TC_OPT_BB && k > 0) {
+            double2 xo = d.xp[row], go = d.gp[row];
+            double sx = x.x - xo.x, sy = x.y - xo.y, yx = g.x - go.x, yy = g.y - go.y;
+            acc[1] += sx * yx + sy * yy;
+            acc[2] += yx * yx + yy * yy;
+        }
+    }
+    if (bad) set_status(d.st, ST_NONFINITE);
+    block_sums(acc, sh);
+    const double rms = sqrt(acc[0] / (double)max(p.m, 1));
+    if (sp.gtol > 0.0 && rms < sp.gtol) {
+        if (threadIdx.x == 0) {
+            d.active[s] = 0;
+            d.rms[s] = rms;
+        }
+        return;
+    }
+    double alpha = sp.step0;
+    if (sp.opt == TC_OPT_BB && k > 0) {
+        alpha = (acc[1] > 0.0 && acc[2] > 0.0) ? acc[1] / acc[2] : sp.alpha_max;
+        alpha = fmin(fmax(alpha, sp.alpha_min), sp.alpha_max);
+    }
+    for (int64_t rl = threadIdx.x; rl < p.m; rl += kUpd) {
+        const int64_t row = p.row_base + rl;
+        const double2 x = d.x[row], g = d.g[row];
+        const bool pinned = d.flags && d.flags[d.gidx[row]];
+        d.xp[row] = x;
+        d.gp[row] = g;
+        double2 xn = make_double2(__dsub_rn(x.x, __dmul_rn(alpha, g.x)), __dsub_rn(x.y, __dmul_rn(alpha, g.y)));
+        xn = project1(xn, sp.radius, pinned);
+        d.x[row] = xn;
+        d.xs[row] = split4(xn.x, xn.y);
+    }
+    if (threadIdx.x == 0) {
+        d.steps[s] = k + 1;
+        d.rms[s] = rms;
+    }
+}
+
+// Sum over the problem's rows of f(row), block-reduced (deterministic).
+#define TC_ROWS(p) for (int64_t rl = threadIdx.x; rl < (p).m; rl += kUpd)
+
+// L-BFGS on the wall parameterisation, one CTA per problem.  Same iteration as
+// the host statement: pair test and store, stop test, two-loop recursion
+// (Nocedal & Wright, Alg. 7.4), descent check, max-displacement scaling.
+__global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
+                                                        StepParams sp)
+{
+    __shared__ double sh[kUpd];
+    __shared__ double al[kMaxMem];
+    const int s = blockIdx.x;
+    if (!d.active[s]) return;
+    const Prob p = d.prob[s];
+    const int k = d.steps[s];
+    const int mem = sp.memory;
+    const int64_t M = d.M;
+    double* rho = d.rho + (int64_t)s * kMaxMem;
+    // new dE/dz into q; pair statistics against the previous z (xp) and dE/dz (gp)
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // |gzn|^2, s.y, s.s, y.y
+    bool bad = false;
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        double2 g = sum_g(p, rl, part_g, v);
+        if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
+        const bool pinned = d.flags && d.flags[d.gidx[row]];
+        const double2 z = d.z[row];
+        double2 gz = grad_z(z, g, sp.radius, pinned);
+        d.q[row] = gz;
+        acc[0] += gz.x * gz.x + gz.y * gz.y;
+        if (k > 0) {
+            double2 zo = d.xp[row], go = d.gp[row];
+            double sx = z.x - zo.x, sy = z.y - zo.y, yx = gz.x - go.x, yy = gz.y - go.y;
+            acc[1] += sx * yx + sy * yy;
+            acc[2] += sx * sx + sy * sy;
+            acc[3] += yx * yx + yy * yy;
+        }
+    }
+    if (bad) set_status(d.st, ST_NONFINITE);
+    block_sums(acc, sh);
+    int hist = d.hist[s], head = d.head[s];
+    const bool keep = k > 0 && acc[1] > 1e-12 * sqrt(acc[2]) * sqrt(acc[3]);
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        const double2 gz = d.q[row];
+        if (keep) {
+            const double2 z = d.z[row], zo = d.xp[row], go = d.gp[row];
+            d.Sh[(int64_t)head * M + row] = make_double2(z.x - zo.x, z.y - zo.y);
+            d.Yh[(int64_t)head * M + row] = make_double2(gz.x - go.x, gz.y - go.y);
+        }
+        d.gp[row] = gz;
+    }
+    if (keep) {
+        if (threadIdx.x == 0) rho[head] = 1.0 / acc[1];
+        head = (head + 1) % mem;
+        hist = min(hist + 1, mem);
+    }
+    const double rms = sqrt(acc[0] / (double)max(p.m, 1));
+    if (sp.gtol > 0.0 && rms < sp.gtol) {
+        if (threadIdx.x == 0) {
+            d.active[s] = 0;
+            d.rms[s] = rms;
+            d.hist[s] = hist;
+            d.head[s] = head;
+        }
+        return;
+    }
+    __syncthreads();
+    // two-loop recursion on q = dE/dz
+    for (int i = 0; i < hist; ++i) {
+        const int j = ((head - 1 - i) % mem + mem) % mem;
+        double a[1] = {0.0};
+        TC_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 sj = d.Sh[(int64_t)j * M + row], qq = d.q[row];
+            a[0] += sj.x * qq.x + sj.y * qq.y;
+        }
+        block_sums(a, sh);
+        const double aj = rho[j] * a[0];
+        if (threadIdx.x == 0) al[j] = aj;
+        TC_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 yj = d.Yh[(int64_t)j * M + row], qq = d.q[row];
+            d.q[row] = make_double2(qq.x - aj * yj.x, qq.y - aj * yj.y);
+        }
+        __syncthreads();
+    }
+    double gamma = sp.step0;
+    if (hist > 0) {
+        const int j = ((head - 1) % mem + mem) % mem;
+        double a[2] = {0.0, 0.0};
+        TC_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 sj = d.Sh[(int64_t)j * M + row], yj = d.Yh[(int64_t)j * M + row];
+            a[0] += sj.x * yj.x + sj.y * yj.y;
+            a[1] += yj.x * yj.x + yj.y * yj.y;
+        }
+        block_sums(a, sh);
+        gamma = a[0] / a[1];
+    }
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        double2 qq = d.q[row];
+        d.q[row] = make_double2(qq.x * gamma, qq.y * gamma);
+    }
+    __syncthreads();
+    for (int i = hist - 1; i >= 0; --i) {
+        const int j = ((head - 1 - i) % mem + mem) % mem;
+        double b[1] = {0.0};
+        TC_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 yj = d.Yh[(int64_t)j * M + row], qq = d.q[row];
+            b[0] += yj.x * qq.x + yj.y * qq.y;
+        }
+        block_sums(b, sh);
+        const double c = al[j] - rho[j] * b[0];
+        TC_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 sj = d.Sh[(int64_t)j * M + row], qq = d.q[row];
+            d.q[row] = make_double2(qq.x + sj.x * c, qq.y + sj.y * c);
+        }
+        __syncthreads();
+    }
+    // d = -q; descent check against dE/dz (gp)
+    double dd[1] = {0.0};
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        double2 qq = d.q[row], gz = d.gp[row];
+        dd[0] -= gz.x * qq.x + gz.y * qq.y;
+    }
+    block_sums(dd, sh);
+    const bool reset = dd[0] >= 0.0;
+    if (reset) {
+        hist = 0;
+        head = 0;
+    }
+    double dmax = 0.0;
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        double2 qq = d.q[row], gz = d.gp[row];
+        double2 dv = reset ? make_double2(-sp.step0 * gz.x, -sp.step0 * gz.y) : make_double2(-qq.x, -qq.y);
+        d.q[row] = dv;
+        dmax = fmax(dmax, sqrt(dv.x * dv.x + dv.y * dv.y));
+    }
+    dmax = block_max(dmax, sh);
+    const double alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        const bool pinned = d.flags && d.flags[d.gidx[row]];
+        double2 z = d.z[row], dv = d.q[row];
+        d.xp[row] = z;
+        double2 zn = make_double2(z.x + alpha * dv.x, z.y + alpha * dv.y);
+        d.z[row] = zn;
+        double2 xn = z_to_x(zn, sp.radius, pinned);
+        d.x[row] = xn;
+        d.xs[row] = split4(xn.x, xn.y);
+    }
+    if (threadIdx.x == 0) {
+        d.steps[s] = k + 1;
+        d.rms[s] = rms;
+        d.hist[s] = hist;
+        d.head[s] = head;
+    }
+}
+
+// ----------------------------------------------------- energy changes ---
+
+__global__ void k_rows4(RelaxDev d, const double2* __restrict__ newpos)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        double2 o = d.pos[d.gidx[rr]];
+        double2 nw = newpos[rr];
+        d.rows4[rr] = make_d4(o.x, o.y, nw.x, nw.y);
+    }
+}
+
+// Per problem: sum of its rows' partials (compensated) into out[s].
+__global__ void __launch_bounds__(kUpd) k_problem_sums(RelaxDev d, const double* __restrict__ part_e, SlotView v,
+                                                        double* out, const int* __restrict__ only)
+{
+    __shared__ double sh[kUpd];
+    const int s = blockIdx.x;
+    if (only && !only[s]) return;
+    const Prob p = d.prob[s];
+    double hi = 0.0, lo = 0.0;
+    TC_ROWS(p) dd_add(hi, lo, sum_e(p, rl, part_e, v));
+    double t = block_sum<kUpd>(hi, sh) + block_sum<kUpd>(lo, sh);
+    if (threadIdx.x == 0) {
+        out[s] = t;
+        if (!isfinite(t)) set_status(d.st, ST_NONFINITE);
+    }
+}
+
+// Sequential accept, problem s: reduce its energy change, apply it if negative,
+// then decide whether problem s + 1 is free of accepted charges.
+__global__ void __launch_bounds__(kUpd) k_accept_apply(RelaxDev d, int s, const double* __restrict__ part1, SlotView v)
+{
+    __shared__ double sh[kUpd];
+    __shared__ int clash;
+    const Prob p = d.prob[s];
+    if (d.ok[s]) {
+        double hi = 0.0, lo = 0.0;
+        TC_ROWS(p) dd_add(hi, lo, sum_e(p, rl, part1, v));
+        const double de = block_sum<kUpd>(hi, sh) + block_sum<kUpd>(lo, sh);
+        const bool acc = de < 0.0;
+        if (!isfinite(de)) set_status(d.st, ST_NONFINITE);
+        if (acc) {
+            TC_ROWS(p)
+            {
+                const int64_t row = p.row_base + rl;
+                const int32_t j = d.gidx[row];
+                d.pos[j] = d.x[row];
+                atomicOr(&d.taken[j >> 5], 1u << (j & 31));
+            }
+        }
+        if (threadIdx.x == 0) {
+            d.delta[s] = de;
+            d.status[s] = acc ? 1 : 0;
+        }
+    } else if (threadIdx.x == 0) {
+        d.delta[s] = 0.0;
+        d.status[s] = 2;
+    }
+    if (s + 1 >= d.S) return;
+    __threadfence();
+    if (threadIdx.x == 0) clash = 0;
+    __syncthreads();
+    const Prob q = d.prob[s + 1];
+    TC_ROWS(q)
+    {
+        const int32_t j = d.gidx[q.row_base + rl];
+        if ((((volatile uint32_t*)d.taken)[j >> 5] >> (j & 31)) & 1u) clash = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) d.ok[s + 1] = clash ? 0 : 1;
+}
+
+// Instance mode write-back: every row (accept = 0) or the rows of problems
+// whose energy change is negative (accept = 1).
+__global__ void k_write_back(RelaxDev d, int accept)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_row_prob(d.prob, d.S, rr);
+        if (accept && !(d.delta[s] < 0.0)) continue;
+        d.pos[d.gidx[rr]] = d.x[rr];
+    }
+}
+
+__global__ void k_results(RelaxDev d, tc_subdomain_result* out, int mode_instances, int accept, int want_energy)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.S) return;
+    tc_subdomain_result r;
+    r.delta_e = accept ? d.delta[s] : NAN;
+    r.energy = want_energy ? d.energy[s] : NAN;
+    r.rms = d.rms[s];
+    r.steps = d.steps[s];
+    if (mode_instances)
+        r.status = accept ? (d.delta[s] < 0.0 ? 1 : 0) : 1;
+    else
+        r.status = accept ? d.status[s] : 0;
+    out[s] = r;
+}
+
+// ------------------------------------------------------------- driver ---
+
+static tc_status check_params(const tc_relax_params* prm)
+{
+    if (!prm) return TC_ERR_INVALID_ARG;
+    if (prm->precision != TC_FP64 && prm->precision != TC_MIXED) return TC_ERR_INVALID_ARG;
+    if (prm->optimizer < TC_OPT_GD || prm->optimizer > TC_OPT_LBFGS) return TC_ERR_INVALID_ARG;
+    if (prm->n_steps < 0 || prm->polish_steps < 0) return TC_ERR_INVALID_ARG;
+    if (prm->optimizer == TC_OPT_LBFGS && (prm->memory < 1 || prm->memory > kMaxMem)) return TC_ERR_INVALID_ARG;
+    if (!(prm->radius > 0.0) || !(prm->step0 > 0.0)) return TC_ERR_INVALID_ARG;
+    if (prm->optimizer == TC_OPT_BB && !(prm->alpha_max >= prm->alpha_min && prm->alpha_min >= 0.0))
+        return TC_ERR_INVALID_ARG;
+    if (prm->optimizer == TC_OPT_LBFGS && !(prm->maxstep > 0.0)) return TC_ERR_INVALID_ARG;
+    if (!(prm->gtol >= 0.0) || !(prm->polish_gtol >= 0.0)) return TC_ERR_INVALID_ARG;
+    return TC_OK;
+}
+
+struct Host {
+    std::vector<int64_t> off, world;
+};
+
+// Launch timing of the last profiled call (per host thread).
+thread_local tc_relax_profile g_last_profile{};
+
+// CUDA events of one profiled call, created on demand per device and reused.
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t get(size_t i)
+    {
+        while (ev.size() <= i) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev.push_back(e);
+        }
+        return ev[i];
+    }
+};
+thread_local EventPool g_events;
+
+static double elapsed(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    if (!a || !b) return 0.0;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();  // a timing query failure must not surface at a later launch check
+        return 0.0;
+    }
+    return ms;
+}
+
+static_assert(sizeof(tc_subdomain_result) == 32, "tc_subdomain_result layout");
+static_assert(sizeof(tc_relax_params) == 88, "tc_relax_params layout");
+static_assert(sizeof(tc_relax_profile) == 56, "tc_relax_profile layout");
+
+// One relaxation phase: `steps` x (pass, update), captured into a CUDA graph.
+template <int KIND>
+static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, const StepParams& sp, int steps,
+                           cudaStream_t s, bool prof, int& launches)
+{
+    if (steps <= 0) return TC_OK;
+    size_t ev0 = 0;  // events 0 .. 2 steps: [pass k] between 2k and 2k+1, [update k] between 2k+1 and 2k+2
+    SlotView v{P.W, G, 0, P.M, 0};
+    cudaStreamCaptureStatus cs;
+    if (cudaError_t e_ = cudaStreamIsCapturing(s, &cs); e_ != cudaSuccess) return cuda_fail(e_, "cudaStreamIsCapturing");
+    // Inside a caller's capture the launches simply join the caller's graph;
+    // otherwise the loop is captured on a private stream and replayed on s.
+    // A profiled call launches directly on s, with an event between launches.
+    const bool capture = cs == cudaStreamCaptureStatusNone && !prof;
+    cudaStream_t cap = s;
+    if (capture) {
+        tc_status err = TC_OK;
+        cap = capture_stream(&err);
+        if (!cap) return err;
+        if (cudaError_t e_ = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal); e_ != cudaSuccess) return cuda_fail(e_, "cudaStreamBeginCapture");
+    }
+    cudaError_t e = cudaSuccess;
+    const char* where = "step loop launch";
+    if (prof) e = cudaEventRecord(g_events.get(ev0), cap);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+        e = launch_pass<KIND, false, true>(a, G, 0, 0, cap);
+        if (e != cudaSuccess) break;
+        if (prof) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 1), cap);
+        if (sp.opt == TC_OPT_LBFGS)
+            k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
+        else
+            k_update_gdbb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (prof && e == cudaSuccess) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 2), cap);
+        launches += (a.W > 0 ? 1 : 0) + 1;
+    }
+    if (capture) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess && (e = e2) != cudaSuccess) where = "cudaStreamEndCapture";
+        if (e == cudaSuccess && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) where = "cudaGraphInstantiate";
+        if (e == cudaSuccess && (e = cudaGraphLaunch(exec, s)) != cudaSuccess) where = "cudaGraphLaunch";
+        // the executable graph is destroyed only after its launch has finished
+        if (e == cudaSuccess && (e = cudaStreamSynchronize(s)) != cudaSuccess) where = "step loop execution";
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    if (prof && e == cudaSuccess) {
+        if (!capture) e = cudaStreamSynchronize(s);
+        for (int k = 0; k < steps; ++k) {
+            g_last_profile.pass_ms += elapsed(g_events.get(ev0 + 2 * k), g_events.get(ev0 + 2 * k + 1));
+            g_last_profile.update_ms += elapsed(g_events.get(ev0 + 2 * k + 1), g_events.get(ev0 + 2 * k + 2));
+        }
+        g_last_profile.relax_ms += elapsed(g_events.get(ev0), g_events.get(ev0 + 2 * steps));
+        g_last_profile.n_pass += a.W > 0 ? steps : 0;
+    }
+    return cuda_status(e, where);
+}
+
+static tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
+                       const int64_t* world, const uint8_t* flags, const tc_relax_params* prm,
+                       tc_subdomain_result* out, cudaStream_t s)
+{
+    tc_status err = check_params(prm);
+    if (err != TC_OK) return err;
+    if (n < 0 || n_sub < 0 || (n > 0 && !pos) || (n_sub > 0 && !out) || (reinterpret_cast<uintptr_t>(pos) & 15) ||
+        (reinterpret_cast<uintptr_t>(out) & 7))
+        return TC_ERR_INVALID_ARG;
+    const bool inst = idx == nullptr;
+    if (inst && !world) return TC_ERR_INVALID_ARG;
+    if (!inst && !offsets) return TC_ERR_INVALID_ARG;
+    g_last_profile = tc_relax_profile{};
+    if (n_sub == 0) return TC_OK;
+    int* st = device_status(&err);
+    if (!st) return err;
+    const bool prof = prm->profile != 0;
+    int launches = 0;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_d = nullptr;
+    if (prof) {
+        // events 0 .. 2 max_steps belong to run_phase; four more after them
+        size_t base = 2 * (size_t)std::max(prm->n_steps, prm->polish_steps) + 2;
+        ev_a = g_events.get(base);
+        ev_b = g_events.get(base + 1);
+        ev_c = g_events.get(base + 2);
+        ev_d = g_events.get(base + 3);
+        if (!ev_a || !ev_b || !ev_c || !ev_d) return TC_ERR_CUDA;
+        // every event is created here: none may be created while a graph is being captured
+    }
+
+    // sizes to the host (one synchronisation per call)
+    Host h;
+    if (!inst) {
+        h.off.resize(n_sub + 1);
+        if (cudaError_t e_ = cudaMemcpyAsync(h.off.data(), offsets, 8 * (n_sub + 1), cudaMemcpyDeviceToHost, s); e_ != cudaSuccess) return cuda_fail(e_, "cudaMemcpyAsync");
+    }
+    if (world) {
+        h.world.resize(2 * (size_t)n_sub);
+        if (cudaError_t e_ = cudaMemcpyAsync(h.world.data(), world, 16 * (size_t)n_sub, cudaMemcpyDeviceToHost, s); e_ != cudaSuccess) return cuda_fail(e_, "cudaMemcpyAsync");
+    }
+    if (cudaError_t e_ = cudaStreamSynchronize(s); e_ != cudaSuccess) return cuda_fail(e_, "cudaStreamSynchronize");
+
+    Plan P;
+    P.prob.resize(n_sub);
+    std::vector<int64_t> wbeg(n_sub);
+    int64_t rows = 0, mask_words = 0, max_m = 0;
+    for (int32_t k = 0; k < n_sub; ++k) {
+        int64_t wb = world ? h.world[2 * k] : 0, we = world ? h.world[2 * k + 1] : n;
+        if (wb < 0 || we > n || wb > we) return TC_ERR_INVALID_ARG;
+        Prob& p = P.prob[k];
+        int64_t m;
+        if (inst) {
+            m = we - wb;
+            p.row_base = rows;
+            p.snap_b = p.snap_e = 0;
+            p.mask_off = -1;
+        } else {
+            if (h.off[k + 1] < h.off[k] || h.off[0] != 0) return TC_ERR_INVALID_ARG;
+            m = h.off[k + 1] - h.off[k];
+            if (m > we - wb) return TC_ERR_INVALID_ARG;
+            p.row_base = h.off[k];
+            p.snap_b = wb;
+            p.snap_e = we;
+            p.mask_off = mask_words;
+            mask_words += (we - wb + 31) / 32;
+        }
+        if (m > INT32_MAX / 2) return TC_ERR_INVALID_ARG;
+        p.m = (int32_t)m;
+        wbeg[k] = wb;
+        rows += m;
+        max_m = std::max(max_m, m);
+    }
+    if (n > INT32_MAX) return TC_ERR_INVALID_ARG;
+    P.M = rows;
+    plan_units(P);
+    const int prec = prm->precision;
+    const bool lbfgs = prm->optimizer == TC_OPT_LBFGS;
+    const int mem = lbfgs ? prm->memory : 0;
+    const int64_t G_bulk = prec == TC_MIXED ? pass_grid<PASS_MIXED, false, true>(P.W) : pass_grid<PASS_F64, false, true>(P.W);
+    const int64_t G_f64 = pass_grid<PASS_F64, false, true>(P.W);
+    const int64_t G_e = pass_grid<PASS_F64, true, false>(P.W);
+    const int64_t G_d = pass_grid<PASS_DELTA, false, false>(P.W);
+    int64_t slots = 1;
+    for (int64_t G : {G_bulk, G_f64, G_e, G_d}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
+    // single-problem passes of the sequential accept
+    int64_t slots1 = 1;
+    std::vector<int64_t> G1(n_sub);
+    if (!inst && prm->accept) {
+        for (int32_t k = 0; k < n_sub; ++k) {
+            const Prob& p = P.prob[k];
+            int64_t Wk = (int64_t)p.n_rb * (p.n_t_snap + p.n_t_priv);
+            G1[k] = std::max<int64_t>(1, std::min<int64_t>(G_d, Wk));
+            slots1 = std::max(slots1, plan_slots(P.prob, k, k + 1, p.unit_off, Wk, G1[k]));
+        }
+    }
+    const int64_t M = P.M;
+    const int64_t taken_words = (n + 31) / 32;
+
+    Carver c;
+    auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
+                      double2*& part_g, double*& part1) {
+        probd = cv.take<Prob>(n_sub);
+        wbd = cv.take<int64_t>(n_sub);
+        d.gidx = cv.take<int32_t>(M);
+        d.x = cv.take<double2>(M);
+        d.xs = cv.take<float4>(M);
+        d.g = cv.take<double2>(M);
+        d.xp = cv.take<double2>(M);
+        d.gp = cv.take<double2>(M);
+        d.z = cv.take<double2>(lbfgs ? M : 0);
+        d.q = cv.take<double2>(lbfgs ? M : 0);
+        d.Sh = cv.take<double2>(lbfgs ? (size_t)mem * M : 0);
+        d.Yh = cv.take<double2>(lbfgs ? (size_t)mem * M : 0);
+        d.rows4 = cv.take<d4>(M);
+        d.mask = cv.take<uint32_t>(mask_words);
+        d.taken = cv.take<uint32_t>(taken_words);
+        d.active = cv.take<int>(n_sub);
+        d.ok = cv.take<int>(n_sub);
+        d.steps = cv.take<int>(n_sub);
+        d.hist = cv.take<int>(n_sub);
+        d.head = cv.take<int>(n_sub);
+        d.status = cv.take<int>(n_sub);
+        d.rho = cv.take<double>((size_t)n_sub * kMaxMem);
+        d.rms = cv.take<double>(n_sub);
+        d.delta = cv.take<double>(n_sub);
+        d.energy = cv.take<double>(n_sub);
+        snap_split = cv.take<float4>(inst ? 0 : n);
+        part_e = cv.take<double>(slots * M);
+        part_g = cv.take<double2>(slots * M);
+        part1 = cv.take<double>(slots1 * max_m);
+    };
+    RelaxDev d{};
+    Prob* probd;
+    int64_t* wbd;
+    float4* snap_split;
+    double *part_e, *part1;
+    double2* part_g;
+    layout(c, d, probd, wbd, snap_split, part_e, part_g, part1);
+    void* ws = workspace(s, c.off, &err);
+    if (!ws) return err;
+    c.base = static_cast<char*>(ws);
+    c.off = kCounterBytes;
+    layout(c, d, probd, wbd, snap_split, part_e, part_g, part1);
+    d.prob = probd;
+    d.S = n_sub;
+    d.M = M;
+    d.wbeg = wbd;
+    d.idx = idx;
+    d.flags = flags;
+    d.pos = reinterpret_cast<double2*>(pos);
+    d.st = st;
+
+    cudaError_t e = cudaSuccess;
+    if (prof) cudaEventRecord(ev_a, s);
+    e = cudaMemcpyAsync(probd, P.prob.data(), sizeof(Prob) * n_sub, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wbd, wbeg.data(), 8 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
+    // per-problem state: active = ok = 1, counters zero
+    std::vector<int> ones(n_sub, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.ok, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
+    for (int* z : {d.steps, d.hist, d.head, d.status})
+        if (e == cudaSuccess) e = cudaMemsetAsync(z, 0, 4 * (size_t)n_sub, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.rms, 0, 8 * (size_t)n_sub, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.delta, 0, 8 * (size_t)n_sub, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.energy, 0, 8 * (size_t)n_sub, s);
+    if (e == cudaSuccess && mask_words) e = cudaMemsetAsync(d.mask, 0, 4 * (size_t)mask_words, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.taken, 0, 4 * (size_t)taken_words, s);
+    if (e != cudaSuccess) return cuda_fail(e, "set-up");
+    const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((M + 255) / 256, 8L * sm_count()));
+    if (M > 0) {
+        k_rows_init<<<eb, 256, 0, s>>>(d, n, prm->radius, lbfgs ? 1 : 0);
+        ++launches;
+        if (!inst) {
+            k_mask_build<<<eb, 256, 0, s>>>(d);
+            ++launches;
+        }
+    }
+    if (!inst && n > 0) {
+        int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8L * sm_count()));
+        k_split_pos<<<nb, 256, 0, s>>>(reinterpret_cast<const double2*>(pos), n, snap_split, st);
+        ++launches;
+    }
+    if (prof) cudaEventRecord(ev_b, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "launch");
+    // argument errors found on the device stop the call before any step
+    {
+        int hst = 0;
+        if (cudaError_t e_ = cudaMemcpyAsync(&hst, st, 4, cudaMemcpyDeviceToHost, s); e_ != cudaSuccess)
+            return cuda_fail(e_, "status read");
+        if (cudaError_t e_ = cudaStreamSynchronize(s); e_ != cudaSuccess) return cuda_fail(e_, "set-up");
+        if (hst != 0) {
+            cudaMemsetAsync(st, 0, 4, s);
+            cudaStreamSynchronize(s);
+            return static_cast<tc_status>(hst);
+        }
+    }
+
+    PassArgs a{};
+    a.prob = probd;
+    a.S = n_sub;
+    a.W = P.W;
+    a.M = M;
+    a.mask = inst ? nullptr : d.mask;
+    a.active = d.active;
+    a.part_e = part_e;
+    a.part_g = part_g;
+    StepParams sp{prm->optimizer, mem, prm->step0, prm->alpha_min, prm->alpha_max, prm->maxstep, prm->gtol, prm->radius};
+    tc_status rs;
+    if (prec == TC_MIXED) {
+        a.rows = d.xs;
+        a.snap = snap_split;
+        rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches);
+    } else {
+        a.rows = d.x;
+        a.snap = pos;
+        rs = run_phase<PASS_F64>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches);
+    }
+    if (rs != TC_OK) return rs;
+    if (prm->polish_steps > 0) {
+        // float64 polish: every problem steps again, L-BFGS history kept
+        if (cudaError_t e_ = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s); e_ != cudaSuccess) return cuda_fail(e_, "cudaMemcpyAsync");
+        StepParams sp2 = sp;
+        sp2.gtol = prm->polish_gtol;
+        a.rows = d.x;
+        a.snap = pos;
+        rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches);
+        if (rs != TC_OK) return rs;
+    }
+    a.active = nullptr;
+    if (prof) cudaEventRecord(ev_c, s);
+    if (prm->want_energy) {
+        // float64 E_sub of the relaxed rows against the entry configuration
+        a.rows = d.x;
+        a.snap = pos;
+        if ((e = launch_pass<PASS_F64, true, false>(a, G_e, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+        SlotView v{P.W, G_e, 0, M, 0};
+        k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, d.energy, nullptr);
+        launches += (P.W > 0 ? 1 : 0) + 1;
+    }
+    if (prm->accept) {
+        k_rows4<<<eb, 256, 0, s>>>(d, d.x);
+        ++launches;
+        a.rows = d.rows4;
+        a.snap = pos;
+        if (inst) {
+            if ((e = launch_pass<PASS_DELTA, false, false>(a, G_d, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+            SlotView v{P.W, G_d, 0, M, 0};
+            k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, d.delta, nullptr);
+            k_write_back<<<eb, 256, 0, s>>>(d, 1);
+            launches += (P.W > 0 ? 1 : 0) + 2;
+        } else {
+            a.part_e = part1;
+            a.active = d.ok;
+            for (int32_t k = 0; k < n_sub; ++k) {
+                const Prob& p = P.prob[k];
+                PassArgs ak = a;
+                ak.W = (int64_t)p.n_rb * (p.n_t_snap + p.n_t_priv);
+                ak.M = std::max<int64_t>(p.m, 1);
+                if ((e = launch_pass<PASS_DELTA, false, false>(ak, G1[k], p.unit_off, p.row_base, s)) != cudaSuccess)
+                    return cuda_fail(e, "accept pass launch");
+                SlotView v{ak.W, G1[k], p.unit_off, ak.M, p.row_base};
+                k_accept_apply<<<1, kUpd, 0, s>>>(d, k, part1, v);
+                launches += (ak.W > 0 ? 1 : 0) + 1;
+            }
+        }
+    } else if (inst) {
+        k_write_back<<<eb, 256, 0, s>>>(d, 0);
+        ++launches;
+    }
+    k_results<<<(n_sub + 127) / 128, 128, 0, s>>>(d, out, inst ? 1 : 0, prm->accept ? 1 : 0, prm->want_energy ? 1 : 0);
+    ++launches;
+    if (prof) cudaEventRecord(ev_d, s);
+    if (cudaError_t e_ = cudaGetLastError(); e_ != cudaSuccess) return cuda_fail(e_, "cudaGetLastError");
+    e = cudaStreamSynchronize(s);
+    if (prof && e == cudaSuccess) {
+        g_last_profile.setup_ms = elapsed(ev_a, ev_b);
+        g_last_profile.accept_ms = elapsed(ev_c, ev_d);
+    }
+    g_last_profile.launches = launches;
+    int64_t pairs = 0;
+    for (const Prob& p : P.prob) {
+        // a row meets every other charge of its world once: m (world - 1) in
+        // subdomain mode, m (m - 1) for an instance
+        int64_t others = inst ? (int64_t)p.m - 1 : (p.snap_e - p.snap_b) - 1;
+        pairs += (int64_t)p.m * std::max<int64_t>(others, 0);
+    }
+    g_last_profile.pass_pairs = pairs;
+    return cuda_status(e, "relaxation (accept / write-back / results)");
+}
+
+// tc_subdomain_delta_energy: every subdomain against pos, in one pass.
+static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
+                           const double* new_active, double* delta, cudaStream_t s)
+{
+    if (n < 0 || n_sub < 0 || (n > 0 && !pos) || (n_sub > 0 && (!offsets || !delta)) ||
+        (reinterpret_cast<uintptr_t>(pos) & 15) || (reinterpret_cast<uintptr_t>(new_active) & 15) ||
+        (reinterpret_cast<uintptr_t>(delta) & 7))
+        return TC_ERR_INVALID_ARG;
+    if (n_sub == 0) return TC_OK;
+    if (n > INT32_MAX) return TC_ERR_INVALID_ARG;
+    tc_status err = TC_OK;
+    int* st = device_status(&err);
+    if (!st) return err;
+    std::vector<int64_t> off(n_sub + 1);
+    if (cudaError_t e_ = cudaMemcpyAsync(off.data(), offsets, 8 * (size_t)(n_sub + 1), cudaMemcpyDeviceToHost, s);
+        e_ != cudaSuccess)
+        return cuda_fail(e_, "offsets read");
+    if (cudaError_t e_ = cudaStreamSynchronize(s); e_ != cudaSuccess) return cuda_fail(e_, "offsets read");
+    Plan P;
+    P.prob.resize(n_sub);
+    int64_t mask_words = 0;
+    if (off[0] != 0) return TC_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < n_sub; ++k) {
+        if (off[k + 1] < off[k] || off[k + 1] - off[k] > n) return TC_ERR_INVALID_ARG;
+        Prob& p = P.prob[k];
+        p.row_base = off[k];
+        p.m = (int32_t)(off[k + 1] - off[k]);
+        p.snap_b = 0;
+        p.snap_e = n;
+        p.mask_off = mask_words;
+        mask_words += (n + 31) / 32;
+    }
+    P.M = off[n_sub];
+    if (P.M > 0 && (!idx || !new_active)) return TC_ERR_INVALID_ARG;
+    plan_units(P);
+    const int64_t G = pass_grid<PASS_DELTA, false, false>(P.W);
+    const int64_t slots = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G);
+    const int64_t M = P.M;
+    Carver c;
+    auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, double*& part_e) {
+        probd = cv.take<Prob>(n_sub);
+        d.gidx = cv.take<int32_t>(M);
+        d.rows4 = cv.take<d4>(M);
+        d.mask = cv.take<uint32_t>(mask_words);
+        part_e = cv.take<double>(slots * std::max<int64_t>(M, 1));
+    };
+    RelaxDev d{};
+    Prob* probd;
+    double* part_e;
+    layout(c, d, probd, part_e);
+    void* ws = workspace(s, c.off, &err);
+    if (!ws) return err;
+    c.base = static_cast<char*>(ws);
+    c.off = kCounterBytes;
+    layout(c, d, probd, part_e);
+    d.prob = probd;
+    d.S = n_sub;
+    d.M = M;
+    d.idx = idx;
+    d.pos = const_cast<double2*>(reinterpret_cast<const double2*>(pos));
+    d.st = st;
+    cudaError_t e = cudaMemcpyAsync(probd, P.prob.data(), sizeof(Prob) * n_sub, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.mask, 0, 4 * (size_t)mask_words, s);
+    if (e != cudaSuccess) return cuda_fail(e, "set-up");
+    const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((M + 255) / 256, 8L * sm_count()));
+    if (M > 0) {
+        d.x = nullptr;
+        d.xs = nullptr;
+        k_rows_init<<<eb, 256, 0, s>>>(d, n, 1.0, 0);
+        k_mask_build<<<eb, 256, 0, s>>>(d);
+        k_rows4<<<eb, 256, 0, s>>>(d, reinterpret_cast<const double2*>(new_active));
+    }
+    PassArgs a{};
+    a.prob = probd;
+    a.S = n_sub;
+    a.W = P.W;
+    a.M = std::max<int64_t>(M, 1);
+    a.rows = d.rows4;
+    a.snap = pos;
+    a.mask = d.mask;
+    a.active = nullptr;
+    a.part_e = part_e;
+    a.part_g = nullptr;
+    if ((e = launch_pass<PASS_DELTA, false, false>(a, G, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+    SlotView v{P.W, G, 0, a.M, 0};
+    k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, delta, nullptr);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace tc
+
+extern "C" {
+
+tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
+                              const int64_t* world, const uint8_t* flags, const tc_relax_params* prm,
+                              tc_subdomain_result* out, tc_stream stream)
+{
+    return tc::relax(pos, n, idx, offsets, n_sub, world, flags, prm, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tc_status tc_relax_last_profile(tc_relax_profile* out)
+{
+    if (!out) return TC_ERR_INVALID_ARG;
+    *out = tc::g_last_profile;
+    return TC_OK;
+}
+
+tc_status tc_subdomain_delta_energy(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
+                                    int32_t n_sub, const double* new_active, double* delta, tc_stream stream)
+{
+    return tc::delta_all(pos, n, idx, offsets, n_sub, new_active, delta, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -29,6 +29,7 @@ __all__ = [
     "arcsine_spacing",
     "min_pair_distance",
     "to_csr",
+    "zorder",
 ]
 
 
@@ -203,3 +204,33 @@ def min_pair_distance(pos: np.ndarray) -> float:
         return math.inf
     d, _ = cKDTree(pos).query(pos, k=2)
     return float(d[:, 1].min())
+
+
+def zorder(pos: np.ndarray, bits: int = 16) -> np.ndarray:
+    """Permutation that lists the charges along a Hilbert curve through their cells.
+
+    The charges are identical, so relabelling them changes nothing physical; a
+    configuration stored in this order keeps nearby charges at nearby indices
+    (the Hilbert curve, unlike the Z curve, never jumps across the square).
+    Coordinates in [-1, 1] are quantised to 2^bits cells per axis; the curve
+    index of a cell follows the usual quadrant-by-quadrant construction (take the
+    quadrant, add its offset, rotate/reflect the remaining bits into it).  Ties
+    keep index order (stable sort).
+    """
+    q = np.clip(((np.asarray(pos, dtype=np.float64) + 1.0) * 0.5 * (1 << bits)).astype(np.int64), 0,
+                (1 << bits) - 1)
+    x, y = q[:, 0].copy(), q[:, 1].copy()
+    side = 1 << bits
+    d = np.zeros(q.shape[0], dtype=np.int64)
+    s = side >> 1
+    while s > 0:
+        rx = ((x & s) > 0).astype(np.int64)
+        ry = ((y & s) > 0).astype(np.int64)
+        d += s * s * ((3 * rx) ^ ry)
+        flip = (ry == 0) & (rx == 1)
+        x = np.where(flip, side - 1 - x, x)
+        y = np.where(flip, side - 1 - y, y)
+        swap = ry == 0
+        x, y = np.where(swap, y, x), np.where(swap, x, y)
+        s >>= 1
+    return np.argsort(d, kind="stable")

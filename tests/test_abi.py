@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every declared entry point."""
+
+import ctypes as C
+
+import pytest
+
+from paper_2609_24722_b300 import _lib as L
+from paper_2609_24722_b300 import build as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def test_exports_every_declared_function(lib):
+    names = L.declared_functions()
+    assert {"tc_energy", "tc_grad", "tc_subdomain_delta_energy", "tc_relax_subdomains",
+            "tc_project_disk"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header(lib):
+    # tc_relax_params: 4 int32, 6 double, 2 int32, 1 double, 2 int32 -> 88 bytes
+    assert C.sizeof(L.RelaxParams) == 88
+    assert L.RelaxParams.step0.offset == 16 and L.RelaxParams.polish_steps.offset == 64
+    assert L.RelaxParams.want_energy.offset == 80
+    assert L.RESULT_BYTES == 32
+    assert C.sizeof(L.RelaxProfile) == 56
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        s = lib.tc_status_string(code)
+        assert isinstance(s, bytes) and len(s) > 0
+    assert lib.tc_status_string(0) == b"ok"
+
+
+def test_argument_errors_are_synchronous_without_touching_a_device(lib):
+    # invalid arguments are rejected on the host before any CUDA call
+    assert lib.tc_energy(None, 10, 0, None, None, None) == 1
+    assert lib.tc_grad(None, 10, 0, None, None, None) == 1
+    assert lib.tc_project_disk(None, 10, 1.0, None, None) == 1
+    assert lib.tc_project_disk(None, 0, -1.0, None, None) == 1
+    prm = L.RelaxParams(precision=7)
+    assert lib.tc_relax_subdomains(None, 10, None, None, 1, None, None, C.byref(prm), None, None) == 1
+
+
+def test_stream_k_owner_formula():
+    """owner(u) = ceil(G (u+1) / W) - 1 is the CTA whose range [floor(W k/G), floor(W (k+1)/G)) holds u."""
+    for W in [1, 2, 7, 100, 391, 1000, 76636]:
+        for G in [1, 2, 3, 148, 296, 592, 1184]:
+            if G > W:
+                continue
+            b = [(W * k) // G for k in range(G + 1)]
+            k = 0
+            for u in range(0, W, max(1, W // 997)):
+                while not (b[k] <= u < b[k + 1]):
+                    k += 1 if b[k + 1] <= u else -1
+                assert (G * (u + 1) + W - 1) // W - 1 == k

@@ -61,3 +61,17 @@ def test_instances():
     assert sizes.min() >= 100 and sizes.max() <= 500
     assert pos.shape == (off[-1], 2)
     np.testing.assert_array_equal(pos[off[2]:off[3]], synth.arcsine_disk(int(sizes[2]), 3 + 1 + 2))
+
+
+def test_zorder_is_a_spatially_local_permutation():
+    pos = synth.arcsine_disk(50000, 4)
+    o = synth.zorder(pos)
+    assert np.array_equal(np.sort(o), np.arange(pos.shape[0]))
+    p = pos[o]
+    # consecutive charges in Z-order are far closer than consecutive charges in random order
+    step_z = np.linalg.norm(np.diff(p, axis=0), axis=1).mean()
+    step_r = np.linalg.norm(np.diff(pos, axis=0), axis=1).mean()
+    assert step_z < 0.05 * step_r
+    # blocks of 512 consecutive charges are compact
+    ext = max(np.ptp(p[k:k + 512], axis=0).max() for k in range(0, 50000 - 512, 512))
+    assert ext < 0.6
