@@ -176,6 +176,27 @@ tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const 
                               int32_t n_sub, const int64_t* world, const uint8_t* flags,
                               const tc_relax_params* prm, tc_subdomain_result* out, tc_stream stream);
 
+/* Total energy (and local energies) exactly as tc_energy computes them, but
+ * without allocating any device memory.  The paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc: code that runs
+ * while a CUDA graph is being captured or inside a host callback, processes
+ * whose device memory is handed out by a framework's own pool, and real-time
+ * hosts that forbid allocation (and its implicit synchronisation) after
+ * start-up.
+ *   pos [2n], energy [1], local_e [n] (nullable): as for tc_energy.
+ *   n <= 200 000; larger n returns TC_ERR_INVALID_ARG (tc_last_error() says why).
+ * Scratch: one fixed 16 MiB array in the library's device image, present on
+ * every GPU that loads libtc until the process exits.  Every call shares it,
+ * so calls that overlap on the GPU (other streams, other host threads) race:
+ * the caller must order them.  Each call clears the part that must start at
+ * zero.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Device-side errors (coincident charges,
+ * non-finite values, charges outside the disk) make *energy NaN; they are not
+ * recorded in the status word that tc_sync_status() reads. */
+tc_status tc_energy_noalloc(const double* pos, int64_t n, tc_precision prec, double* energy,
+                            double* local_e, tc_stream stream);
+
 /* Launch timings of the calling thread's last tc_relax_subdomains call made
  * with prm->profile = 1 (measurement utility; the paper has no counterpart).
  * Times are CUDA-event intervals on the launching stream, in milliseconds. */

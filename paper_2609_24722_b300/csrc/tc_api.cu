@@ -33,6 +33,11 @@ tc_status cuda_fail(cudaError_t e, const char* where)
     return TC_ERR_CUDA;
 }
 
+void set_last_error(const char* msg)
+{
+    g_last_error = msg;
+}
+
 void* workspace(cudaStream_t s, size_t bytes, tc_status* err)
 {
     int dev = 0;

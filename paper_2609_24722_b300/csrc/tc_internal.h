@@ -30,6 +30,9 @@ tc_status cuda_fail(cudaError_t e, const char* where);
 
 inline tc_status cuda_status(cudaError_t e, const char* where = "CUDA call") { return cuda_fail(e, where); }
 
+// Set the text tc_last_error() returns for this host thread.
+void set_last_error(const char* msg);
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // The first kCounterBytes of every workspace hold zero-initialised counters
