@@ -53,12 +53,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-instances", action="store_true", help="skip the batched-instances (C5) section")
     # a single small kernel case (used for profiler captures): no JSON bench line
     ap.add_argument("--case", choices=["allpairs", "relax"], default=None)
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--nsub", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--config", type=int, default=None, help="mixed pass launch shape (tc_set_pass_config)")
     return ap.parse_args()
 
 
@@ -70,6 +72,10 @@ def run_case(args):
     import paper_2609_24722_b300 as tc
 
     dev = torch.device("cuda", 0)
+    if args.config is not None:
+        from paper_2609_24722_b300 import _lib
+
+        _lib.check(_lib.lib().tc_set_pass_config(_lib.TC_MIXED, args.config), "tc_set_pass_config")
     if args.case == "allpairs":
         pa = synth.arcsine_disk(args.n, 0)
         p = torch.tensor(pa[synth.zorder(pa)], device=dev)
@@ -193,6 +199,69 @@ def cpu_baseline(pos, idx, off, seconds: float = 12.0) -> dict:
     return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"float64 gradient + energy rows of the first {n_rows} subdomain charges against all "
                       f"{N} charges (tco_rows_grad, single thread, Neumaier sums), {dt:.1f} s"}
+
+
+def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
+                  polish: int = 100, fp64_steps: int = 20):
+    """Config C5: 512 independent instances (N_k ~ U{100..5000}, arcsine init each), relaxed in one
+    batched call per round (mixed L-BFGS, memory 8, then float64 polish), 3 perturbation restarts
+    (Gaussian kicks of 0.05 x the instance's lattice spacing) keeping each instance's best energy;
+    then the same instances with float64 pair terms for a few steps (throughput side by side)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    import paper_2609_24722_b300 as tc
+
+    pos_np, off = synth.instances(n_inst, 100, 5000, seed)
+    sizes = np.diff(off)
+    world = torch.tensor(np.stack([off[:-1], off[1:]], 1), device=dev)
+    h = np.sqrt(2 * math.pi / (math.sqrt(3.0) * sizes))
+    sig = np.repeat(0.05 * h, sizes)
+    best = pos_np.copy()
+    best_e = np.full(n_inst, np.inf)
+    kw = dict(precision="mixed", optimizer="lbfgs", n_steps=steps, memory=8, step0=1e-5,
+              maxstep=0.1 * float(h.min()), polish_steps=polish, polish_gtol=0.0, accept=False,
+              want_energy=True)
+    ms_total, pairs_total, launches = 0.0, 0, 0
+    for r in range(rounds):
+        start = pos_np if r == 0 else synth.jitter_inside(best, sig, seed + 100 + r)
+        p = torch.tensor(start, device=dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        res = tc.relax_subdomains(p, world=world, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        tc.sync_status()
+        ms_total += a.elapsed_time(b)
+        pairs_total += int((sizes * (sizes - 1)).sum()) * (steps + polish)
+        e = res.energy.cpu().numpy()
+        x = p.cpu().numpy()
+        better = e < best_e
+        for k in np.flatnonzero(better):
+            best[off[k]:off[k + 1]] = x[off[k]:off[k + 1]]
+        best_e = np.where(better, e, best_e)
+    # the float64-polished energies against the oracle's evaluation of the same configurations
+    check = [0, int(np.argmax(sizes)), n_inst - 1]
+    parity = max(abs(best_e[k] - oracle.energy(best[off[k]:off[k + 1]])) / best_e[k] for k in check)
+    # float64 pair terms, same instances, a few steps
+    p = torch.tensor(pos_np, device=dev)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    tc.relax_subdomains(p, world=world, **{**kw, "precision": "fp64", "n_steps": fp64_steps, "polish_steps": 0})
+    b.record()
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b)
+    pairs64 = int((sizes * (sizes - 1)).sum()) * fp64_steps
+    return {"workload": f"{n_inst} instances, N_k~U[100,5000] (sum {int(sizes.sum())}), arcsine init, "
+                        f"{rounds - 1} kick restarts, mixed L-BFGS(8) {steps} steps + fp64 polish {polish}",
+            "relax_time_s": ms_total / 1e3, "pairs_per_s_mixed_with_polish": pairs_total / (ms_total / 1e3),
+            "pairs_per_s_fp64": pairs64 / (ms64 / 1e3), "fp64_steps": fp64_steps,
+            "best_energy_sum": float(best_e.sum()),
+            "fp64_energy_vs_oracle_max_rel": parity}
 
 
 def run_reference(args):
@@ -346,6 +415,7 @@ def main():
 
     ms_mixed = time_allpairs("mixed", 5)
     ms_f64 = time_allpairs("fp64", 3)
+    c5 = run_instances(dev) if not args.no_instances else None
     pipes = tc.probe_pipes()
     tc.sync_status()
 
@@ -381,6 +451,7 @@ def main():
         "accepted_subdomains": accepted[-1],
         "allpairs_n1e5": {"mixed_pairs_per_s": N * (N - 1) / (ms_mixed / 1e3), "mixed_ms": ms_mixed,
                           "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64},
+        "instances_c5": c5,
         "e2e": {"value": world * pairs_step / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": args.steps * (prof["launches"] + 3),

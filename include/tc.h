@@ -59,6 +59,17 @@ typedef enum {
                      in float32, cross-tile sums double-float, rows combined in float64 */
 } tc_precision;
 
+/* Launch shapes of the pair passes (tuning; the paper has no counterpart).
+ * Every shape computes the same sums in the same order: a row block of 512
+ * charges against tiles of 256 sources; shapes differ in CTA size and rows
+ * per thread.  tc_pass_config_count(prec) shapes exist (0 .. count-1);
+ * tc_set_pass_config selects one for every later call in this process
+ * (TC_ERR_INVALID_ARG for an unknown shape); the default is 0.  An autotuner
+ * (paper_2609_24722_b300/autotune.py) times the shapes and picks one. */
+int32_t tc_pass_config_count(tc_precision prec);
+tc_status tc_set_pass_config(tc_precision prec, int32_t config);
+int32_t tc_get_pass_config(tc_precision prec);
+
 /* Human-readable name of a status code (static storage). */
 const char* tc_status_string(tc_status s);
 
@@ -216,8 +227,11 @@ tc_status tc_relax_last_profile(tc_relax_profile* out);
 /* Measurement utility (the paper has no counterpart): achieved throughput of
  * the instruction pipes that bound the pair kernels, measured with long
  * chains of independent instructions on every SM of the current device.
- *   rates [3] HOST array, written: float32 FFMA lane operations/s,
- *             float64 DFMA operations/s, MUFU.RSQ operations/s.
+ *   rates [4] HOST array, written: float32 FFMA lane operations/s,
+ *             float64 DFMA operations/s, MUFU.RSQ operations/s, and ordered
+ *             pairs/s of the far-tile pair instruction mix (packed float32
+ *             differences, r^2, two MUFU.RSQ, r^-3, gradient fmas) run from
+ *             registers with no memory traffic.
  * Synchronous; allocates and frees a 64-byte scratch buffer. */
 tc_status tc_probe_pipes(double* rates, tc_stream stream);
 

@@ -166,9 +166,9 @@ def relax_last_profile() -> dict:
 
 def probe_pipes() -> dict:
     """Measured FFMA lane-ops/s, DFMA ops/s and MUFU.RSQ ops/s of the current device."""
-    rates = (C.c_double * 3)()
+    rates = (C.c_double * 4)()
     L.check(L.lib().tc_probe_pipes(C.cast(rates, C.c_void_p), _stream()), "tc_probe_pipes")
-    return {"ffma_per_s": rates[0], "dfma_per_s": rates[1], "mufu_per_s": rates[2]}
+    return {"ffma_per_s": rates[0], "dfma_per_s": rates[1], "mufu_per_s": rates[2], "pairmix_per_s": rates[3]}
 
 
 class CoulombEnergy(torch.autograd.Function):

@@ -92,6 +92,9 @@ def _lib() -> C.CDLL:
             "tc_project_disk": ([vp, i64, d, vp, vp], C.c_int),
             "tc_status_string": ([C.c_int], C.c_char_p),
             "tc_last_error": ([], C.c_char_p),
+            "tc_pass_config_count": ([i32], C.c_int32),
+            "tc_set_pass_config": ([i32, i32], C.c_int),
+            "tc_get_pass_config": ([i32], C.c_int32),
             "tc_sync_status": ([vp], C.c_int),
             "tc_shutdown": ([], None),
             "tc_probe_pipes": ([vp, vp], C.c_int),

@@ -5,9 +5,12 @@
 #include <string>
 #include <utility>
 
-#include "tc_internal.h"
+#include "tc_plan.cuh"
 
 namespace tc {
+
+int g_mixed_config = 0;
+
 namespace {
 
 struct Block {
@@ -139,6 +142,26 @@ const char* tc_status_string(tc_status s)
         case TC_ERR_NO_MEMORY: return "out of device memory";
     }
     return "unknown status";
+}
+
+int32_t tc_pass_config_count(tc_precision prec)
+{
+    return prec == TC_MIXED ? tc::kMixedConfigs : (prec == TC_FP64 ? 1 : 0);
+}
+
+tc_status tc_set_pass_config(tc_precision prec, int32_t config)
+{
+    if (prec == TC_MIXED && config >= 0 && config < tc::kMixedConfigs) {
+        tc::g_mixed_config = config;
+        return TC_OK;
+    }
+    if (prec == TC_FP64 && config == 0) return TC_OK;
+    return TC_ERR_INVALID_ARG;
+}
+
+int32_t tc_get_pass_config(tc_precision prec)
+{
+    return prec == TC_MIXED ? tc::g_mixed_config : 0;
 }
 
 const char* tc_last_error(void)

@@ -65,9 +65,22 @@ template <int R> struct MixedRows {
 
     // One tile of T sources.  hi[j] = (-x_hi, -x_hi, -y_hi, -y_hi), lo[j] the
     // same for the lo parts.  Accumulates sum dx r^-3 (= -grad) and sum 1/r.
-    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G>
+    // SCALAR_TAIL: the work after the two MUFU.RSQ results (r^-3 and the two
+    // gradient fmas) runs as scalar float32 per lane instead of packed pairs,
+    // so the two results never have to be gathered into one register pair.
+    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G, bool SCALAR_TAIL>
     __device__ __forceinline__ void tile(const float4* __restrict__ hi, const float4* __restrict__ lo,
                                          const int (&jself)[R], float escale)
+    {
+        if constexpr (SCALAR_TAIL)
+            tile_scalar_tail<T, NEAR, SELF, WANT_E, WANT_G>(hi, lo, jself, escale);
+        else
+            tile_packed<T, NEAR, SELF, WANT_E, WANT_G>(hi, lo, jself, escale);
+    }
+
+    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G>
+    __device__ __forceinline__ void tile_packed(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                                                const int (&jself)[R], float escale)
     {
         float2 et[P], gxt[P], gyt[P];
 #pragma unroll
@@ -116,6 +129,57 @@ template <int R> struct MixedRows {
                 df_add(gxh[2 * p + 1], gxl[2 * p + 1], -gxt[p].y);
                 df_add(gyh[2 * p], gyl[2 * p], -gyt[p].x);
                 df_add(gyh[2 * p + 1], gyl[2 * p + 1], -gyt[p].y);
+            }
+        }
+    }
+
+    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G>
+    __device__ __forceinline__ void tile_scalar_tail(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                                                     const int (&jself)[R], float escale)
+    {
+        float et[R], gxt[R], gyt[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) et[r] = gxt[r] = gyt[r] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < T; ++j) {
+            const float4 h = hi[j];
+            const float2 qx = make_float2(h.x, h.y), qy = make_float2(h.z, h.w);
+            float2 lx, ly;
+            if (NEAR) {
+                const float4 l = lo[j];
+                lx = make_float2(l.x, l.y);
+                ly = make_float2(l.z, l.w);
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float2 dx = __fadd2_rn(xh[p], qx);
+                float2 dy = __fadd2_rn(yh[p], qy);
+                if (NEAR) {
+                    dx = __fadd2_rn(dx, __fadd2_rn(xl[p], lx));
+                    dy = __fadd2_rn(dy, __fadd2_rn(yl[p], ly));
+                }
+                const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                const float d0[2] = {dx.x, dx.y}, e0[2] = {dy.x, dy.y}, q0[2] = {r2.x, r2.y};
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int r = 2 * p + h2;
+                    float inv = rsqrt_mufu(q0[h2]);
+                    if (SELF) inv = (j == jself[r]) ? 0.f : inv;
+                    if (WANT_E) et[r] += inv;
+                    if (WANT_G) {
+                        const float inv3 = inv * inv * inv;
+                        gxt[r] = fmaf(d0[h2], inv3, gxt[r]);
+                        gyt[r] = fmaf(e0[h2], inv3, gyt[r]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (WANT_E) df_add(eh[r], el[r], et[r] * escale);
+            if (WANT_G) {
+                df_add(gxh[r], gxl[r], -gxt[r]);
+                df_add(gyh[r], gyl[r], -gyt[r]);
             }
         }
     }
@@ -173,10 +237,15 @@ __device__ __forceinline__ bool boxes_far(float4 a, float4 b)
     return gx * gx + gy * gy >= kFarDist * kFarDist;
 }
 
-template <int R, int THREADS, bool WANT_E, bool WANT_G>
-__global__ void __launch_bounds__(THREADS) k_pass_mixed(PassArgs a, int64_t u_base, int64_t row_sub)
+// The mixed pass kernel.  THREADS threads per CTA, R rows per thread (row
+// block RB = THREADS * R), tiles of T sources (T / THREADS staged per thread);
+// MINB: resident CTAs per SM the register allocation must allow; ST: scalar
+// tail (see MixedRows::tile).
+template <int R, int THREADS, int T, int MINB, bool ST, bool WANT_E, bool WANT_G>
+__global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_t u_base, int64_t row_sub)
 {
-    constexpr int T = THREADS;
+    static_assert(T % THREADS == 0, "each thread stages a whole number of sources");
+    constexpr int S = T / THREADS;
     constexpr int RB = THREADS * R;
     constexpr int NW = THREADS / 32;
     __shared__ float4 shi[2][T];
@@ -191,12 +260,27 @@ __global__ void __launch_bounds__(THREADS) k_pass_mixed(PassArgs a, int64_t u_ba
     const int64_t u_end = sk_begin(a.W, G, k + 1);
 
     MixedRows<R> rs;
-    // stage one source into buffer b (negated hi/lo lanes) and its warp's box
-    auto stage = [&](int b, float4 q, bool valid) {
-        shi[b][tid] = make_float4(-q.x, -q.x, -q.y, -q.y);
-        slo[b][tid] = make_float4(-q.z, -q.z, -q.w, -q.w);
-        float4 bx = valid ? make_float4(q.x, q.y, q.x, q.y)
-                          : make_float4(kBoxEmptyLo, kBoxEmptyLo, kBoxEmptyHi, kBoxEmptyHi);
+    float4 pre[S];
+    bool valid[S];
+    // fetch tile t's S sources of this thread (positions tid + c * THREADS)
+    auto fetch = [&](const Prob& p, int t) {
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            bool v;
+            pre[c] = load_src_mixed<T>(a, p, t, tid + c * THREADS, v);
+            valid[c] = v;
+        }
+    };
+    // stage them into buffer b (negated hi/lo lanes) with the warp's box
+    auto stage = [&](int b) {
+        float4 bx = make_float4(kBoxEmptyLo, kBoxEmptyLo, kBoxEmptyHi, kBoxEmptyHi);
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            const float4 q = pre[c];
+            shi[b][tid + c * THREADS] = make_float4(-q.x, -q.x, -q.y, -q.y);
+            slo[b][tid + c * THREADS] = make_float4(-q.z, -q.z, -q.w, -q.w);
+            if (valid[c]) bx = box_union(bx, make_float4(q.x, q.y, q.x, q.y));
+        }
         bx = warp_box(bx);
         if (lane == 0) swbox[b][warp] = bx;
     };
@@ -213,16 +297,15 @@ __global__ void __launch_bounds__(THREADS) k_pass_mixed(PassArgs a, int64_t u_ba
             const int64_t rl0 = (int64_t)rb * RB + tid;
             float4 rbox = warp_box(rs.load(static_cast<const float4*>(a.rows), p.row_base, rl0, THREADS, p.m));
             if (lane == 0) srbox[warp] = rbox;
-            bool valid;
-            float4 pre = load_src_mixed<T>(a, p, t0, tid, valid);
-            stage(0, pre, valid);
+            fetch(p, t0);
+            stage(0);
             __syncthreads();
             rbox = srbox[0];
 #pragma unroll
             for (int w = 1; w < NW; ++w) rbox = box_union(rbox, srbox[w]);
             for (int t = t0; t < t1; ++t) {
                 const int buf = (t - t0) & 1;
-                if (t + 1 < t1) pre = load_src_mixed<T>(a, p, t + 1, tid, valid);
+                if (t + 1 < t1) fetch(p, t + 1);
                 float4 tbox = swbox[buf][0];
 #pragma unroll
                 for (int w = 1; w < NW; ++w) tbox = box_union(tbox, swbox[buf][w]);
@@ -234,12 +317,12 @@ __global__ void __launch_bounds__(THREADS) k_pass_mixed(PassArgs a, int64_t u_ba
                 for (int r = 0; r < R; ++r) jself[r] = (int)(rl0 + r * THREADS) - tp * T;
                 const float sc = own ? 0.5f : 1.0f;
                 if (self)
-                    rs.template tile<T, true, true, WANT_E, WANT_G>(shi[buf], slo[buf], jself, sc);
+                    rs.template tile<T, true, true, WANT_E, WANT_G, ST>(shi[buf], slo[buf], jself, sc);
                 else if (!boxes_far(rbox, tbox))
-                    rs.template tile<T, true, false, WANT_E, WANT_G>(shi[buf], slo[buf], jself, sc);
+                    rs.template tile<T, true, false, WANT_E, WANT_G, ST>(shi[buf], slo[buf], jself, sc);
                 else
-                    rs.template tile<T, false, false, WANT_E, WANT_G>(shi[buf], slo[buf], jself, sc);
-                if (t + 1 < t1) stage(buf ^ 1, pre, valid);
+                    rs.template tile<T, false, false, WANT_E, WANT_G, ST>(shi[buf], slo[buf], jself, sc);
+                if (t + 1 < t1) stage(buf ^ 1);
                 __syncthreads();
             }
             const int64_t slot = k - sk_owner(p.unit_off + (int64_t)rb * n_t - u_base, a.W, G);

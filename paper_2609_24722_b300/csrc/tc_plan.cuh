@@ -61,7 +61,10 @@ inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last
 template <class K> inline int64_t grid_for(K kernel, int64_t W)
 {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess || occ < 1) occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
     int64_t g = (int64_t)sm_count() * occ;
     return std::max<int64_t>(1, std::min<int64_t>(g, W));
 }
@@ -128,27 +131,59 @@ __device__ __forceinline__ double2 wall_grad(double2 x, double2 g, double radius
 
 // ------------------------------------------------------ pass launching ---
 
-// The float32 pass has its own kernel (packed FP32x2, near/far tiles); the
-// float64 and energy-change passes share k_pass.
-template <int KIND, bool WANT_E, bool WANT_G> inline auto pass_kernel()
+// Launch shapes of the float32 pass.  All keep the row block at kRB = 512
+// rows and the tile at kT = 256 sources, so one plan serves every shape; they
+// differ in threads per CTA and rows per thread (register blocking).
+constexpr int kMixedConfigs = 6;
+extern int g_mixed_config;  // chosen shape (tc_set_pass_config); 0 by default
+
+template <bool WANT_E, bool WANT_G> struct MixedShape {
+    using fn_t = void (*)(PassArgs, int64_t, int64_t);
+    // (rows per thread, threads per CTA, minimum resident CTAs per SM, scalar tail)
+    static fn_t kernel(int c, int* threads)
+    {
+        switch (c) {
+            case 1: *threads = 256; return k_pass_mixed<2, 256, kT, 3, true, WANT_E, WANT_G>;
+            case 2: *threads = 128; return k_pass_mixed<4, 128, kT, 3, false, WANT_E, WANT_G>;
+            case 3: *threads = 128; return k_pass_mixed<4, 128, kT, 3, true, WANT_E, WANT_G>;
+            case 4: *threads = 256; return k_pass_mixed<2, 256, kT, 4, true, WANT_E, WANT_G>;
+            case 5: *threads = 128; return k_pass_mixed<4, 128, kT, 4, true, WANT_E, WANT_G>;
+            default: *threads = 256; return k_pass_mixed<2, 256, kT, 3, false, WANT_E, WANT_G>;
+        }
+    }
+};
+
+template <int KIND, bool WANT_E, bool WANT_G> inline auto pass_kernel(int* threads)
 {
-    if constexpr (KIND == PASS_MIXED)
-        return k_pass_mixed<kR, kThreads, WANT_E, WANT_G>;
-    else
+    if constexpr (KIND == PASS_MIXED) {
+        return MixedShape<WANT_E, WANT_G>::kernel(g_mixed_config, threads);
+    } else {
+        *threads = kThreads;
         return k_pass<KIND, kR, kThreads, WANT_E, WANT_G>;
+    }
 }
 
 template <int KIND, bool WANT_E, bool WANT_G>
 inline cudaError_t launch_pass(const PassArgs& a, int64_t G, int64_t u_base, int64_t row_sub, cudaStream_t s)
 {
     if (a.W <= 0) return cudaSuccess;
-    pass_kernel<KIND, WANT_E, WANT_G>()<<<(unsigned)G, kThreads, 0, s>>>(a, u_base, row_sub);
+    int threads = 0;
+    auto fn = pass_kernel<KIND, WANT_E, WANT_G>(&threads);
+    fn<<<(unsigned)G, threads, 0, s>>>(a, u_base, row_sub);
     return cudaGetLastError();
 }
 
 template <int KIND, bool WANT_E, bool WANT_G> inline int64_t pass_grid(int64_t W)
 {
-    return grid_for(pass_kernel<KIND, WANT_E, WANT_G>(), W);
+    int threads = 0;
+    auto fn = pass_kernel<KIND, WANT_E, WANT_G>(&threads);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    int64_t g = (int64_t)sm_count() * occ;
+    return std::max<int64_t>(1, std::min<int64_t>(g, W));
 }
 
 }  // namespace tc

@@ -109,6 +109,38 @@ def test_mixed_sorted_input_uses_far_tiles_within_tolerance(n, seed):
     np.testing.assert_allclose(loc.cpu().numpy()[rows], 0.5 * eo_rows, rtol=1e-6)
 
 
+def test_every_mixed_launch_shape_gives_identical_results():
+    """Launch shapes only change the CTA size and register blocking, never a sum's order."""
+    lib = L.lib()
+    n = 9000
+    pos = synth.lattice_disk(n, 3)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    subs = synth.subdomains(pos, 6, 100, 900, 4)
+    idx, off = synth.to_csr(subs)
+    eta = 1e-4 / n
+    old = lib.tc_get_pass_config(1)
+    outs = []
+    try:
+        for cfg in range(lib.tc_pass_config_count(1)):
+            assert lib.tc_set_pass_config(1, cfg) == 0
+            p = T(pos)
+            g, e = tc.grad(p, "mixed", with_energy=True)
+            q = T(pos.copy())
+            tc.relax_subdomains(q, T(idx), T(off), precision="mixed", optimizer="bb", n_steps=5, step0=eta,
+                                alpha_min=0.0, alpha_max=10 * eta, accept=True)
+            tc.sync_status()
+            outs.append((g.cpu().numpy(), e.item(), q.cpu().numpy()))
+    finally:
+        lib.tc_set_pass_config(1, old)
+    assert lib.tc_set_pass_config(1, 99) == 1
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        assert o[1] == outs[0][1]
+        np.testing.assert_array_equal(o[2], outs[0][2])
+    go = oracle.grad(pos)
+    assert np.linalg.norm(outs[0][0] - go) <= 1e-5 * np.linalg.norm(go)
+
+
 @pytest.mark.parametrize("n", [3, 10, 100, 1000])
 def test_ngon_on_gpu(n):
     import mpmath as mp
