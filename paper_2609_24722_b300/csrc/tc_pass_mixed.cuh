@@ -27,22 +27,25 @@ namespace tc {
 constexpr float kFarDist = 0.02f;
 constexpr float kBoxEmptyLo = 3.0e38f, kBoxEmptyHi = -3.0e38f;
 
-// Packed rows of one thread: R rows as R/2 float2 pairs.
+// Packed rows of one thread: R rows as R/2 float2 pairs of hi parts in
+// registers; their lo parts and the cross-tile accumulators stay in shared
+// memory (per-thread slots) so the tile loop keeps few registers live.
 template <int R> struct MixedRows {
     static_assert(R % 2 == 0, "rows come in pairs");
     static constexpr int P = R / 2;
-    float2 xh[P], yh[P], xl[P], yl[P];
-    float eh[R], el[R], gxh[R], gxl[R], gyh[R], gyl[R];
+    float2 xh[P], yh[P];
 
-    // Loads rows rl0 + r*stride (r < R); rows past m sit far away.  Returns
-    // the bounding box (xmin, ymin, xmax, ymax) of the valid rows' hi parts.
-    __device__ float4 load(const float4* rows, int64_t base, int64_t rl0, int stride, int m)
+    // Loads rows rl0 + r*stride (r < R); rows past m sit far away.  lo parts go
+    // to lo2[2P][stride] (x pairs then y pairs), accumulators acc[6R][stride]
+    // are zeroed.  Returns the box (xmin, ymin, xmax, ymax) of the valid rows.
+    __device__ float4 load(const float4* rows, int64_t base, int64_t rl0, int stride, int m, float2* lo2, float* acc,
+                           int tid)
     {
-        float4 box = make_float4(kBoxEmptyLo, kBoxEmptyLo, kBoxEmptyHi, kBoxEmptyHi);
+        float4 box = make_float4(3.0e38f, 3.0e38f, -3.0e38f, -3.0e38f);
         float4 q[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            int64_t rl = rl0 + (int64_t)r * stride;
+            const int64_t rl = rl0 + (int64_t)r * stride;
             const bool ok = rl < m;
             q[r] = ok ? rows[base + rl] : make_float4(kFarRow32, kFarRow32, 0.f, 0.f);
             if (ok) {
@@ -51,41 +54,37 @@ template <int R> struct MixedRows {
                 box.z = fmaxf(box.z, q[r].x);
                 box.w = fmaxf(box.w, q[r].y);
             }
-            eh[r] = el[r] = gxh[r] = gxl[r] = gyh[r] = gyl[r] = 0.f;
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             xh[p] = make_float2(q[2 * p].x, q[2 * p + 1].x);
             yh[p] = make_float2(q[2 * p].y, q[2 * p + 1].y);
-            xl[p] = make_float2(q[2 * p].z, q[2 * p + 1].z);
-            yl[p] = make_float2(q[2 * p].w, q[2 * p + 1].w);
+            lo2[p * stride + tid] = make_float2(q[2 * p].z, q[2 * p + 1].z);
+            lo2[(P + p) * stride + tid] = make_float2(q[2 * p].w, q[2 * p + 1].w);
         }
+#pragma unroll
+        for (int c = 0; c < 6 * R; ++c) acc[c * stride + tid] = 0.f;
         return box;
     }
 
     // One tile of T sources.  hi[j] = (-x_hi, -x_hi, -y_hi, -y_hi), lo[j] the
-    // same for the lo parts.  Accumulates sum dx r^-3 (= -grad) and sum 1/r.
-    // SCALAR_TAIL: the work after the two MUFU.RSQ results (r^-3 and the two
-    // gradient fmas) runs as scalar float32 per lane instead of packed pairs,
-    // so the two results never have to be gathered into one register pair.
-    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G, bool SCALAR_TAIL>
-    __device__ __forceinline__ void tile(const float4* __restrict__ hi, const float4* __restrict__ lo,
-                                         const int (&jself)[R], float escale)
-    {
-        if constexpr (SCALAR_TAIL)
-            tile_scalar_tail<T, NEAR, SELF, WANT_E, WANT_G>(hi, lo, jself, escale);
-        else
-            tile_packed<T, NEAR, SELF, WANT_E, WANT_G>(hi, lo, jself, escale);
-    }
-
+    // same for the lo parts.  The tile sums (sum dx r^-3 = -grad, sum 1/r) are
+    // folded into the shared accumulators acc[6R][stride] with TwoSum.
     template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G>
-    __device__ __forceinline__ void tile_packed(const float4* __restrict__ hi, const float4* __restrict__ lo,
-                                                const int (&jself)[R], float escale)
+    __device__ __forceinline__ void tile(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                                         const float2* lo2, float* acc, int stride, int tid, int jself0,
+                                         float escale)
     {
-        float2 et[P], gxt[P], gyt[P];
+        float2 et[P], gxt[P], gyt[P], xl[P], yl[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) et[p] = gxt[p] = gyt[p] = make_float2(0.f, 0.f);
-#pragma unroll 4
+        for (int p = 0; p < P; ++p) {
+            et[p] = gxt[p] = gyt[p] = make_float2(0.f, 0.f);
+            if (NEAR) {
+                xl[p] = lo2[p * stride + tid];
+                yl[p] = lo2[(P + p) * stride + tid];
+            }
+        }
+#pragma unroll 8
         for (int j = 0; j < T; ++j) {
             const float4 h = hi[j];
             const float2 qx = make_float2(h.x, h.y), qy = make_float2(h.z, h.w);
@@ -106,8 +105,9 @@ template <int R> struct MixedRows {
                 const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
                 float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
                 if (SELF) {
-                    inv.x = (j == jself[2 * p]) ? 0.f : inv.x;
-                    inv.y = (j == jself[2 * p + 1]) ? 0.f : inv.y;
+                    // row r of this thread is source jself0 + r * stride of this tile
+                    inv.x = (j == jself0 + (2 * p) * stride) ? 0.f : inv.x;
+                    inv.y = (j == jself0 + (2 * p + 1) * stride) ? 0.f : inv.y;
                 }
                 if (WANT_E) et[p] = __fadd2_rn(et[p], inv);
                 if (WANT_G) {
@@ -119,97 +119,32 @@ template <int R> struct MixedRows {
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            if (WANT_E) {
-                df_add(eh[2 * p], el[2 * p], et[p].x * escale);
-                df_add(eh[2 * p + 1], el[2 * p + 1], et[p].y * escale);
-            }
-            if (WANT_G) {
-                // the tile sums hold sum dx r^-3 = -dE/dx
-                df_add(gxh[2 * p], gxl[2 * p], -gxt[p].x);
-                df_add(gxh[2 * p + 1], gxl[2 * p + 1], -gxt[p].y);
-                df_add(gyh[2 * p], gyl[2 * p], -gyt[p].x);
-                df_add(gyh[2 * p + 1], gyl[2 * p + 1], -gyt[p].y);
-            }
-        }
-    }
-
-    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G>
-    __device__ __forceinline__ void tile_scalar_tail(const float4* __restrict__ hi, const float4* __restrict__ lo,
-                                                     const int (&jself)[R], float escale)
-    {
-        float et[R], gxt[R], gyt[R];
+            const float ev[2] = {et[p].x, et[p].y}, gxv[2] = {gxt[p].x, gxt[p].y}, gyv[2] = {gyt[p].x, gyt[p].y};
 #pragma unroll
-        for (int r = 0; r < R; ++r) et[r] = gxt[r] = gyt[r] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < T; ++j) {
-            const float4 h = hi[j];
-            const float2 qx = make_float2(h.x, h.y), qy = make_float2(h.z, h.w);
-            float2 lx, ly;
-            if (NEAR) {
-                const float4 l = lo[j];
-                lx = make_float2(l.x, l.y);
-                ly = make_float2(l.z, l.w);
-            }
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                float2 dx = __fadd2_rn(xh[p], qx);
-                float2 dy = __fadd2_rn(yh[p], qy);
-                if (NEAR) {
-                    dx = __fadd2_rn(dx, __fadd2_rn(xl[p], lx));
-                    dy = __fadd2_rn(dy, __fadd2_rn(yl[p], ly));
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int r = 2 * p + h2;
+                float* a = acc + tid;
+                if (WANT_E) {
+                    float hi_ = a[(6 * r + 0) * stride], lo_ = a[(6 * r + 1) * stride];
+                    df_add(hi_, lo_, ev[h2] * escale);
+                    a[(6 * r + 0) * stride] = hi_;
+                    a[(6 * r + 1) * stride] = lo_;
                 }
-                const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-                const float d0[2] = {dx.x, dx.y}, e0[2] = {dy.x, dy.y}, q0[2] = {r2.x, r2.y};
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int r = 2 * p + h2;
-                    float inv = rsqrt_mufu(q0[h2]);
-                    if (SELF) inv = (j == jself[r]) ? 0.f : inv;
-                    if (WANT_E) et[r] += inv;
-                    if (WANT_G) {
-                        const float inv3 = inv * inv * inv;
-                        gxt[r] = fmaf(d0[h2], inv3, gxt[r]);
-                        gyt[r] = fmaf(e0[h2], inv3, gyt[r]);
-                    }
+                if (WANT_G) {
+                    // the tile sums hold sum dx r^-3 = -dE/dx
+                    float gh = a[(6 * r + 2) * stride], gl = a[(6 * r + 3) * stride];
+                    df_add(gh, gl, -gxv[h2]);
+                    a[(6 * r + 2) * stride] = gh;
+                    a[(6 * r + 3) * stride] = gl;
+                    float yh_ = a[(6 * r + 4) * stride], yl_ = a[(6 * r + 5) * stride];
+                    df_add(yh_, yl_, -gyv[h2]);
+                    a[(6 * r + 4) * stride] = yh_;
+                    a[(6 * r + 5) * stride] = yl_;
                 }
             }
         }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (WANT_E) df_add(eh[r], el[r], et[r] * escale);
-            if (WANT_G) {
-                df_add(gxh[r], gxl[r], -gxt[r]);
-                df_add(gyh[r], gyl[r], -gyt[r]);
-            }
-        }
-    }
-
-    __device__ double e(int r) const { return (double)eh[r] + (double)el[r]; }
-    __device__ double2 g(int r) const
-    {
-        return make_double2((double)gxh[r] + (double)gxl[r], (double)gyh[r] + (double)gyl[r]);
     }
 };
-
-// Source entry (x_hi, y_hi, x_lo, y_lo) of tile t for thread tid; `valid`
-// tells whether it is a real, unmasked charge.
-template <int T>
-__device__ __forceinline__ float4 load_src_mixed(const PassArgs& a, const Prob& p, int t, int tid, bool& valid)
-{
-    if (t < p.n_t_snap) {
-        int64_t j = (int64_t)t * T + tid;
-        bool ok = j < p.snap_e - p.snap_b;
-        if (ok && p.mask_off >= 0) {
-            uint32_t w = a.mask[p.mask_off + (j >> 5)];
-            ok = ((w >> (j & 31)) & 1u) == 0u;
-        }
-        valid = ok;
-        return ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
-    }
-    int64_t j = (int64_t)(t - p.n_t_snap) * T + tid;
-    valid = j < p.m;
-    return valid ? static_cast<const float4*>(a.rows)[p.row_base + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
-}
 
 // Warp-level min/max of a box.
 __device__ __forceinline__ float4 warp_box(float4 b)
@@ -239,19 +174,27 @@ __device__ __forceinline__ bool boxes_far(float4 a, float4 b)
 
 // The mixed pass kernel.  THREADS threads per CTA, R rows per thread (row
 // block RB = THREADS * R), tiles of T sources (T / THREADS staged per thread);
-// MINB: resident CTAs per SM the register allocation must allow; ST: scalar
-// tail (see MixedRows::tile).
-template <int R, int THREADS, int T, int MINB, bool ST, bool WANT_E, bool WANT_G>
+// MINB: resident CTAs per SM the register allocation must allow.  The next
+// tile's sources arrive by cp.async in a landing buffer while the current tile
+// is computed; the problem record, boxes, lo parts and accumulators live in
+// shared memory.
+template <int R, int THREADS, int T, int MINB, bool WANT_E, bool WANT_G>
 __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_t u_base, int64_t row_sub)
 {
     static_assert(T % THREADS == 0, "each thread stages a whole number of sources");
     constexpr int S = T / THREADS;
     constexpr int RB = THREADS * R;
     constexpr int NW = THREADS / 32;
+    constexpr int P = R / 2;
     __shared__ float4 shi[2][T];
     __shared__ float4 slo[2][T];
+    __shared__ float4 sraw[T];
     __shared__ float4 swbox[2][NW];
     __shared__ float4 srbox[NW];
+    __shared__ float sacc[6 * R * THREADS];
+    __shared__ float2 slo2[2 * P * THREADS];
+    __shared__ Prob sprob;
+    __shared__ int sprob_s;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t G = gridDim.x;
@@ -260,83 +203,123 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
     const int64_t u_end = sk_begin(a.W, G, k + 1);
 
     MixedRows<R> rs;
-    float4 pre[S];
-    bool valid[S];
-    // fetch tile t's S sources of this thread (positions tid + c * THREADS)
-    auto fetch = [&](const Prob& p, int t) {
+    unsigned valid = 0;  // bit c: this thread's c-th staged source is a real charge
+    // start the copies of tile t's sources (positions tid + c * THREADS) into sraw
+    auto fetch = [&](int t) {
+        valid = 0;
 #pragma unroll
         for (int c = 0; c < S; ++c) {
-            bool v;
-            pre[c] = load_src_mixed<T>(a, p, t, tid + c * THREADS, v);
-            valid[c] = v;
+            const int jt = tid + c * THREADS;
+            const float4* src;
+            bool ok;
+            if (t < sprob.n_t_snap) {
+                const int64_t j = (int64_t)t * T + jt;
+                ok = j < sprob.snap_e - sprob.snap_b;
+                if (ok && sprob.mask_off >= 0) ok = ((a.mask[sprob.mask_off + (j >> 5)] >> (j & 31)) & 1u) == 0u;
+                src = static_cast<const float4*>(a.snap) + sprob.snap_b + j;
+            } else {
+                const int64_t j = (int64_t)(t - sprob.n_t_snap) * T + jt;
+                ok = j < sprob.m;
+                src = static_cast<const float4*>(a.rows) + sprob.row_base + j;
+            }
+            if (ok) {
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sraw[jt]);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+                valid |= 1u << c;
+            } else {
+                sraw[jt] = make_float4(kFar32, kFar32, 0.f, 0.f);
+            }
         }
+        asm volatile("cp.async.commit_group;\n" ::);
     };
-    // stage them into buffer b (negated hi/lo lanes) with the warp's box
+    // wait for them and stage into buffer b (negated hi/lo lanes) with the warp's box
     auto stage = [&](int b) {
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         float4 bx = make_float4(kBoxEmptyLo, kBoxEmptyLo, kBoxEmptyHi, kBoxEmptyHi);
 #pragma unroll
         for (int c = 0; c < S; ++c) {
-            const float4 q = pre[c];
-            shi[b][tid + c * THREADS] = make_float4(-q.x, -q.x, -q.y, -q.y);
-            slo[b][tid + c * THREADS] = make_float4(-q.z, -q.z, -q.w, -q.w);
-            if (valid[c]) bx = box_union(bx, make_float4(q.x, q.y, q.x, q.y));
+            const int jt = tid + c * THREADS;
+            const float4 q = sraw[jt];
+            shi[b][jt] = make_float4(-q.x, -q.x, -q.y, -q.y);
+            slo[b][jt] = make_float4(-q.z, -q.z, -q.w, -q.w);
+            if ((valid >> c) & 1u) bx = box_union(bx, make_float4(q.x, q.y, q.x, q.y));
         }
         bx = warp_box(bx);
         if (lane == 0) swbox[b][warp] = bx;
     };
     while (u < u_end) {
-        const int s = a.prob ? find_prob(a.prob, a.S, u_base + u) : 0;
-        const Prob p = a.prob ? a.prob[s] : a.single;
-        const int n_t = p.n_t_snap + p.n_t_priv;
-        const int64_t local = u_base + u - p.unit_off;
+        if (tid == 0) {
+            const int s = a.prob ? find_prob(a.prob, a.S, u_base + u) : 0;
+            sprob = a.prob ? a.prob[s] : a.single;
+            sprob_s = s;
+        }
+        __syncthreads();
+        const int n_t = sprob.n_t_snap + sprob.n_t_priv;
+        const int64_t local = u_base + u - sprob.unit_off;
         const int rb = (int)(local / n_t);
         const int t0 = (int)(local % n_t);
         const int t1 = (int)min((int64_t)n_t, (int64_t)t0 + (u_end - u));
-        const bool act = (a.active == nullptr) || (a.active[s] != 0);
+        const bool act = (a.active == nullptr) || (a.active[sprob_s] != 0);
         if (act) {
             const int64_t rl0 = (int64_t)rb * RB + tid;
-            float4 rbox = warp_box(rs.load(static_cast<const float4*>(a.rows), p.row_base, rl0, THREADS, p.m));
+            float4 rbox = warp_box(rs.load(static_cast<const float4*>(a.rows), sprob.row_base, rl0, THREADS, sprob.m,
+                                           slo2, sacc, tid));
             if (lane == 0) srbox[warp] = rbox;
-            fetch(p, t0);
+            fetch(t0);
             stage(0);
             __syncthreads();
-            rbox = srbox[0];
-#pragma unroll
-            for (int w = 1; w < NW; ++w) rbox = box_union(rbox, srbox[w]);
             for (int t = t0; t < t1; ++t) {
                 const int buf = (t - t0) & 1;
-                if (t + 1 < t1) fetch(p, t + 1);
-                float4 tbox = swbox[buf][0];
+                if (t + 1 < t1) fetch(t + 1);
+                float4 tbox = swbox[buf][0], rb4 = srbox[0];
 #pragma unroll
-                for (int w = 1; w < NW; ++w) tbox = box_union(tbox, swbox[buf][w]);
-                const bool own = t >= p.n_t_snap;
-                const int tp = t - p.n_t_snap;
+                for (int w = 1; w < NW; ++w) {
+                    tbox = box_union(tbox, swbox[buf][w]);
+                    rb4 = box_union(rb4, srbox[w]);
+                }
+                const bool own = t >= sprob.n_t_snap;
+                const int tp = t - sprob.n_t_snap;
                 const bool self = own && (rb * RB < tp * T + T) && (tp * T < rb * RB + RB);
-                int jself[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) jself[r] = (int)(rl0 + r * THREADS) - tp * T;
+                const int jself0 = (int)(rl0 - (int64_t)tp * T);
                 const float sc = own ? 0.5f : 1.0f;
-                if (self)
-                    rs.template tile<T, true, true, WANT_E, WANT_G, ST>(shi[buf], slo[buf], jself, sc);
-                else if (!boxes_far(rbox, tbox))
-                    rs.template tile<T, true, false, WANT_E, WANT_G, ST>(shi[buf], slo[buf], jself, sc);
-                else
-                    rs.template tile<T, false, false, WANT_E, WANT_G, ST>(shi[buf], slo[buf], jself, sc);
+                // each buffer gets its own copy of the tile loop, so the shared
+                // memory base is a compile-time address and every source load
+                // uses an immediate offset
+                const int kind = self ? 2 : (boxes_far(rb4, tbox) ? 0 : 1);
+                if (buf == 0) {
+                    if (kind == 0)
+                        rs.template tile<T, false, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
+                    else if (kind == 1)
+                        rs.template tile<T, true, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
+                    else
+                        rs.template tile<T, true, true, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
+                } else {
+                    if (kind == 0)
+                        rs.template tile<T, false, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
+                    else if (kind == 1)
+                        rs.template tile<T, true, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
+                    else
+                        rs.template tile<T, true, true, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
+                }
                 if (t + 1 < t1) stage(buf ^ 1);
                 __syncthreads();
             }
-            const int64_t slot = k - sk_owner(p.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
+            const int64_t slot = k - sk_owner(sprob.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int64_t rl = rl0 + (int64_t)r * THREADS;
-                if (rl < p.m) {
-                    const int64_t o = slot * a.M + p.row_base + rl - row_sub;
-                    if (WANT_E) a.part_e[o] = rs.e(r);
-                    if (WANT_G) a.part_g[o] = rs.g(r);
+                if (rl < sprob.m) {
+                    const int64_t o = slot * a.M + sprob.row_base + rl - row_sub;
+                    const float* ac = sacc + tid;
+                    if (WANT_E) a.part_e[o] = (double)ac[(6 * r + 0) * THREADS] + (double)ac[(6 * r + 1) * THREADS];
+                    if (WANT_G)
+                        a.part_g[o] = make_double2((double)ac[(6 * r + 2) * THREADS] + (double)ac[(6 * r + 3) * THREADS],
+                                                   (double)ac[(6 * r + 4) * THREADS] + (double)ac[(6 * r + 5) * THREADS]);
                 }
             }
         }
         u += t1 - t0;
+        __syncthreads();  // every thread is done with sprob before the next segment rewrites it
     }
 }
 

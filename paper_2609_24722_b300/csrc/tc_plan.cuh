@@ -139,16 +139,16 @@ extern int g_mixed_config;  // chosen shape (tc_set_pass_config); 0 by default
 
 template <bool WANT_E, bool WANT_G> struct MixedShape {
     using fn_t = void (*)(PassArgs, int64_t, int64_t);
-    // (rows per thread, threads per CTA, minimum resident CTAs per SM, scalar tail)
+    // (rows per thread, threads per CTA, minimum resident CTAs per SM)
     static fn_t kernel(int c, int* threads)
     {
         switch (c) {
-            case 1: *threads = 256; return k_pass_mixed<2, 256, kT, 3, true, WANT_E, WANT_G>;
-            case 2: *threads = 128; return k_pass_mixed<4, 128, kT, 3, false, WANT_E, WANT_G>;
-            case 3: *threads = 128; return k_pass_mixed<4, 128, kT, 3, true, WANT_E, WANT_G>;
-            case 4: *threads = 256; return k_pass_mixed<2, 256, kT, 4, true, WANT_E, WANT_G>;
-            case 5: *threads = 128; return k_pass_mixed<4, 128, kT, 4, true, WANT_E, WANT_G>;
-            default: *threads = 256; return k_pass_mixed<2, 256, kT, 3, false, WANT_E, WANT_G>;
+            case 1: *threads = 256; return k_pass_mixed<2, 256, kT, 4, WANT_E, WANT_G>;
+            case 2: *threads = 256; return k_pass_mixed<2, 256, kT, 6, WANT_E, WANT_G>;
+            case 3: *threads = 128; return k_pass_mixed<4, 128, kT, 4, WANT_E, WANT_G>;
+            case 4: *threads = 128; return k_pass_mixed<4, 128, kT, 6, WANT_E, WANT_G>;
+            case 5: *threads = 64; return k_pass_mixed<8, 64, kT, 6, WANT_E, WANT_G>;
+            default: *threads = 256; return k_pass_mixed<2, 256, kT, 3, WANT_E, WANT_G>;
         }
     }
 };

@@ -17,6 +17,10 @@ namespace tc {
 
 constexpr int kUpd = 256;   // update / reduction CTA size
 constexpr int kMaxMem = 16; // largest L-BFGS memory
+// Problems with more rows than this take the L-BFGS update as a sequence of
+// grid-wide launches instead of one CTA.
+constexpr int kLargeRows = 16384;
+constexpr int kLargeBlocks = 296;  // CTAs of the grid-wide update launches
 
 struct RelaxDev {
     const Prob* prob;
@@ -218,6 +222,7 @@ struct StepParams {
     int opt;
     int memory;
     double step0, alpha_min, alpha_max, maxstep, gtol, radius;
+    int measure;  // 1: only record the RMS stationarity of the current rows (no step)
 };
 
 // Projected gradient descent (fixed or Barzilai-Borwein step), one CTA per problem.
@@ -250,9 +255,9 @@ __global__ void __launch_bounds__(kUpd) k_update_gdbb(RelaxDev d, const double2*
     if (bad) set_status(d.st, ST_NONFINITE);
     block_sums(acc, sh);
     const double rms = sqrt(acc[0] / (double)max(p.m, 1));
-    if (sp.gtol > 0.0 && rms < sp.gtol) {
+    if (sp.measure || (sp.gtol > 0.0 && rms < sp.gtol)) {
         if (threadIdx.x == 0) {
-            d.active[s] = 0;
+            if (!sp.measure) d.active[s] = 0;
             d.rms[s] = rms;
         }
         return;
@@ -293,6 +298,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
     const int s = blockIdx.x;
     if (!d.active[s]) return;
     const Prob p = d.prob[s];
+    if (p.m > kLargeRows) return;  // updated by the grid-wide sequence below
     const int k = d.steps[s];
     const int mem = sp.memory;
     const int64_t M = d.M;
@@ -320,6 +326,10 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
     }
     if (bad) set_status(d.st, ST_NONFINITE);
     block_sums(acc, sh);
+    if (sp.measure) {
+        if (threadIdx.x == 0) d.rms[s] = sqrt(acc[0] / (double)max(p.m, 1));
+        return;
+    }
     int hist = d.hist[s], head = d.head[s];
     const bool keep = k > 0 && acc[1] > 1e-12 * sqrt(acc[2]) * sqrt(acc[3]);
     TC_ROWS(p)
@@ -453,6 +463,321 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
         d.hist[s] = hist;
         d.head[s] = head;
     }
+}
+
+// ------------------------------------------- L-BFGS for large problems ---
+// The same iteration as k_update_lbfgs, for one problem with many rows, as a
+// fixed sequence of grid-wide launches (host loops run to the memory size;
+// launches past the stored history return at once).  Every dot product is
+// written as per-block partials and added in block order by one CTA, so the
+// result does not depend on scheduling.  No launch waits on another CTA.
+
+struct LbScal {
+    double al[kMaxMem];  // two-loop alphas
+    double c;            // current second-loop coefficient
+    double gamma;        // H0 scale
+    double alpha;        // step scale
+    int keep, slot, done, reset;
+};
+
+struct LbArgs {
+    int s;
+    double* part;  // [kLargeBlocks][4]
+    LbScal* sc;
+};
+
+__device__ __forceinline__ int lb_slot(int head, int i, int mem) { return ((head - 1 - i) % mem + mem) % mem; }
+
+// block partial of up to 4 doubles into part[blockIdx.x][0..3]
+__device__ void lb_partial(double (&v)[4], double* part, double* sh)
+{
+    block_sums(v, sh);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) part[blockIdx.x * 4 + c] = v[c];
+}
+
+__device__ void lb_total(const double* part, double (&t)[4])
+{
+    for (int c = 0; c < 4; ++c) t[c] = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b)
+        for (int c = 0; c < 4; ++c) t[c] += part[b * 4 + c];
+}
+
+#define TC_GRID_ROWS(p) for (int64_t rl = blockIdx.x * (int64_t)kUpd + threadIdx.x; rl < (p).m; rl += (int64_t)gridDim.x * kUpd)
+
+// 1. dE/dz into q; partials |gz|^2, s.y, s.s, y.y
+__global__ void __launch_bounds__(kUpd) k_lb_grad(RelaxDev d, LbArgs la, const double2* __restrict__ part_g,
+                                                  SlotView v, StepParams sp)
+{
+    __shared__ double sh[kUpd];
+    if (!d.active[la.s]) return;
+    const Prob p = d.prob[la.s];
+    const int k = d.steps[la.s];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    TC_GRID_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        const double2 g = sum_g(p, rl, part_g, v);
+        if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
+        const bool pinned = d.flags && d.flags[d.gidx[row]];
+        const double2 z = d.z[row];
+        const double2 gz = grad_z(z, g, sp.radius, pinned);
+        d.q[row] = gz;
+        acc[0] += gz.x * gz.x + gz.y * gz.y;
+        if (k > 0) {
+            const double2 zo = d.xp[row], go = d.gp[row];
+            const double sx = z.x - zo.x, sy = z.y - zo.y, yx = gz.x - go.x, yy = gz.y - go.y;
+            acc[1] += sx * yx + sy * yy;
+            acc[2] += sx * sx + sy * sy;
+            acc[3] += yx * yx + yy * yy;
+        }
+    }
+    if (bad) set_status(d.st, ST_NONFINITE);
+    lb_partial(acc, la.part, sh);
+}
+
+// 2. pair test, history bookkeeping, stop test (one CTA)
+__global__ void k_lb_decide(RelaxDev d, LbArgs la, StepParams sp)
+{
+    if (threadIdx.x != 0) return;
+    LbScal& c = *la.sc;
+    c.done = 1;
+    if (!d.active[la.s]) return;
+    const Prob p = d.prob[la.s];
+    const int k = d.steps[la.s];
+    double t[4];
+    for (int q = 0; q < 4; ++q) t[q] = 0.0;
+    for (int b = 0; b < kLargeBlocks; ++b)
+        for (int q = 0; q < 4; ++q) t[q] += la.part[b * 4 + q];
+    if (sp.measure) {
+        d.rms[la.s] = sqrt(t[0] / (double)max(p.m, 1));
+        return;
+    }
+    const int mem = sp.memory;
+    int hist = d.hist[la.s], head = d.head[la.s];
+    c.keep = k > 0 && t[1] > 1e-12 * sqrt(t[2]) * sqrt(t[3]);
+    c.slot = head;
+    if (c.keep) {
+        d.rho[(int64_t)la.s * kMaxMem + head] = 1.0 / t[1];
+        head = (head + 1) % mem;
+        hist = min(hist + 1, mem);
+    }
+    const double rms = sqrt(t[0] / (double)max(p.m, 1));
+    d.rms[la.s] = rms;
+    d.hist[la.s] = hist;
+    d.head[la.s] = head;
+    if (sp.gtol > 0.0 && rms < sp.gtol) {
+        d.active[la.s] = 0;
+        return;
+    }
+    c.done = 0;
+}
+
+// 3. store the pair, keep dE/dz
+__global__ void __launch_bounds__(kUpd) k_lb_store(RelaxDev d, LbArgs la)
+{
+    const LbScal& c = *la.sc;
+    const Prob p = d.prob[la.s];
+    const int64_t M = d.M;
+    TC_GRID_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        const double2 gz = d.q[row];
+        if (c.keep) {
+            const double2 z = d.z[row], zo = d.xp[row], go = d.gp[row];
+            d.Sh[(int64_t)c.slot * M + row] = make_double2(z.x - zo.x, z.y - zo.y);
+            d.Yh[(int64_t)c.slot * M + row] = make_double2(gz.x - go.x, gz.y - go.y);
+        }
+        d.gp[row] = gz;
+    }
+}
+
+// 4. two-loop recursion step.  phase 1, entry i: q -= al[j_{i-1}] y_{j_{i-1}} (i > 0),
+// then partial s_{j_i} . q (i < hist); at i == hist also the gamma partials.
+// phase 2, entry i (counting down from hist - 1): q += c s_{j_{i+1}} (i < hist - 1)
+// or q *= gamma (i == hist - 1), then partial y_{j_i} . q.
+__global__ void __launch_bounds__(kUpd) k_lb_loop(RelaxDev d, LbArgs la, StepParams sp, int phase, int i)
+{
+    __shared__ double sh[kUpd];
+    const LbScal& c = *la.sc;
+    if (c.done) return;
+    const Prob p = d.prob[la.s];
+    const int hist = d.hist[la.s], head = d.head[la.s], mem = sp.memory;
+    const int64_t M = d.M;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (phase == 1) {
+        if (i > hist) return;
+        const int jp = i > 0 ? lb_slot(head, i - 1, mem) : 0;
+        const int jn = i < hist ? lb_slot(head, i, mem) : 0;
+        const int jnew = lb_slot(head, 0, mem);
+        const double a = i > 0 ? c.al[jp] : 0.0;
+        TC_GRID_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 q = d.q[row];
+            if (i > 0) {
+                const double2 y = d.Yh[(int64_t)jp * M + row];
+                q = make_double2(q.x - a * y.x, q.y - a * y.y);
+                d.q[row] = q;
+            }
+            if (i < hist) {
+                const double2 sv = d.Sh[(int64_t)jn * M + row];
+                acc[0] += sv.x * q.x + sv.y * q.y;
+            } else if (hist > 0) {
+                const double2 sv = d.Sh[(int64_t)jnew * M + row], y = d.Yh[(int64_t)jnew * M + row];
+                acc[1] += sv.x * y.x + sv.y * y.y;
+                acc[2] += y.x * y.x + y.y * y.y;
+            }
+        }
+    } else {
+        if (i >= hist) return;
+        const int jn = lb_slot(head, i, mem);
+        const int jp = i < hist - 1 ? lb_slot(head, i + 1, mem) : 0;
+        TC_GRID_ROWS(p)
+        {
+            const int64_t row = p.row_base + rl;
+            double2 q = d.q[row];
+            if (i == hist - 1) {
+                q = make_double2(q.x * c.gamma, q.y * c.gamma);
+            } else {
+                const double2 sv = d.Sh[(int64_t)jp * M + row];
+                q = make_double2(q.x + c.c * sv.x, q.y + c.c * sv.y);
+            }
+            d.q[row] = q;
+            const double2 y = d.Yh[(int64_t)jn * M + row];
+            acc[0] += y.x * q.x + y.y * q.y;
+        }
+    }
+    lb_partial(acc, la.part, sh);
+}
+
+// 5. scalars after a loop step (one CTA)
+__global__ void k_lb_loop_fin(RelaxDev d, LbArgs la, StepParams sp, int phase, int i)
+{
+    if (threadIdx.x != 0) return;
+    LbScal& c = *la.sc;
+    if (c.done) return;
+    const int hist = d.hist[la.s], head = d.head[la.s], mem = sp.memory;
+    const double* rho = d.rho + (int64_t)la.s * kMaxMem;
+    double t[4];
+    for (int q = 0; q < 4; ++q) t[q] = 0.0;
+    for (int b = 0; b < kLargeBlocks; ++b)
+        for (int q = 0; q < 4; ++q) t[q] += la.part[b * 4 + q];
+    if (phase == 1) {
+        if (i > hist) return;
+        if (i < hist) {
+            const int j = lb_slot(head, i, mem);
+            c.al[j] = rho[j] * t[0];
+        } else {
+            c.gamma = hist > 0 ? t[1] / t[2] : sp.step0;
+        }
+    } else {
+        if (i >= hist) return;
+        const int j = lb_slot(head, i, mem);
+        c.c = c.al[j] - rho[j] * t[0];
+    }
+}
+
+// 6. finish the direction: last second-loop update (or the gamma scaling
+// without history), then partials of gz . q and max |q|
+__global__ void __launch_bounds__(kUpd) k_lb_dir(RelaxDev d, LbArgs la, StepParams sp)
+{
+    __shared__ double sh[kUpd];
+    const LbScal& c = *la.sc;
+    if (c.done) return;
+    const Prob p = d.prob[la.s];
+    const int hist = d.hist[la.s], head = d.head[la.s], mem = sp.memory;
+    const int64_t M = d.M;
+    const int j0 = lb_slot(head, 0, mem);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double mx = 0.0;
+    TC_GRID_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        double2 q = d.q[row];
+        if (hist > 0) {
+            const double2 sv = d.Sh[(int64_t)j0 * M + row];
+            q = make_double2(q.x + c.c * sv.x, q.y + c.c * sv.y);
+        } else {
+            q = make_double2(q.x * c.gamma, q.y * c.gamma);
+        }
+        d.q[row] = q;  // H gz; the direction is -q
+        const double2 gz = d.gp[row];
+        acc[0] += gz.x * q.x + gz.y * q.y;
+        mx = fmax(mx, sqrt(q.x * q.x + q.y * q.y));
+        acc[2] = fmax(acc[2], sqrt(gz.x * gz.x + gz.y * gz.y));
+    }
+    acc[1] = block_max(mx, sh);
+    acc[2] = block_max(acc[2], sh);
+    acc[0] = block_sum<kUpd>(acc[0], sh);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) la.part[blockIdx.x * 4 + q] = acc[q];
+}
+
+// 7. descent check and step scale (one CTA)
+__global__ void k_lb_dir_fin(RelaxDev d, LbArgs la, StepParams sp)
+{
+    if (threadIdx.x != 0) return;
+    LbScal& c = *la.sc;
+    if (c.done) return;
+    double dd = 0.0, qmax = 0.0, gmax = 0.0;
+    for (int b = 0; b < kLargeBlocks; ++b) {
+        dd += la.part[b * 4 + 0];
+        qmax = fmax(qmax, la.part[b * 4 + 1]);
+        gmax = fmax(gmax, la.part[b * 4 + 2]);
+    }
+    // direction -q is a descent direction iff gz . q > 0
+    c.reset = !(dd > 0.0);
+    if (c.reset) {
+        d.hist[la.s] = 0;
+        d.head[la.s] = 0;
+    }
+    const double dmax = c.reset ? sp.step0 * gmax : qmax;
+    c.alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
+}
+
+// 8. the step z += alpha d, then x and its split
+__global__ void __launch_bounds__(kUpd) k_lb_step(RelaxDev d, LbArgs la, StepParams sp)
+{
+    const LbScal& c = *la.sc;
+    if (c.done) return;
+    const Prob p = d.prob[la.s];
+    TC_GRID_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        const bool pinned = d.flags && d.flags[d.gidx[row]];
+        const double2 z = d.z[row], q = d.q[row], gz = d.gp[row];
+        const double2 dv = c.reset ? make_double2(-sp.step0 * gz.x, -sp.step0 * gz.y) : make_double2(-q.x, -q.y);
+        d.xp[row] = z;
+        const double2 zn = make_double2(z.x + c.alpha * dv.x, z.y + c.alpha * dv.y);
+        d.z[row] = zn;
+        const double2 xn = z_to_x(zn, sp.radius, pinned);
+        d.x[row] = xn;
+        d.xs[row] = split4(xn.x, xn.y);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.steps[la.s] = d.steps[la.s] + 1;
+}
+
+// Launch the sequence for one large problem.
+static cudaError_t lbfgs_large(RelaxDev& d, LbArgs la, const double2* part_g, SlotView v, const StepParams& sp,
+                               cudaStream_t s)
+{
+    k_lb_grad<<<kLargeBlocks, kUpd, 0, s>>>(d, la, part_g, v, sp);
+    k_lb_decide<<<1, 32, 0, s>>>(d, la, sp);
+    k_lb_store<<<kLargeBlocks, kUpd, 0, s>>>(d, la);
+    for (int i = 0; i <= sp.memory; ++i) {
+        k_lb_loop<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp, 1, i);
+        k_lb_loop_fin<<<1, 32, 0, s>>>(d, la, sp, 1, i);
+    }
+    for (int i = sp.memory - 1; i >= 0; --i) {
+        k_lb_loop<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp, 2, i);
+        k_lb_loop_fin<<<1, 32, 0, s>>>(d, la, sp, 2, i);
+    }
+    k_lb_dir<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp);
+    k_lb_dir_fin<<<1, 32, 0, s>>>(d, la, sp);
+    k_lb_step<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp);
+    return cudaGetLastError();
 }
 
 // ----------------------------------------------------- energy changes ---
@@ -609,9 +934,16 @@ static_assert(sizeof(tc_relax_params) == 88, "tc_relax_params layout");
 static_assert(sizeof(tc_relax_profile) == 56, "tc_relax_profile layout");
 
 // One relaxation phase: `steps` x (pass, update), captured into a CUDA graph.
+// Problems whose L-BFGS update runs as the grid-wide sequence.
+struct LargeSet {
+    std::vector<int> ids;
+    double* part = nullptr;
+    LbScal* sc = nullptr;  // one per entry of ids
+};
+
 template <int KIND>
 static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, const StepParams& sp, int steps,
-                           cudaStream_t s, bool prof, int& launches)
+                           cudaStream_t s, bool prof, int& launches, const LargeSet& large)
 {
     if (steps <= 0) return TC_OK;
     size_t ev0 = 0;  // events 0 .. 2 steps: [pass k] between 2k and 2k+1, [update k] between 2k+1 and 2k+2
@@ -636,12 +968,37 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
         e = launch_pass<KIND, false, true>(a, G, 0, 0, cap);
         if (e != cudaSuccess) break;
         if (prof) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 1), cap);
-        if (sp.opt == TC_OPT_LBFGS)
+        if (sp.opt == TC_OPT_LBFGS) {
             k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
-        else
+            for (size_t q = 0; q < large.ids.size(); ++q) {
+                LbArgs la{large.ids[q], large.part, large.sc + q};
+                if (e == cudaSuccess) e = lbfgs_large(d, la, a.part_g, v, sp, cap);
+                launches += 2 * (2 * sp.memory + 1) + 6;
+            }
+        } else {
             k_update_gdbb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
+        }
         if (e == cudaSuccess) e = cudaGetLastError();
         if (prof && e == cudaSuccess) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 2), cap);
+        launches += (a.W > 0 ? 1 : 0) + 1;
+    }
+    // one more pass at the final rows: the reported RMS describes the returned configuration
+    if (e == cudaSuccess) e = launch_pass<KIND, false, true>(a, G, 0, 0, cap);
+    if (e == cudaSuccess) {
+        StepParams sm = sp;
+        sm.measure = 1;
+        if (sp.opt == TC_OPT_LBFGS) {
+            k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sm);
+            for (size_t q = 0; q < large.ids.size(); ++q) {
+                LbArgs la{large.ids[q], large.part, large.sc + q};
+                k_lb_grad<<<kLargeBlocks, kUpd, 0, cap>>>(d, la, a.part_g, v, sm);
+                k_lb_decide<<<1, 32, 0, cap>>>(d, la, sm);
+                launches += 2;
+            }
+        } else {
+            k_update_gdbb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sm);
+        }
+        e = cudaGetLastError();
         launches += (a.W > 0 ? 1 : 0) + 1;
     }
     if (capture) {
@@ -765,6 +1122,10 @@ static tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t
     }
     const int64_t M = P.M;
     const int64_t taken_words = (n + 31) / 32;
+    LargeSet large;
+    if (lbfgs)
+        for (int32_t k = 0; k < n_sub; ++k)
+            if (P.prob[k].m > kLargeRows) large.ids.push_back(k);
 
     Carver c;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
@@ -795,6 +1156,8 @@ static tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t
         d.delta = cv.take<double>(n_sub);
         d.energy = cv.take<double>(n_sub);
         snap_split = cv.take<float4>(inst ? 0 : n);
+        large.part = cv.take<double>(lbfgs ? (size_t)kLargeBlocks * 4 : 0);
+        large.sc = cv.take<LbScal>(lbfgs ? large.ids.size() : 0);
         part_e = cv.take<double>(slots * M);
         part_g = cv.take<double2>(slots * M);
         part1 = cv.take<double>(slots1 * max_m);
@@ -874,16 +1237,16 @@ static tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t
     a.active = d.active;
     a.part_e = part_e;
     a.part_g = part_g;
-    StepParams sp{prm->optimizer, mem, prm->step0, prm->alpha_min, prm->alpha_max, prm->maxstep, prm->gtol, prm->radius};
+    StepParams sp{prm->optimizer, mem, prm->step0, prm->alpha_min, prm->alpha_max, prm->maxstep, prm->gtol, prm->radius, 0};
     tc_status rs;
     if (prec == TC_MIXED) {
         a.rows = d.xs;
         a.snap = snap_split;
-        rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches);
+        rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
     } else {
         a.rows = d.x;
         a.snap = pos;
-        rs = run_phase<PASS_F64>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches);
+        rs = run_phase<PASS_F64>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
     }
     if (rs != TC_OK) return rs;
     if (prm->polish_steps > 0) {
@@ -893,7 +1256,7 @@ static tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t
         sp2.gtol = prm->polish_gtol;
         a.rows = d.x;
         a.snap = pos;
-        rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches);
+        rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large);
         if (rs != TC_OK) return rs;
     }
     a.active = nullptr;

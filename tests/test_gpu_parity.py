@@ -278,6 +278,23 @@ def test_lbfgs_instances_fp64_match_oracle():
         assert abs(r.energy[k].item() - oracle.energy(xo)) <= 1e-12 * oracle.energy(xo)
 
 
+def test_lbfgs_large_instance_grid_update_matches_oracle():
+    """An instance above 16384 charges takes the grid-wide L-BFGS update; it must follow the oracle."""
+    n = 17000
+    pos = synth.arcsine_disk(n, 77)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    p = T(pos.copy())
+    world = T(np.array([[0, n]], dtype=np.int64))
+    iters = 3
+    r = tc.relax_subdomains(p, world=world, precision="fp64", optimizer="lbfgs", n_steps=iters, memory=8,
+                            step0=1e-6, maxstep=0.002, accept=False)
+    tc.sync_status()
+    xo, it, rms = oracle.lbfgs(pos, memory=8, max_iter=iters, gtol=0.0, step0=1e-6, maxstep=0.002)
+    assert int(r.steps[0]) == iters
+    assert np.abs(p.cpu().numpy() - xo).max() <= 1e-9
+    assert abs(r.rms[0].item() - rms) <= 1e-6 * rms
+
+
 def test_lbfgs_mixed_then_fp64_polish_converges():
     """Mixed bulk steps then float64 polish end at a float64-stationary configuration."""
     sizes = [5, 8, 60]
