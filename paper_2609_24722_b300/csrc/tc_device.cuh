@@ -18,13 +18,14 @@ namespace tc {
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_NONFINITE = 3, ST_OUTSIDE = 4, ST_TIMEOUT = 5 };
 
 // A masked-out or padding source sits this far away: its 1/r term is below
-// 1e-30 (float64) or 1e-18 (float32) and its gradient term underflows, so it
-// vanishes below one rounding of any real row sum.
-constexpr double kFar64 = 1.0e30;
+// 1e-18 and its gradient term below 1e-36, so even 255 of them change no real
+// row sum by more than a rounding.  Every squared distance to such a source
+// (< 1e37) stays inside the float32 range the rsqrt seed of rsqrt64 needs.
+constexpr double kFar64 = 1.0e18;
 constexpr float kFar32 = 1.0e18f;
 // Rows past the end of a problem sit at the opposite far corner, so they
 // never coincide with a far source.
-constexpr double kFarRow64 = -1.0e30;
+constexpr double kFarRow64 = -1.0e18;
 constexpr float kFarRow32 = -1.0e18f;
 
 // Slack above the wall radius that still counts as inside (Eq. potential).
@@ -45,16 +46,31 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
 
 // float64 1/sqrt(r2): a float32 seed y0, then one correction step of the
 // binomial series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3) with
-// e = 1 - r2 y0^2.  With |e| < 2^-21 the truncation is below 2^-63, so the
-// result is within a few rounding errors of the correctly rounded value.
-// r2 = 0 gives NaN (coincident charges are caught by the finiteness checks).
+// e = 1 - r2 y0^2.
+//
+// The seed avoids float64<->float32 conversion instructions, which occupy the
+// (on B300 very narrow) float64 pipe: the high word of r2 holds its sign, 11
+// exponent bits and top 20 mantissa bits, and rebiasing the exponent
+// (1023 -> 127, i.e. subtracting 896 << 20) and shifting left by 3 gives the
+// float32 with r2's mantissa truncated to 20 bits (relative error < 2^-20);
+// MUFU.RSQ of it, widened back exactly (exponent +896, mantissa bits moved
+// down by 3 into the high word and 29 into the low word), has |e| < 2^-19, so
+// the cubic remainder (5/16) e^3 stays below 2^-58 relative and the result is
+// within a few roundings of the correctly rounded value.  Integer work runs on
+// the ALU pipe.  Valid for 2^-126 <= r2 < 2^128; r2 below that (coincident
+// charges) gives NaN, which the finiteness checks report.
 __device__ __forceinline__ double rsqrt64(double r2)
 {
-    double y0 = (double)rsqrt_mufu((float)r2);
-    double t = r2 * y0;
-    double e = fma(-t, y0, 1.0);
-    double p = fma(0.375, e, 0.5);
-    double q = e * p;
+    const unsigned hi = (unsigned)__double2hiint(r2);
+    const float seed = __uint_as_float((hi - (896u << 20)) << 3);
+    const unsigned fb = __float_as_uint(rsqrt_mufu(seed));
+    double y0 = __hiloint2double((int)((fb >> 3) + (896u << 20)), (int)(fb << 29));
+    // r2 below 2^-126 (coincident charges) has no float seed: make the result NaN
+    y0 = hi < (897u << 20) ? __longlong_as_double(0x7ff8000000000000LL) : y0;
+    const double t = r2 * y0;
+    const double e = fma(-t, y0, 1.0);
+    const double p = fma(0.375, e, 0.5);
+    const double q = e * p;
     return fma(y0, q, y0);
 }
 

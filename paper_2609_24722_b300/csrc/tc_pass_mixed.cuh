@@ -27,17 +27,18 @@ namespace tc {
 constexpr float kFarDist = 0.02f;
 constexpr float kBoxEmptyLo = 3.0e38f, kBoxEmptyHi = -3.0e38f;
 
-// Packed rows of one thread: R rows as R/2 float2 pairs of hi parts in
-// registers; their lo parts and the cross-tile accumulators stay in shared
-// memory (per-thread slots) so the tile loop keeps few registers live.
+// Packed rows of one thread: R rows as R/2 float2 pairs.  The pairs (hi and
+// lo parts) and the cross-tile accumulators stay in shared memory
+// (per-thread slots); each tile reads the pairs back with one LDS.64 each, so
+// they occupy adjacent registers only while the tile loop runs.
 template <int R> struct MixedRows {
     static_assert(R % 2 == 0, "rows come in pairs");
     static constexpr int P = R / 2;
-    float2 xh[P], yh[P];
 
-    // Loads rows rl0 + r*stride (r < R); rows past m sit far away.  lo parts go
-    // to lo2[2P][stride] (x pairs then y pairs), accumulators acc[6R][stride]
-    // are zeroed.  Returns the box (xmin, ymin, xmax, ymax) of the valid rows.
+    // Loads rows rl0 + r*stride (r < R); rows past m sit far away.  The pairs go
+    // to lo2[4P][stride] (x lo, y lo, x hi, y hi pairs), accumulators
+    // acc[6R][stride] are zeroed.  Returns the box (xmin, ymin, xmax, ymax) of
+    // the valid rows.
     __device__ float4 load(const float4* rows, int64_t base, int64_t rl0, int stride, int m, float2* lo2, float* acc,
                            int tid)
     {
@@ -57,10 +58,10 @@ template <int R> struct MixedRows {
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            xh[p] = make_float2(q[2 * p].x, q[2 * p + 1].x);
-            yh[p] = make_float2(q[2 * p].y, q[2 * p + 1].y);
             lo2[p * stride + tid] = make_float2(q[2 * p].z, q[2 * p + 1].z);
             lo2[(P + p) * stride + tid] = make_float2(q[2 * p].w, q[2 * p + 1].w);
+            lo2[(2 * P + p) * stride + tid] = make_float2(q[2 * p].x, q[2 * p + 1].x);
+            lo2[(3 * P + p) * stride + tid] = make_float2(q[2 * p].y, q[2 * p + 1].y);
         }
 #pragma unroll
         for (int c = 0; c < 6 * R; ++c) acc[c * stride + tid] = 0.f;
@@ -75,10 +76,12 @@ template <int R> struct MixedRows {
                                          const float2* lo2, float* acc, int stride, int tid, int jself0,
                                          float escale)
     {
-        float2 et[P], gxt[P], gyt[P], xl[P], yl[P];
+        float2 et[P], gxt[P], gyt[P], xl[P], yl[P], xh[P], yh[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             et[p] = gxt[p] = gyt[p] = make_float2(0.f, 0.f);
+            xh[p] = lo2[(2 * P + p) * stride + tid];
+            yh[p] = lo2[(3 * P + p) * stride + tid];
             if (NEAR) {
                 xl[p] = lo2[p * stride + tid];
                 yl[p] = lo2[(P + p) * stride + tid];
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
     __shared__ float4 swbox[2][NW];
     __shared__ float4 srbox[NW];
     __shared__ float sacc[6 * R * THREADS];
-    __shared__ float2 slo2[2 * P * THREADS];
+    __shared__ float2 slo2[4 * P * THREADS];
     __shared__ Prob sprob;
     __shared__ int sprob_s;
 
