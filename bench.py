@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-instances", action="store_true", help="skip the batched-instances (C5) section")
     # a single small kernel case (used for profiler captures): no JSON bench line
-    ap.add_argument("--case", choices=["allpairs", "relax", "full-relax"], default=None)
+    ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle"], default=None)
+    ap.add_argument("--batch", type=int, default=64, help="cycle case: subdomains per batch")
+    ap.add_argument("--zone-steps", type=int, default=100, help="cycle case: relaxation steps per zone")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--nsub", type=int, default=16)
@@ -74,6 +76,11 @@ def run_case(args):
     dev = torch.device("cuda", 0)
     if args.case == "full-relax":
         print(json.dumps(run_full_relax(dev, n=args.n)))
+        return
+    if args.case == "cycle":
+        # cycle time against N at a fixed number of subdomain optimisations (Sec. II E)
+        for n in [args.n // 8, args.n // 4, args.n // 2, args.n]:
+            print(json.dumps(run_cycle(dev, n=n, n_sub=args.nsub, batch=args.batch, steps=args.zone_steps)))
         return
     if args.config is not None:
         from paper_2609_24722_b300 import _lib
@@ -215,13 +222,24 @@ def cpu_baseline(pos, idx, off, seconds: float = 12.0) -> dict:
     oracle.rows_grad(pos, rows)
     dt = time.perf_counter() - t0
     pairs = n_rows * (N - 1)
-    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"float64 gradient + energy rows of the first {n_rows} subdomain charges against all "
-                      f"{N} charges (tco_rows_grad, single thread, Neumaier sums), {dt:.1f} s"}
+    out = {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"float64 gradient + energy rows of the first {n_rows} subdomain charges against all "
+                     f"{N} charges (tco_rows_grad, single thread, Neumaier sums), {dt:.1f} s"}
+    # the same oracle source built with OpenMP: rows split over every host thread
+    threads = oracle.threads(openmp=True)
+    n_omp = int(min(len(rows_all), max(n_rows, n_rows * threads * 0.5)))
+    rows = np.ascontiguousarray(rows_all[:n_omp])
+    t0 = time.perf_counter()
+    oracle.rows_grad(pos, rows, openmp=True)
+    dt = time.perf_counter() - t0
+    out["all_cores"] = {"value": n_omp * (N - 1) / dt, "unit": UNIT, "cores": threads, "kind": "oracle-openmp",
+                        "sample": f"the first {n_omp} subdomain rows against all {N} charges "
+                                  f"(tco_rows_grad built with -fopenmp, bit-identical rows), {dt:.1f} s"}
+    return out
 
 
 def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
-                  polish: int = 100, fp64_steps: int = 20):
+                  polish: int = 20, fp64_steps: int = 10):
     """Config C5: 512 independent instances (N_k ~ U{100..5000}, arcsine init each), relaxed in one
     batched call per round (mixed L-BFGS, memory 8, then float64 polish), 3 perturbation restarts
     (Gaussian kicks of 0.05 x the instance's lattice spacing) keeping each instance's best energy;
@@ -318,6 +336,48 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
             "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1,
             "relax_time_s": t2 - t0, "mean_force_initial": f_ref, "energy_initial": e0, "energy_final": e,
             "E_over_N2": e / n ** 2, "pi_over_4": math.pi / 4}
+
+
+def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 100, m_min: int = 200,
+              m_max: int = 4000, period: int = 64, seed: int = 0, local_precision: str = "mixed") -> dict:
+    """The adaptive optimisation cycle (Sec. II C) on the GPU: per batch of `batch` subdomains, local
+    energies of all N charges, defect threshold e_i > mu - sigma_e, centres (80 % at defects, 20 %
+    uniform in the disk), zones of the m nearest charges (m a triangle wave between m_min and m_max),
+    `steps` mixed projected BB steps per zone against all N, sequential float64 accept."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2609_24722_b300 as tc
+
+    pos = synth.lattice_disk(n, seed)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    p = torch.tensor(pos, device=dev)
+    u = torch.tensor(np.random.default_rng(seed + 7).random((n_sub, 3)), device=dev)
+    eta = 1e-4 / n
+    kw = dict(batch=batch, m_min=m_min, m_max=m_max, period=period, local_precision=local_precision,
+              precision="mixed", optimizer="bb", n_steps=steps, step0=eta, alpha_min=0.0, alpha_max=10 * eta)
+    sizes = np.diff(tc.zone_offsets(n, n_sub, m_min=m_min, m_max=m_max, period=period))
+    # warm-up on a copy (graph capture, workspace growth)
+    tc.cycle(p.clone(), u[: min(batch, n_sub)], **kw)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    r, trace = tc.cycle(p, u, **kw)
+    b.record()
+    torch.cuda.synchronize()
+    tc.sync_status()
+    ms = a.elapsed_time(b)
+    n_batches = -(-n_sub // batch)
+    pairs = int(sizes.sum()) * (n - 1) * (steps + 1) + n_batches * n * (n - 1)
+    tr = trace.cpu().numpy()
+    st = r.status.cpu().numpy()
+    return {"workload": f"N={n} lattice background, {n_sub} subdomains in batches of {batch}, zones of "
+                        f"{m_min}..{m_max} nearest charges (triangle wave, period {period}), {steps} mixed BB "
+                        f"steps each, {local_precision} local energies per batch, fp64 sequential accept",
+            "cycle_time_s": ms / 1e3, "ms_per_subdomain": ms / n_sub, "pairs_per_s": pairs / (ms / 1e3),
+            "accepted": int((st == 1).sum()), "skipped_overlap": int((st == 2).sum()),
+            "energy_start": float(tr[0]), "energy_end": float(tr[-1]), "energy_drop": float(tr[0] - tr[-1])}
 
 
 def run_reference(args):
@@ -468,6 +528,7 @@ def main():
     ms_mixed = time_allpairs("mixed", 5)
     ms_f64 = time_allpairs("fp64", 3)
     c5 = run_instances(dev) if not args.no_instances else None
+    cyc = run_cycle(dev) if not args.no_instances else None
     pipes = tc.probe_pipes()
     tc.sync_status()
 
@@ -506,6 +567,7 @@ def main():
         "allpairs_n1e5": {"mixed_pairs_per_s": N * (N - 1) / (ms_mixed / 1e3), "mixed_ms": ms_mixed,
                           "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64},
         "instances_c5": c5,
+        "adaptive_cycle": cyc,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": args.steps * (prof["launches"] + 3),

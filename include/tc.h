@@ -187,6 +187,81 @@ tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const 
                               int32_t n_sub, const int64_t* world, const uint8_t* flags,
                               const tc_relax_params* prm, tc_subdomain_result* out, tc_stream stream);
 
+/* ---- The adaptive optimisation cycle (Sec. II C) ----
+ *
+ * One cycle runs T subdomain optimisations.  Each picks a centre (step 3) --
+ * with probability p_defect a defect charge found by the local-energy
+ * threshold of step 2, otherwise a point drawn uniformly over the disk -- and
+ * optimises the charges of a zone around it (step 4) against all the others.
+ * The paper lets the zone radius r_zone oscillate periodically without giving
+ * the law; here a zone is the m charges nearest to the centre, and m follows
+ * a triangle wave between m_min and m_max.  Random numbers are inputs: three
+ * uniforms in [0,1) per subdomain, so a cycle is reproducible bit for bit. */
+typedef struct {
+    double kappa;     /* defects: e_i > mu + kappa sigma_e (the paper's rule: kappa = -1) */
+    double p_defect;  /* probability that a centre is a defect charge (the paper: 0.8) */
+    double radius;    /* disk radius (> 0) */
+    double wall_tol;  /* |r_i| >= radius - wall_tol marks a boundary charge: never a defect */
+    int32_t m_min;    /* zone size at schedule position q = 0 mod period (>= 0) */
+    int32_t m_max;    /* zone size at q = period / 2 mod period (>= m_min) */
+    int32_t period;   /* schedule period in subdomains (>= 1) */
+    int32_t phase;    /* schedule position of the first subdomain (>= 0) */
+} tc_zone_params;
+
+/* Zone sizes and CSR offsets of n_sub subdomains at schedule positions
+ * phase .. phase + n_sub - 1: with q' = q mod period,
+ *   m_q = min(n, m_min + floor(2 (m_max - m_min) min(q', period - q') / period)),
+ * offsets[0] = 0, offsets[s+1] = offsets[s] + m_(phase+s).
+ *   offsets [n_sub + 1]  HOST array, written.  Host-only; no GPU work. */
+tc_status tc_zone_offsets(const tc_zone_params* prm, int64_t n, int32_t n_sub, int64_t* offsets);
+
+/* Steps 2-3 of Sec. II C and the zone of step 4, for n_sub subdomains:
+ *   mu, sigma_e = mean and population standard deviation of local_e over all n;
+ *   defects D = { i : local_e[i] > mu + kappa sigma_e and |r_i| < radius - wall_tol },
+ *     in ascending i;
+ *   subdomain s takes u = uniforms[3s .. 3s+2]:
+ *     centre = r_(D[floor(u1 |D|)]) if u0 < p_defect and D is not empty, else
+ *              sqrt(u1) radius (cos 2 pi u2, sin 2 pi u2);
+ *     zone   = the m_s charges with the smallest (d^2, i), d^2 = (x_i - c_x)^2 +
+ *              (y_i - c_y)^2 rounded as written (no fused multiply-add), listed
+ *              in ascending i -- a valid idx range for tc_relax_subdomains.
+ *   pos      [2n]          device positions
+ *   local_e  [n]           device e_i (tc_energy's local_e)
+ *   uniforms [3 n_sub]     device, each in [0, 1)
+ *   idx      [offsets[n_sub]] device, written (size it with tc_zone_offsets)
+ *   offsets  [n_sub + 1]   device, written
+ *   centres  [2 n_sub]     device, written; nullable
+ *   stats    [3]           device, written (mu, sigma_e, |D|); nullable
+ * Asynchronous on `stream`; TC_ERR_INVALID_ARG for bad sizes or parameters. */
+tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local_e, const tc_zone_params* prm,
+                               int32_t n_sub, const double* uniforms, int32_t* idx, int64_t* offsets,
+                               double* centres, double* stats, tc_stream stream);
+
+typedef struct {
+    tc_zone_params zone;    /* zone.phase is the schedule position of the cycle's first subdomain */
+    tc_relax_params relax;  /* optimiser of step 4; accept is forced to 1 */
+    int32_t batch;          /* subdomains selected and relaxed together (1 = one at a time) */
+    int32_t local_precision;/* tc_precision of the e_i that pick the centres */
+} tc_cycle_params;
+
+/* One optimisation cycle (Sec. II C) of n_sub subdomains, in batches of
+ * `batch` consecutive ones.  For each batch: the local energies e_i of the
+ * current configuration (step 1), tc_select_subdomains at schedule position
+ * zone.phase + first subdomain of the batch (steps 2-3), then
+ * tc_relax_subdomains with the sequential float64 accept (step 4).  batch = 1
+ * recomputes e_i before every subdomain, as the paper's cycle does; a larger
+ * batch relaxes its zones concurrently against the configuration at the
+ * batch's start and accepts them in order.
+ *   pos      [2n]          in/out configuration (device)
+ *   uniforms [3 n_sub]     device, each in [0, 1)
+ *   out      [n_sub]       device results, as tc_relax_subdomains
+ *   energy   [n_batches+1] device; E (in local_precision) before each batch and
+ *                          after the last; nullable
+ * Synchronises the stream once per batch (the zone sizes are host-known, the
+ * relaxation reads its offsets back).  Device errors as tc_relax_subdomains. */
+tc_status tc_cycle(double* pos, int64_t n, const tc_cycle_params* prm, int32_t n_sub, const double* uniforms,
+                   tc_subdomain_result* out, double* energy, tc_stream stream);
+
 /* Total energy (and local energies) exactly as tc_energy computes them, but
  * without allocating any device memory.  The paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc: code that runs

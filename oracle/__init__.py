@@ -15,6 +15,9 @@ Paper passages followed (Lavrov & Nikonov, Thomson problem in a disk):
   lbfgs / bb / pgd  projected descent on E (the paper's local optimiser is
                   L-BFGS-B, Sec. II C step 4; see the function docs for the
                   variant written here)
+  zone_select     steps 1-3 of the optimisation cycle of Sec. II C (defect
+                  threshold, centre choice) and the zone of step 4
+  cycle           the optimisation cycle of Sec. II C, in batches
 """
 
 from __future__ import annotations
@@ -36,13 +39,13 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-_lib = None
+_libs: dict = {}
 
 
-def lib() -> C.CDLL:
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(openmp: bool = False) -> C.CDLL:
+    """The plain single-thread build, or (openmp=True) the same source built with OpenMP."""
+    if openmp not in _libs:
+        path = _build.build(openmp=openmp)
         L = C.CDLL(path)
         d, i64, vp = C.c_double, C.c_int64, C.c_void_p
         sig = {
@@ -57,13 +60,23 @@ def lib() -> C.CDLL:
             "tco_subdomain_bb": [vp, i64, vp, i64, d, d, d, i64, d, vp],
             "tco_accept_sequential": [vp, i64, vp, vp, i64, vp, vp, vp],
             "tco_lbfgs": [vp, i64, i64, i64, d, d, d, d, vp, vp, vp],
+            "tco_threads": [],
+            "tco_zone_select": [vp, i64, vp, d, d, d, d, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp],
+            "tco_cycle": [vp, i64, d, d, d, d, i64, i64, i64, i64, i64, vp, d, d, d, i64, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
-        _lib = L
-    return _lib
+        L.tco_zone_size.argtypes = [i64, i64, i64, i64, i64]
+        L.tco_zone_size.restype = i64
+        _libs[openmp] = L
+    return _libs[openmp]
+
+
+def threads(openmp: bool = False) -> int:
+    """Host threads tco_rows_grad runs on in the plain (1) or OpenMP build."""
+    return int(lib(openmp).tco_threads())
 
 
 def _pos(pos) -> np.ndarray:
@@ -99,13 +112,15 @@ def grad(pos) -> np.ndarray:
     return g
 
 
-def rows_grad(pos, rows):
-    """Gradient rows (and sum_{j != i} 1/r_ij) of the charges `rows` against all n."""
+def rows_grad(pos, rows, openmp: bool = False):
+    """Gradient rows (and sum_{j != i} 1/r_ij) of the charges `rows` against all n.
+
+    openmp=True runs the rows on all host threads (same arithmetic per row)."""
     p = _pos(pos)
     r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
     g = np.zeros((r.size, 2))
     e = np.zeros(r.size)
-    _check(lib().tco_rows_grad(_p(p), p.shape[0], _p(r), r.size, _p(g), _p(e)), "rows_grad")
+    _check(lib(openmp).tco_rows_grad(_p(p), p.shape[0], _p(r), r.size, _p(g), _p(e)), "rows_grad")
     return g, e
 
 
@@ -197,6 +212,49 @@ def lbfgs(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: 
     _check(lib().tco_lbfgs(_p(p), p.shape[0], int(memory), int(max_iter), float(gtol), float(step0),
                            float(maxstep), float(radius), _p(f), _p(it), _p(rms)), "lbfgs")
     return p, int(it[0]), float(rms[0])
+
+
+def zone_size(q: int, m_min: int, m_max: int, period: int, n: int) -> int:
+    """Active-set size at schedule position q (triangle wave between m_min and m_max)."""
+    return int(lib().tco_zone_size(int(q), int(m_min), int(m_max), int(period), int(n)))
+
+
+def zone_select(pos, local_e, uniforms, m_min: int, m_max: int, period: int, phase: int = 0,
+                kappa: float = -1.0, p_defect: float = 0.8, radius: float = 1.0, wall_tol: float = 1e-9):
+    """Defects, centres and nearest-m zones of Sec. II C; returns (idx, offsets, centres, stats).
+
+    uniforms: (n_sub, 3) in [0, 1); stats = (mu, sigma_e, number of defects)."""
+    p = _pos(pos)
+    n = p.shape[0]
+    e = np.ascontiguousarray(np.asarray(local_e, dtype=np.float64))
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1, 3))
+    ns = u.shape[0]
+    cap = sum(zone_size(phase + s, m_min, m_max, period, n) for s in range(ns))
+    idx = np.zeros(max(cap, 1), dtype=np.int32)
+    off = np.zeros(ns + 1, dtype=np.int64)
+    cen = np.zeros((ns, 2))
+    stats = np.zeros(3)
+    _check(lib().tco_zone_select(_p(p), n, _p(e), float(kappa), float(p_defect), float(radius), float(wall_tol),
+                                 int(m_min), int(m_max), int(period), int(phase), ns, _p(u), _p(idx), _p(off),
+                                 _p(cen), _p(stats)), "zone_select")
+    return idx[:cap], off, cen, stats
+
+
+def cycle(pos, uniforms, m_min: int, m_max: int, period: int, batch: int, step0: float, alpha_min: float,
+          alpha_max: float, steps: int, kappa: float = -1.0, p_defect: float = 0.8, radius: float = 1.0,
+          wall_tol: float = 1e-9):
+    """One optimisation cycle (Sec. II C) in batches; returns (pos, trace, delta, accepted)."""
+    p = _pos(pos).copy()
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1, 3))
+    ns = u.shape[0]
+    nb = -(-ns // batch) if ns else 0
+    trace = np.zeros(nb + 1)
+    d = np.zeros(max(ns, 1))
+    acc = np.zeros(max(ns, 1), dtype=np.uint8)
+    _check(lib().tco_cycle(_p(p), p.shape[0], float(kappa), float(p_defect), float(radius), float(wall_tol),
+                           int(m_min), int(m_max), int(period), ns, int(batch), _p(u), float(step0),
+                           float(alpha_min), float(alpha_max), int(steps), _p(trace), _p(d), _p(acc)), "cycle")
+    return p, trace, d[:ns], acc[:ns]
 
 
 def library_path() -> str:

@@ -19,6 +19,9 @@
  *       optimised by a box-constrained quasi-Newton method with analytic
  *       gradients (Sec. II C step 4).
  *   Sec. II E: each subproblem's gradient is n_act rows against all N charges.
+ *   Sec. II C, steps 2-4: defect threshold on the local energies, centre
+ *       choice (defect charge or uniform point), the zone around the centre,
+ *       and the optimisation cycle built from them.
  *
  * Parity status: every function here is pinned by tests against closed forms,
  * brute force in extended precision, invariants or the paper's asymptotic
@@ -28,6 +31,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define TCO_OK 0
 #define TCO_ERR_INVALID_ARG 1
@@ -38,6 +44,8 @@
 /* A charge with |r| above this radius is outside the hard wall of Eq. (potential);
  * the slack admits positions a projection left one rounding above R = 1. */
 #define TCO_WALL_SLACK 1e-12
+
+#define TCO_PI 3.14159265358979323846
 
 /* ---------------------------------------------------------------- sums --- */
 
@@ -148,10 +156,16 @@ int tco_rows_grad(const double* pos, int64_t n, const int32_t* rows, int64_t m,
                   double* grad_rows, double* e_rows)
 {
     if (n < 0 || m < 0 || (m > 0 && (!rows || !grad_rows || !pos))) return TCO_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < m; ++k)
+        if (rows[k] < 0 || rows[k] >= n) return TCO_ERR_INVALID_ARG;
     int bad = 0;
+    /* Rows are independent; the OpenMP build (libtco_omp.so) splits them over
+     * threads with identical per-row arithmetic, so both builds agree bit for bit. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+#endif
     for (int64_t k = 0; k < m; ++k) {
         int64_t i = rows[k];
-        if (i < 0 || i >= n) return TCO_ERR_INVALID_ARG;
         acc_t gx = {0.0, 0.0}, gy = {0.0, 0.0}, e = {0.0, 0.0};
         grad_row(pos[2 * i], pos[2 * i + 1], pos, n, i, NULL, &gx, &gy, &e);
         grad_rows[2 * k] = acc_get(&gx);
@@ -160,6 +174,16 @@ int tco_rows_grad(const double* pos, int64_t n, const int32_t* rows, int64_t m,
         if (!isfinite(grad_rows[2 * k]) || !isfinite(grad_rows[2 * k + 1])) bad = 1;
     }
     return bad ? TCO_ERR_NONFINITE : TCO_OK;
+}
+
+/* Threads the rows_grad loop runs on: 1 in the plain build. */
+int tco_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 static unsigned char* membership(int64_t n, const int32_t* idx, int64_t m, int* st)
@@ -600,5 +624,163 @@ int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double g
     if (iters_out) *iters_out = it;
     if (rms_out) *rms_out = rms;
     free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
+    return st;
+}
+
+/* ------------------------------------------------ adaptive subdomains --- */
+
+/* Active-set size at schedule position q.  Sec. II C lets the zone radius
+ * r_zone oscillate periodically over a cycle of T subdomain optimisations
+ * without giving the law; the zone is read here as "the m charges nearest to
+ * the centre" and m follows a triangle wave of the given period:
+ *     q' = q mod period,  m = m_min + floor(2 (m_max - m_min) min(q', period - q') / period),
+ * so m = m_min at q' = 0 and m = m_max at q' = period/2; m is capped at n. */
+int64_t tco_zone_size(int64_t q, int64_t m_min, int64_t m_max, int64_t period, int64_t n)
+{
+    int64_t qq = q % period;
+    int64_t tri = qq < period - qq ? qq : period - qq;
+    int64_t m = m_min + (2 * (m_max - m_min) * tri) / period;
+    return m < n ? m : n;
+}
+
+typedef struct {
+    double d2;
+    int32_t i;
+} near_t;
+
+static int near_cmp(const void* a, const void* b)
+{
+    const near_t* p = (const near_t*)a;
+    const near_t* q = (const near_t*)b;
+    if (p->d2 < q->d2) return -1;
+    if (p->d2 > q->d2) return 1;
+    return (p->i > q->i) - (p->i < q->i);
+}
+
+static int int_cmp(const void* a, const void* b)
+{
+    int32_t p = *(const int32_t*)a, q = *(const int32_t*)b;
+    return (p > q) - (p < q);
+}
+
+/* Steps 1-3 of the optimisation cycle of Sec. II C, and the zone of step 4,
+ * for n_sub subdomains at schedule positions phase, phase+1, ...:
+ *   local_e: e_i of step 1 (tco_energy with local_e);
+ *   mu = mean of e_i, sigma_e = its population standard deviation, over all n;
+ *   defects D = { i : e_i > mu + kappa sigma_e and |r_i| < radius - wall_tol }
+ *     in ascending i (the paper's rule is kappa = -1; charges at the wall are
+ *     the boundary population that step 2 does not target);
+ *   subdomain s draws u = uniforms[3s .. 3s+2] in [0,1):
+ *     centre = r_{D[floor(u1 |D|)]} when u0 < p_defect and D is not empty,
+ *     otherwise the area-uniform point sqrt(u1) radius (cos 2 pi u2, sin 2 pi u2);
+ *     active set = the m_s = tco_zone_size(phase + s) charges with the smallest
+ *     (d^2, i), d^2 = (x_i - c_x)^2 + (y_i - c_y)^2, listed in ascending i.
+ * offsets (n_sub + 1) are written; idx holds offsets[n_sub] entries;
+ * centres (2 n_sub), stats (3: mu, sigma_e, |D|) are nullable. */
+int tco_zone_select(const double* pos, int64_t n, const double* local_e, double kappa, double p_defect,
+                    double radius, double wall_tol, int64_t m_min, int64_t m_max, int64_t period,
+                    int64_t phase, int64_t n_sub, const double* uniforms, int32_t* idx, int64_t* offsets,
+                    double* centres, double* stats)
+{
+    if (n < 0 || n_sub < 0 || m_min < 0 || m_max < m_min || period < 1 || phase < 0 || !(radius > 0.0) ||
+        (n_sub > 0 && (!uniforms || !offsets || n < 1 || !pos || !local_e || !idx)))
+        return TCO_ERR_INVALID_ARG;
+    if (n_sub == 0) {
+        if (offsets) offsets[0] = 0;
+        return TCO_OK;
+    }
+    /* step 2: statistics of the local-energy distribution */
+    acc_t s1 = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) acc_add(&s1, local_e[i]);
+    double mu = acc_get(&s1) / (double)n;
+    acc_t s2 = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) acc_add(&s2, (local_e[i] - mu) * (local_e[i] - mu));
+    double sigma = sqrt(acc_get(&s2) / (double)n);
+    double thr = mu + kappa * sigma;
+    double rin = radius - wall_tol;
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    near_t* nr = (near_t*)malloc(sizeof(near_t) * (size_t)n);
+    if (!D || !nr) { free(D); free(nr); return TCO_ERR_NO_MEMORY; }
+    int64_t nd = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[2 * i], y = pos[2 * i + 1];
+        if (local_e[i] > thr && x * x + y * y < rin * rin) D[nd++] = (int32_t)i;
+    }
+    if (stats) { stats[0] = mu; stats[1] = sigma; stats[2] = (double)nd; }
+    offsets[0] = 0;
+    for (int64_t s = 0; s < n_sub; ++s) {
+        /* step 3: the centre */
+        double u0 = uniforms[3 * s], u1 = uniforms[3 * s + 1], u2 = uniforms[3 * s + 2];
+        double cx, cy;
+        if (u0 < p_defect && nd > 0) {
+            int64_t k = (int64_t)(u1 * (double)nd);
+            if (k > nd - 1) k = nd - 1;
+            if (k < 0) k = 0;
+            cx = pos[2 * D[k]];
+            cy = pos[2 * D[k] + 1];
+        } else {
+            double r = sqrt(u1) * radius, t = 2.0 * TCO_PI * u2;
+            cx = r * cos(t);
+            cy = r * sin(t);
+        }
+        if (centres) { centres[2 * s] = cx; centres[2 * s + 1] = cy; }
+        /* step 4's zone: the m_s nearest charges */
+        int64_t m = tco_zone_size(phase + s, m_min, m_max, period, n);
+        for (int64_t i = 0; i < n; ++i) {
+            double dx = pos[2 * i] - cx, dy = pos[2 * i + 1] - cy;
+            nr[i].d2 = dx * dx + dy * dy;
+            nr[i].i = (int32_t)i;
+        }
+        qsort(nr, (size_t)n, sizeof(near_t), near_cmp);
+        int32_t* out = idx + offsets[s];
+        for (int64_t k = 0; k < m; ++k) out[k] = nr[k].i;
+        qsort(out, (size_t)m, sizeof(int32_t), int_cmp);
+        offsets[s + 1] = offsets[s] + m;
+    }
+    free(D);
+    free(nr);
+    return TCO_OK;
+}
+
+/* One optimisation cycle of Sec. II C over n_sub subdomains, taken in batches
+ * of `batch` consecutive subdomains (batch = 1 is the paper's one-at-a-time
+ * cycle).  For each batch b:
+ *   E_b, e_i = tco_energy(pos)                       (step 1; trace[b] = E_b)
+ *   zones    = tco_zone_select(pos, e, ..., phase = b batch)   (steps 2-3)
+ *   each zone relaxes against the batch-start snapshot with tco_subdomain_bb
+ *   (step 4, projected gradient descent with BB steps, `steps` steps)
+ *   tco_accept_sequential applies the relaxed zones in order (dE < 0, no clash).
+ * trace (nullable, n_batches + 1): E before each batch and after the last.
+ * delta, accepted (n_sub): per subdomain, as tco_accept_sequential. */
+int tco_cycle(double* pos, int64_t n, double kappa, double p_defect, double radius, double wall_tol,
+              int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub, int64_t batch,
+              const double* uniforms, double step0, double alpha_min, double alpha_max, int64_t steps,
+              double* trace, double* delta, unsigned char* accepted)
+{
+    if (n < 1 || n_sub < 0 || batch < 1 || !pos || (n_sub > 0 && (!uniforms || !delta || !accepted)))
+        return TCO_ERR_INVALID_ARG;
+    int64_t cap = (m_max < n ? m_max : n) * (batch < n_sub ? batch : (n_sub > 0 ? n_sub : 1));
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(batch + 1));
+    double* act = (double*)malloc(sizeof(double) * 2 * (size_t)(cap > 0 ? cap : 1));
+    if (!e || !idx || !off || !act) { free(e); free(idx); free(off); free(act); return TCO_ERR_NO_MEMORY; }
+    int st = TCO_OK;
+    int64_t nb = 0;
+    for (int64_t b0 = 0; b0 < n_sub && !st; b0 += batch, ++nb) {
+        int64_t k = n_sub - b0 < batch ? n_sub - b0 : batch;
+        double E;
+        st = tco_energy(pos, n, &E, e);
+        if (st) break;
+        if (trace) trace[nb] = E;
+        st = tco_zone_select(pos, n, e, kappa, p_defect, radius, wall_tol, m_min, m_max, period, b0, k,
+                             uniforms + 3 * b0, idx, off, NULL, NULL);
+        for (int64_t s = 0; s < k && !st; ++s)
+            st = tco_subdomain_bb(pos, n, idx + off[s], off[s + 1] - off[s], step0, alpha_min, alpha_max,
+                                  steps, radius, act + 2 * off[s]);
+        if (!st) st = tco_accept_sequential(pos, n, idx, off, k, act, delta + b0, accepted + b0);
+    }
+    if (!st && trace) st = tco_energy(pos, n, &trace[nb], NULL);
+    free(e); free(idx); free(off); free(act);
     return st;
 }

@@ -27,7 +27,7 @@ from ._lib import TCError, RelaxParams
 __all__ = [
     "energy", "grad", "local_energy", "project_disk", "subdomain_delta_energy", "relax_subdomains",
     "coulomb_energy", "CoulombEnergy", "sync_status", "probe_pipes", "relax_last_profile", "TCError", "RelaxParams",
-    "library_path",
+    "library_path", "zone_params", "zone_offsets", "select_subdomains", "cycle",
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED}
@@ -143,18 +143,94 @@ def relax_subdomains(pos, idx=None, offsets=None, world=None, flags=None, *, pre
         n_sub = world.shape[0]
     if world is not None and (world.dtype != torch.int64 or not world.is_cuda or not world.is_contiguous()):
         raise TypeError("world must be a contiguous CUDA int64 tensor of shape (n_sub, 2)")
-    prm = RelaxParams(precision=_prec(precision), optimizer=_OPT[optimizer] if isinstance(optimizer, str) else optimizer,
-                      n_steps=int(n_steps), memory=int(memory), step0=float(step0), alpha_min=float(alpha_min),
-                      alpha_max=float(alpha_max), maxstep=float(maxstep), gtol=float(gtol), radius=float(radius),
-                      polish_steps=int(polish_steps), accept=int(bool(accept)), polish_gtol=float(polish_gtol),
-                      want_energy=int(bool(want_energy)), profile=int(bool(profile)))
+    prm = _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol, radius,
+                        polish_steps, polish_gtol, accept, want_energy, profile)
     raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
     L.check(L.lib().tc_relax_subdomains(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub, _p(world), _p(flags),
                                         C.byref(prm), _p(raw), _stream()), "tc_relax_subdomains")
+    return _results(raw, n_sub)
+
+
+def _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol, radius,
+                  polish_steps, polish_gtol, accept, want_energy, profile) -> RelaxParams:
+    return RelaxParams(precision=_prec(precision), optimizer=_OPT[optimizer] if isinstance(optimizer, str) else optimizer,
+                       n_steps=int(n_steps), memory=int(memory), step0=float(step0), alpha_min=float(alpha_min),
+                       alpha_max=float(alpha_max), maxstep=float(maxstep), gtol=float(gtol), radius=float(radius),
+                       polish_steps=int(polish_steps), accept=int(bool(accept)), polish_gtol=float(polish_gtol),
+                       want_energy=int(bool(want_energy)), profile=int(bool(profile)))
+
+
+def _results(raw: torch.Tensor, n_sub: int) -> RelaxResult:
     raw = raw[:n_sub]
     # the two int32 fields share the fourth 8-byte column of each 32-byte record
     ints = raw.view(torch.int32).view(n_sub, 8)[:, 6:8]
     return RelaxResult(raw[:, 0], raw[:, 1], raw[:, 2], ints[:, 0].clone(), ints[:, 1].clone())
+
+
+def zone_params(m_min: int, m_max: int, period: int, phase: int = 0, kappa: float = -1.0, p_defect: float = 0.8,
+                radius: float = 1.0, wall_tol: float = 1e-9) -> L.ZoneParams:
+    """tc_zone_params: defect threshold mu + kappa sigma_e, centre mix, zone-size triangle wave."""
+    return L.ZoneParams(kappa=float(kappa), p_defect=float(p_defect), radius=float(radius), wall_tol=float(wall_tol),
+                        m_min=int(m_min), m_max=int(m_max), period=int(period), phase=int(phase))
+
+
+def zone_offsets(n: int, n_sub: int, **zone) -> list[int]:
+    """Host CSR offsets of n_sub zones (no GPU work)."""
+    prm = zone_params(**zone)
+    off = (C.c_int64 * (n_sub + 1))()
+    L.check(L.lib().tc_zone_offsets(C.byref(prm), int(n), int(n_sub), C.cast(off, C.c_void_p)), "tc_zone_offsets")
+    return list(off)
+
+
+def _vec(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def select_subdomains(pos, local_e, uniforms, **zone):
+    """Defect threshold, centres and nearest-m zones (Sec. II C steps 2-4).
+
+    uniforms: (n_sub, 3) CUDA float64 in [0, 1).  Returns (idx int32, offsets int64,
+    centres (n_sub, 2), stats (mu, sigma_e, number of defects))."""
+    _pos(pos)
+    _vec(local_e, torch.float64, "local_e")
+    _vec(uniforms, torch.float64, "uniforms")
+    n_sub = uniforms.numel() // 3
+    off_h = zone_offsets(pos.shape[0], n_sub, **zone)
+    prm = zone_params(**zone)
+    idx = torch.empty(max(off_h[-1], 1), dtype=torch.int32, device=pos.device)
+    offsets = torch.empty(n_sub + 1, dtype=torch.int64, device=pos.device)
+    centres = torch.empty((max(n_sub, 1), 2), dtype=torch.float64, device=pos.device)
+    stats = torch.empty(3, dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_select_subdomains(_p(pos), pos.shape[0], _p(local_e), C.byref(prm), n_sub, _p(uniforms),
+                                         _p(idx), _p(offsets), _p(centres), _p(stats), _stream()),
+            "tc_select_subdomains")
+    return idx[:off_h[-1]], offsets, centres[:n_sub], stats
+
+
+def cycle(pos, uniforms, *, batch: int, m_min: int, m_max: int, period: int, phase: int = 0, kappa: float = -1.0,
+          p_defect: float = 0.8, wall_tol: float = 1e-9, local_precision="mixed", precision="mixed",
+          optimizer="bb", n_steps=200, memory=8, step0=1e-9, alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0,
+          radius=1.0, polish_steps=0, polish_gtol=0.0, want_energy=False, profile=False):
+    """One optimisation cycle (Sec. II C) of uniforms.shape[0] subdomains in batches, in place on pos.
+
+    Returns (RelaxResult per subdomain, energy trace: E before each batch and after the last)."""
+    _pos(pos)
+    _vec(uniforms, torch.float64, "uniforms")
+    n_sub = uniforms.numel() // 3
+    prm = L.CycleParams()
+    prm.zone = zone_params(m_min, m_max, period, phase, kappa, p_defect, radius, wall_tol)
+    prm.relax = _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol,
+                              radius, polish_steps, polish_gtol, True, want_energy, profile)
+    prm.batch = int(batch)
+    prm.local_precision = _prec(local_precision)
+    n_batches = -(-n_sub // max(int(batch), 1)) if n_sub else 0
+    raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
+    trace = torch.full((n_batches + 1,), float("nan"), dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_cycle(_p(pos), pos.shape[0], C.byref(prm), n_sub, _p(uniforms), _p(raw), _p(trace),
+                             _stream()), "tc_cycle")
+    return _results(raw, n_sub), trace
 
 
 def relax_last_profile() -> dict:

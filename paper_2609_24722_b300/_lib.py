@@ -71,6 +71,32 @@ class RelaxProfile(C.Structure):
     ]
 
 
+class ZoneParams(C.Structure):
+    """tc_zone_params of include/tc.h."""
+
+    _fields_ = [
+        ("kappa", C.c_double),
+        ("p_defect", C.c_double),
+        ("radius", C.c_double),
+        ("wall_tol", C.c_double),
+        ("m_min", C.c_int32),
+        ("m_max", C.c_int32),
+        ("period", C.c_int32),
+        ("phase", C.c_int32),
+    ]
+
+
+class CycleParams(C.Structure):
+    """tc_cycle_params of include/tc.h."""
+
+    _fields_ = [
+        ("zone", ZoneParams),
+        ("relax", RelaxParams),
+        ("batch", C.c_int32),
+        ("local_precision", C.c_int32),
+    ]
+
+
 RESULT_BYTES = 32  # sizeof(tc_subdomain_result): 3 double + 2 int32
 
 _LIB = None
@@ -99,6 +125,9 @@ def _lib() -> C.CDLL:
             "tc_shutdown": ([], None),
             "tc_probe_pipes": ([vp, vp], C.c_int),
             "tc_relax_last_profile": ([C.POINTER(RelaxProfile)], C.c_int),
+            "tc_zone_offsets": ([C.POINTER(ZoneParams), i64, i32, vp], C.c_int),
+            "tc_select_subdomains": ([vp, i64, vp, C.POINTER(ZoneParams), i32, vp, vp, vp, vp, vp, vp], C.c_int),
+            "tc_cycle": ([vp, i64, C.POINTER(CycleParams), i32, vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sigs.items():
             f = getattr(L, name)

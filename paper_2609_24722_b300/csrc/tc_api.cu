@@ -3,6 +3,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 
 #include "tc_plan.cuh"
@@ -19,7 +20,7 @@ struct Block {
 };
 
 std::mutex g_mu;
-std::map<std::pair<int, cudaStream_t>, Block> g_ws;
+std::map<std::tuple<int, cudaStream_t, int>, Block> g_ws;
 std::map<int, int*> g_status;
 std::map<int, cudaStream_t> g_cap;
 
@@ -41,7 +42,7 @@ void set_last_error(const char* msg)
     g_last_error = msg;
 }
 
-void* workspace(cudaStream_t s, size_t bytes, tc_status* err)
+void* workspace(cudaStream_t s, size_t bytes, tc_status* err, int slot)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -49,7 +50,7 @@ void* workspace(cudaStream_t s, size_t bytes, tc_status* err)
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    Block& b = g_ws[{dev, s}];
+    Block& b = g_ws[{dev, s, slot}];
     if (b.bytes >= bytes && b.ptr) return b.ptr;
     size_t want = align_up(bytes + bytes / 4, size_t(2) << 20);
     if (b.ptr) {
@@ -188,8 +189,8 @@ void tc_shutdown(void)
     int cur = 0;
     cudaGetDevice(&cur);
     for (auto& kv : tc::g_ws) {
-        cudaSetDevice(kv.first.first);
-        cudaStreamSynchronize(kv.first.second);
+        cudaSetDevice(std::get<0>(kv.first));
+        cudaStreamSynchronize(std::get<1>(kv.first));
         cudaFree(kv.second.ptr);
     }
     tc::g_ws.clear();

@@ -107,7 +107,7 @@ __global__ void k_project(double2* __restrict__ pos, int64_t n, double radius, c
 
 // ------------------------------------------------------------ all pairs ---
 
-static tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad, double* energy,
+tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad, double* energy,
                           double* local_e, cudaStream_t s)
 {
     if (n < 0 || (n > 0 && !pos) || (prec != TC_FP64 && prec != TC_MIXED)) return TC_ERR_INVALID_ARG;

@@ -9,10 +9,12 @@
 
 namespace tc {
 
-// Per-(device, stream) scratch workspace.  Grows with cudaMalloc (after a
-// stream synchronisation, so no in-flight kernel uses the old block) and is
-// freed by tc_shutdown().  Returns nullptr and sets *err on failure.
-void* workspace(cudaStream_t s, size_t bytes, tc_status* err);
+// Per-(device, stream, slot) scratch workspace.  Grows with cudaMalloc (after
+// a stream synchronisation, so no in-flight kernel uses the old block) and is
+// freed by tc_shutdown().  Slot 0 is the per-call scratch of every entry
+// point; slot 1 holds buffers that must outlive the calls a driver makes in
+// sequence (the cycle's zones).  Returns nullptr and sets *err on failure.
+void* workspace(cudaStream_t s, size_t bytes, tc_status* err, int slot = 0);
 
 // Per-device status word (device int), allocated on first use.
 int* device_status(tc_status* err);
@@ -53,5 +55,13 @@ struct Carver {
         return p;
     }
 };
+
+// Entry points reused by the cycle driver (same contracts as tc_energy /
+// tc_grad and tc_relax_subdomains).
+tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad, double* energy,
+                   double* local_e, cudaStream_t s);
+tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
+                const int64_t* world, const uint8_t* flags, const tc_relax_params* prm,
+                tc_subdomain_result* out, cudaStream_t s);
 
 }  // namespace tc

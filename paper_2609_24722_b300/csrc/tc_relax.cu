@@ -1025,7 +1025,7 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
     return cuda_status(e, where);
 }
 
-static tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
+tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
                        const int64_t* world, const uint8_t* flags, const tc_relax_params* prm,
                        tc_subdomain_result* out, cudaStream_t s)
 {

@@ -29,6 +29,9 @@ def test_struct_layouts_match_header(lib):
     assert L.RelaxParams.want_energy.offset == 80
     assert L.RESULT_BYTES == 32
     assert C.sizeof(L.RelaxProfile) == 56
+    # tc_zone_params: 4 double, 4 int32; tc_cycle_params: zone, relax, 2 int32
+    assert C.sizeof(L.ZoneParams) == 48 and L.ZoneParams.m_min.offset == 32
+    assert C.sizeof(L.CycleParams) == 144 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 136
 
 
 def test_status_strings(lib):
@@ -46,6 +49,29 @@ def test_argument_errors_are_synchronous_without_touching_a_device(lib):
     assert lib.tc_project_disk(None, 0, -1.0, None, None) == 1
     prm = L.RelaxParams(precision=7)
     assert lib.tc_relax_subdomains(None, 10, None, None, 1, None, None, C.byref(prm), None, None) == 1
+    z = L.ZoneParams(kappa=-1.0, p_defect=0.8, radius=1.0, wall_tol=1e-9, m_min=5, m_max=3, period=4)
+    assert lib.tc_select_subdomains(None, 10, None, C.byref(z), 1, None, None, None, None, None, None) == 1
+    cp = L.CycleParams(zone=z, batch=0)
+    assert lib.tc_cycle(None, 10, C.byref(cp), 1, None, None, None, None) == 1
+
+
+def test_zone_offsets_host_only_matches_oracle(lib):
+    """tc_zone_offsets is host logic: the zone-size schedule equals the oracle's on every position."""
+    import oracle
+
+    for (m_min, m_max, period, phase, n) in [(50, 200, 4, 0, 1000), (200, 5000, 7, 3, 100000), (0, 9, 1, 5, 20),
+                                             (10, 400, 10, 0, 300), (3, 3, 2, 1, 2)]:
+        z = L.ZoneParams(kappa=-1.0, p_defect=0.8, radius=1.0, wall_tol=1e-9, m_min=m_min, m_max=m_max,
+                         period=period, phase=phase)
+        ns = 23
+        off = (C.c_int64 * (ns + 1))()
+        assert lib.tc_zone_offsets(C.byref(z), n, ns, C.cast(off, C.c_void_p)) == 0
+        sizes = [off[s + 1] - off[s] for s in range(ns)]
+        assert off[0] == 0
+        assert sizes == [oracle.zone_size(phase + s, m_min, m_max, period, n) for s in range(ns)]
+    bad = L.ZoneParams(kappa=-1.0, p_defect=1.5, radius=1.0, wall_tol=0.0, m_min=1, m_max=2, period=1)
+    off = (C.c_int64 * 2)()
+    assert lib.tc_zone_offsets(C.byref(bad), 10, 1, C.cast(off, C.c_void_p)) == 1
 
 
 def test_stream_k_owner_formula():

@@ -1,0 +1,156 @@
+"""GPU parity of the adaptive cycle (Sec. II C): defect statistics, centres, nearest-m zones and
+the batched cycle driver against the CPU oracle on the same seeded inputs.
+
+Zones are integer results: they must match the oracle exactly.  The only floating-point inputs to
+those decisions that the two sides may round differently are mu and sigma_e (summation order) and
+the trigonometric centre (CUDA's and the host's sin/cos may differ in the last place); each test
+first checks on the oracle's side that no decision lies within that rounding of its threshold,
+so an exact comparison is meaningful.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2609_24722_b300 as tc
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def margin_ok(pos, e, u, off, idx, cen, st, kappa, wall_tol=1e-9):
+    """No defect decision within 1e-12 of the threshold, no zone boundary within 1e-12 relative."""
+    thr = st[0] + kappa * st[1]
+    if np.any(np.abs(e - thr) <= 1e-12 * abs(thr)):
+        return False
+    for s in range(len(off) - 1):
+        z = idx[off[s]:off[s + 1]]
+        if 0 < len(z) < len(pos):
+            d2 = ((pos - cen[s]) ** 2).sum(1)
+            inside, outside = d2[z].max(), np.delete(d2, z).min()
+            if outside - inside <= 1e-12 * max(outside, 1e-300) and outside != inside:
+                return False
+    return True
+
+
+def select_both(pos, e, u, **kw):
+    idx_o, off_o, cen_o, st_o = oracle.zone_select(pos, e, u, **kw)
+    idx, off, cen, st = tc.select_subdomains(T(pos), T(e), T(u), **kw)
+    torch.cuda.synchronize()
+    return (idx_o, off_o, cen_o, st_o), (idx.cpu().numpy(), off.cpu().numpy(), cen.cpu().numpy(), st.cpu().numpy())
+
+
+@pytest.mark.parametrize("n,seed", [(700, 1), (2000, 2), (5003, 3)])
+def test_select_matches_oracle(n, seed):
+    pos = synth.lattice_disk(n, seed, 0.05)
+    _, e = oracle.energy(pos, local=True)
+    u = np.random.default_rng(seed).random((37, 3))
+    kw = dict(m_min=17, m_max=min(n - 1, 900), period=9, phase=4)
+    (io, oo, co, so), (ig, og, cg, sg) = select_both(pos, e, u, **kw)
+    assert margin_ok(pos, e, u, oo, io, co, so, -1.0)
+    np.testing.assert_array_equal(og, oo)
+    np.testing.assert_array_equal(ig, io)
+    assert sg[2] == so[2]
+    assert abs(sg[0] - so[0]) <= 1e-15 * so[0] and abs(sg[1] - so[1]) <= 1e-12 * so[1]
+    np.testing.assert_allclose(cg, co, rtol=0, atol=4e-16)
+
+
+def test_select_edge_cases():
+    """m = 0, m >= n, one charge, exact ties broken by index, all-defect and no-defect draws."""
+    g = np.arange(-6, 7) / 8.0
+    grid = np.array([(x, y) for x in g for y in g if x * x + y * y <= 0.75])
+    grid = grid[np.random.default_rng(2).permutation(len(grid))]
+    n = len(grid)
+    e = np.zeros(n)
+    u = np.array([[0.5, 0.0, 0.3], [0.2, 0.0, 0.9]])
+    for m in [0, 1, 5, 6, 9, 13, 20, 21, n - 1, n, n + 5]:
+        (io, oo, co, so), (ig, og, cg, sg) = select_both(grid, e, u, m_min=m, m_max=m, period=1, kappa=1.0)
+        np.testing.assert_array_equal(og, oo)
+        np.testing.assert_array_equal(ig, io)
+    # a single charge
+    one = np.array([[0.1, -0.2]])
+    (io, oo, _, _), (ig, og, _, _) = select_both(one, np.array([0.0]), u, m_min=0, m_max=3, period=2)
+    np.testing.assert_array_equal(og, oo)
+    np.testing.assert_array_equal(ig, io)
+    # every centre a defect charge, then none
+    pos = synth.arcsine_disk(900, 4)
+    _, e = oracle.energy(pos, local=True)
+    uu = np.random.default_rng(9).random((25, 3))
+    for pd in [1.0, 0.0]:
+        (io, oo, co, so), (ig, og, cg, sg) = select_both(pos, e, uu, m_min=10, m_max=200, period=5, p_defect=pd)
+        np.testing.assert_array_equal(ig, io)
+        np.testing.assert_allclose(cg, co, rtol=0, atol=4e-16)
+    # zero subdomains
+    idx, off, cen, st = tc.select_subdomains(T(pos), T(e), torch.zeros((0, 3), dtype=torch.float64, device=DEV),
+                                             m_min=1, m_max=2, period=1)
+    assert off.cpu().tolist() == [0]
+
+
+def test_select_at_full_size_sampled():
+    """N = 100 000 lattice background, 64 zones of 200..5000: the zones equal the oracle's."""
+    n = 100_000
+    pos = synth.lattice_disk(n, 0)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    p = T(pos)
+    _, e = tc.local_energy(p, "fp64")
+    e_np = e.cpu().numpy()
+    u = np.random.default_rng(12).random((64, 3))
+    kw = dict(m_min=200, m_max=5000, period=16, phase=0)
+    idx, off, cen, st = tc.select_subdomains(p, e, T(u), **kw)
+    torch.cuda.synchronize()
+    io, oo, co, so = oracle.zone_select(pos, e_np, u, **kw)
+    assert margin_ok(pos, e_np, u, oo, io, co, so, -1.0)
+    np.testing.assert_array_equal(off.cpu().numpy(), oo)
+    np.testing.assert_array_equal(idx.cpu().numpy(), io)
+
+
+@pytest.mark.parametrize("batch", [1, 3, 8])
+def test_cycle_fp64_matches_oracle(batch):
+    """float64 local energies and float64 BB relaxation: the cycle follows the oracle's cycle."""
+    n = 1500
+    pos = synth.lattice_disk(n, 21, 0.05)
+    u = np.random.default_rng(22).random((8, 3))
+    eta = 1e-4 / n
+    kw = dict(m_min=20, m_max=200, period=4)
+    po, trace_o, do, ao = oracle.cycle(pos, u, batch=batch, step0=eta, alpha_min=0.0, alpha_max=10 * eta, steps=10,
+                                       **kw)
+    p = T(pos.copy())
+    r, trace = tc.cycle(p, T(u), batch=batch, local_precision="fp64", precision="fp64", optimizer="bb", n_steps=10,
+                        step0=eta, alpha_min=0.0, alpha_max=10 * eta, **kw)
+    tc.sync_status()
+    np.testing.assert_array_equal(r.status.cpu().numpy(), ao)
+    np.testing.assert_allclose(p.cpu().numpy(), po, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(trace.cpu().numpy(), trace_o, rtol=1e-13)
+    d = r.delta_e.cpu().numpy()
+    m = ao != 2
+    np.testing.assert_allclose(d[m], do[m], rtol=1e-9, atol=1e-9)
+
+
+def test_cycle_mixed_lowers_energy_and_books_it():
+    """Mixed local energies and mixed relaxation at N = 20 000: every batch lowers E by its accepted dE."""
+    n = 20_000
+    pos = synth.lattice_disk(n, 5)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    p = T(pos.copy())
+    u = np.random.default_rng(31).random((24, 3))
+    eta = 1e-4 / n
+    r, trace = tc.cycle(p, T(u), batch=8, m_min=100, m_max=1500, period=12, local_precision="fp64",
+                        precision="mixed", optimizer="bb", n_steps=40, step0=eta, alpha_min=0.0, alpha_max=10 * eta)
+    tc.sync_status()
+    tr = trace.cpu().numpy()
+    st = r.status.cpu().numpy()
+    d = r.delta_e.cpu().numpy()
+    assert np.all(np.diff(tr) <= 0) and (st == 1).sum() >= 1
+    for b in range(3):
+        sl = slice(8 * b, 8 * b + 8)
+        assert abs((tr[b + 1] - tr[b]) - d[sl][st[sl] == 1].sum()) <= 1e-12 * tr[b]
+    assert abs(tr[-1] - oracle.energy(p.cpu().numpy())) <= 1e-13 * tr[-1]

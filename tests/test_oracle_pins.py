@@ -388,3 +388,126 @@ def test_error_statuses():
     with pytest.raises(oracle.OracleError) as e:
         oracle.delta_energy(synth.arcsine_disk(10, 0), [3, 3], np.zeros((2, 2)))
     assert e.value.code == 1
+
+
+def test_openmp_build_is_bit_identical():
+    """The OpenMP build only splits independent rows over threads: results equal the plain build."""
+    pos = synth.arcsine_disk(3000, 5)
+    rows = np.arange(0, 3000, 3, dtype=np.int32)
+    g1, e1 = oracle.rows_grad(pos, rows)
+    g2, e2 = oracle.rows_grad(pos, rows, openmp=True)
+    assert oracle.threads() == 1 and oracle.threads(True) >= 1
+    assert np.array_equal(g1, g2) and np.array_equal(e1, e2)
+    with pytest.raises(oracle.OracleError):
+        oracle.rows_grad(pos, np.array([0, 3000], dtype=np.int32), openmp=True)
+
+
+# ---------------------------------------------------------------- the cycle (Sec. II C) ---
+
+def test_zone_size_triangle_wave():
+    """m = m_min at q = 0 mod P, m_max at q = P/2, linear in between, symmetric, capped at n."""
+    assert [oracle.zone_size(q, 50, 200, 4, 10 ** 6) for q in range(9)] == [50, 125, 200, 125, 50, 125, 200, 125, 50]
+    assert [oracle.zone_size(q, 50, 200, 5, 10 ** 6) for q in range(5)] == [50, 110, 170, 170, 110]
+    assert {oracle.zone_size(q, 7, 900, 1, 10 ** 6) for q in range(10)} == {7}
+    assert oracle.zone_size(2, 50, 200, 4, 120) == 120
+
+
+def _zones(pos, e, u, **kw):
+    idx, off, cen, st = oracle.zone_select(pos, e, u, **kw)
+    return [idx[off[s]:off[s + 1]] for s in range(len(off) - 1)], off, cen, st
+
+
+def test_zone_select_statistics_defects_and_nearest_sets():
+    """mu and sigma_e equal numpy's mean and population std; the defect count follows the rule;
+    each zone holds exactly m charges, ascending, and none outside it is nearer to the centre."""
+    n = 1500
+    pos = synth.lattice_disk(n, 11, 0.05)
+    _, e = oracle.energy(pos, local=True)
+    u = np.random.default_rng(4).random((12, 3))
+    zones, off, cen, st = _zones(pos, e, u, m_min=30, m_max=300, period=6, phase=2)
+    assert abs(st[0] - e.mean()) <= 1e-15 * e.mean()
+    assert abs(st[1] - e.std()) <= 1e-12 * e.std()
+    r = np.hypot(pos[:, 0], pos[:, 1])
+    thr = e.mean() - e.std()
+    n_def = int(np.sum((e > thr) & (r < 1 - 1e-9)))
+    assert st[2] == n_def and 0 < n_def < n
+    for s, z in enumerate(zones):
+        assert len(z) == oracle.zone_size(2 + s, 30, 300, 6, n)
+        assert np.all(np.diff(z) > 0)
+        d2 = ((pos - cen[s]) ** 2).sum(1)
+        out = np.setdiff1d(np.arange(n), z)
+        assert d2[z].max() <= d2[out].min()
+        assert np.hypot(*cen[s]) <= 1.0
+
+
+def test_zone_centres_follow_the_mix():
+    """p_defect = 1: every centre is a defect charge (the zone's nearest, at distance 0);
+    p_defect = 0: centres are area-uniform in the disk (|c|^2 ~ U(0,1), angle ~ U(0, 2 pi))."""
+    from scipy import stats as ss
+
+    n = 800
+    pos = synth.arcsine_disk(n, 3)
+    _, e = oracle.energy(pos, local=True)
+    u = np.random.default_rng(5).random((40, 3))
+    zones, _, cen, st = _zones(pos, e, u, m_min=5, m_max=5, period=1, p_defect=1.0)
+    r = np.hypot(pos[:, 0], pos[:, 1])
+    defects = np.flatnonzero((e > st[0] - st[1]) & (r < 1 - 1e-9))
+    for s in range(40):
+        k = np.flatnonzero((pos == cen[s]).all(1))
+        assert len(k) == 1 and k[0] in defects and k[0] in zones[s]
+        # floor(u1 |D|) picks the defect
+        assert k[0] == defects[int(u[s, 1] * len(defects))]
+    u = np.random.default_rng(6).random((3000, 3))
+    _, _, cen, _ = _zones(pos, e, u, m_min=0, m_max=0, period=1, p_defect=0.0)
+    rr = (cen ** 2).sum(1)
+    assert ss.kstest(rr, "uniform").pvalue > 1e-3
+    th = np.mod(np.arctan2(cen[:, 1], cen[:, 0]), 2 * np.pi) / (2 * np.pi)
+    assert ss.kstest(th, "uniform").pvalue > 1e-3
+
+
+def test_zone_ties_break_by_index():
+    """Charges on a dyadic grid have exact, equal distances to the centre (0, 0): the zone takes the
+    ring members with the smallest indices, and m >= n takes every charge."""
+    g = np.arange(-6, 7) / 8.0
+    pos = np.array([(x, y) for x in g for y in g if x * x + y * y <= 0.75])
+    rng = np.random.default_rng(2)
+    pos = pos[rng.permutation(len(pos))]
+    n = len(pos)
+    e = np.zeros(n)  # flat energies: no defects, so the centre is the uniform draw
+    u = np.array([[0.5, 0.0, 0.3]])  # u1 = 0: the centre is the origin
+    d2 = (pos ** 2).sum(1)
+    for m in [1, 5, 6, 9, 13, 20, 21, n, n + 5]:
+        zones, _, cen, st = _zones(pos, e, u, m_min=m, m_max=m, period=1, kappa=1.0)
+        assert st[2] == 0 and np.all(cen[0] == 0)
+        z = zones[0]
+        mm = min(m, n)
+        assert len(z) == mm
+        if mm < n:
+            cut = np.sort(d2)[mm - 1]
+            below = np.flatnonzero(d2 < cut)
+            ties = np.flatnonzero(d2 == cut)[: mm - len(below)]
+            assert np.array_equal(z, np.sort(np.concatenate([below, ties])))
+
+
+def test_cycle_energy_bookkeeping():
+    """Over a cycle the energy falls by exactly the accepted pairwise changes: E_(b+1) - E_b equals
+    the sum of dE_s over the batch's accepted subdomains; rejected and skipped ones change nothing;
+    batch = 1 never skips."""
+    n = 1200
+    pos = synth.lattice_disk(n, 9, 0.05)
+    u = np.random.default_rng(8).random((9, 3))
+    eta = 1e-4 / n
+    for batch in [4, 1]:
+        p, trace, d, acc = oracle.cycle(pos, u, m_min=20, m_max=160, period=4, batch=batch, step0=eta,
+                                        alpha_min=0.0, alpha_max=10 * eta, steps=8)
+        nb = -(-9 // batch)
+        assert len(trace) == nb + 1 and np.all(np.diff(trace) <= 0)
+        assert abs(trace[-1] - oracle.energy(p)) <= 1e-15 * trace[-1]
+        for b in range(nb):
+            sl = slice(b * batch, min(9, (b + 1) * batch))
+            dsum = d[sl][acc[sl] == 1].sum()
+            assert abs((trace[b + 1] - trace[b]) - dsum) <= 1e-12 * trace[b]
+        assert np.all(d[acc == 1] < 0) and np.all(d[acc == 0] >= 0)
+        assert (acc == 1).sum() >= 1
+        if batch == 1:
+            assert not np.any(acc == 2)
