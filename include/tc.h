@@ -121,6 +121,23 @@ tc_status tc_subdomain_delta_energy(const double* pos, int64_t n, const int32_t*
                                     const int64_t* offsets, int32_t n_sub, const double* new_active,
                                     double* delta, tc_stream stream);
 
+/* The same energy change in the difference form, evaluated in float32 (the
+ * paper has no counterpart: it is the float32 variant of E_sub(new) -
+ * E_sub(old) of Sec. II D that stays accurate for small moves).  For a pair
+ * with old separation d whose separation moves by u (d' = d + u),
+ *     1/|d'| - 1/|d| = -u.(d + d') / (|d| |d'| (|d| + |d'|)),
+ * so the result carries an error proportional to the moves, not to E_sub:
+ *     |delta[s] - exact| <= bound[s] = 2^-15 sum over the pairs of |u|_a (1/|d| + 1/|d'|) / |d'|,
+ * |u|_a the L1 norm of the moves entering u (valid for separations above ~1e-6;
+ * a pair that ends nearly on top of another charge makes the bound huge).
+ * Float64 pair differences (tc_subdomain_delta_energy) instead lose about
+ * 1e-16 E_sub to cancellation, which dominates when the moves are small.
+ *   arguments as tc_subdomain_delta_energy; bound [n_sub] device, nullable.
+ * A pair whose float32 separation is exactly zero gives TC_ERR_NONFINITE. */
+tc_status tc_subdomain_delta_energy_mixed(const double* pos, int64_t n, const int32_t* idx,
+                                          const int64_t* offsets, int32_t n_sub, const double* new_active,
+                                          double* delta, double* bound, tc_stream stream);
+
 /* Hard wall of Eq. (potential) as a projection, in place:
  *   r <- r min(1, radius/|r|);  a charge with flags[i] != 0 is pinned to the
  *   unit circle (the boundary population of Sec. II B): r <- r/|r| (unchanged

@@ -27,7 +27,7 @@ from ._lib import TCError, RelaxParams
 __all__ = [
     "energy", "grad", "local_energy", "project_disk", "subdomain_delta_energy", "relax_subdomains",
     "coulomb_energy", "CoulombEnergy", "sync_status", "probe_pipes", "relax_last_profile", "TCError", "RelaxParams",
-    "library_path", "zone_params", "zone_offsets", "select_subdomains", "cycle",
+    "library_path", "zone_params", "zone_offsets", "select_subdomains", "cycle", "subdomain_delta_energy_mixed",
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED}
@@ -117,6 +117,20 @@ def subdomain_delta_energy(pos, idx, offsets, new_active) -> torch.Tensor:
     L.check(L.lib().tc_subdomain_delta_energy(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub,
                                               _p(new_active), _p(out), _stream()), "tc_subdomain_delta_energy")
     return out
+
+
+def subdomain_delta_energy_mixed(pos, idx, offsets, new_active) -> tuple[torch.Tensor, torch.Tensor]:
+    """Difference-form float32 energy change of each subdomain and its error bound (delta, bound)."""
+    _pos(pos)
+    _csr(idx, offsets)
+    _pos(new_active, "new_active")
+    n_sub = offsets.numel() - 1
+    out = torch.empty(max(n_sub, 0), dtype=torch.float64, device=pos.device)
+    bound = torch.empty(max(n_sub, 0), dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_subdomain_delta_energy_mixed(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub,
+                                                    _p(new_active), _p(out), _p(bound), _stream()),
+            "tc_subdomain_delta_energy_mixed")
+    return out, bound
 
 
 @dataclass

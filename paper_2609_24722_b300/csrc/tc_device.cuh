@@ -44,6 +44,14 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
     return y;
 }
 
+// One MUFU.RCP: approximate 1/x in float32.
+__device__ __forceinline__ float rcp_mufu(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // float64 1/sqrt(r2): a float32 seed y0, then one correction step of the
 // binomial series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3) with
 // e = 1 - r2 y0^2.
@@ -162,13 +170,30 @@ __host__ __device__ __forceinline__ d4 make_d4(double x, double y, double z, dou
     return r;
 }
 
+// A charge for the difference-form energy change: old position split hi/lo
+// and its move new - old in float32 (zero for charges that stay), 32 bytes.
+struct alignas(32) f8 {
+    float4 p;   // (x_hi, y_hi, x_lo, y_lo) of the old position
+    float2 d;   // move (dx, dy)
+    float2 pad;
+};
+__host__ __device__ __forceinline__ f8 make_f8(float4 p, float dx, float dy)
+{
+    f8 r;
+    r.p = p;
+    r.d = make_float2(dx, dy);
+    r.pad = make_float2(0.f, 0.f);
+    return r;
+}
+
 // Pass flavours.
-enum PassKind { PASS_MIXED = 0, PASS_F64 = 1, PASS_DELTA = 2 };
+enum PassKind { PASS_MIXED = 0, PASS_F64 = 1, PASS_DELTA = 2, PASS_DMIX = 3 };
 
 template <int KIND> struct SrcT;
 template <> struct SrcT<PASS_MIXED> { using type = float4; };   // (x_hi, y_hi, x_lo, y_lo)
 template <> struct SrcT<PASS_F64> { using type = double2; };    // (x, y)
 template <> struct SrcT<PASS_DELTA> { using type = d4; };  // (x_old, y_old, x_new, y_new)
+template <> struct SrcT<PASS_DMIX> { using type = f8; };   // old split + move
 
 // Arguments of one pass launch.
 struct PassArgs {
@@ -177,8 +202,9 @@ struct PassArgs {
     int S;              // problems
     int64_t W;          // total units
     int64_t M;          // total rows (row arrays and partial-slot stride)
-    const void* rows;   // row positions: float4 split (mixed), double2 (f64), d4 old/new (delta)
-    const void* snap;   // snapshot: float4 split (mixed), double2 (f64, delta)
+    const void* rows;   // row positions: float4 split (mixed), double2 (f64), d4 old/new (delta),
+                        // f8 old split + move (difference form)
+    const void* snap;   // snapshot: float4 split (mixed, difference form), double2 (f64, delta)
     const uint32_t* mask;
     const int* active;  // nullable; problems with active[s] == 0 are skipped
     double* part_e;     // [slots x M] row partial energies (or energy changes)

@@ -8,6 +8,8 @@
 // reducer can add the slots of a row in a fixed order (deterministic).
 #pragma once
 
+#include <type_traits>
+
 #include "tc_device.cuh"
 
 namespace tc {
@@ -170,6 +172,78 @@ template <int R> struct RowState<PASS_DELTA, R> {
     __device__ double e(int r) const { return dh[r] + dl[r]; }
 };
 
+// ---- difference-form energy change in float32 (rows and own sources carry a move) ----
+// For a pair with old separation d and move m of the separation (the row's move
+// minus the source's), the new separation is d' = d + m and
+//     1/|d'| - 1/|d| = (|d|^2 - |d'|^2) / (|d| |d'| (|d| + |d'|)),
+//     |d|^2 - |d'|^2 = -m . (d + d'),
+// which stays accurate relative to the move instead of cancelling two 1/r terms.
+// Alongside it accumulates b = |m|_a / |d'| (1/|d| + 1/|d'|), |m|_a the L1 norm of
+// the moves entering m (the row's, plus the source's for own rows).  b bounds
+// |term| <= |m| / (|d| |d'|) and the first-order effect of float32 errors in d
+// (|grad(1/|d'|) - grad(1/|d|)| <= |m| (|d| + |d'|) / (|d|^2 |d'|^2), times
+// |error of d| <= 2^-22 |d|) and in m (|error of m| / |d'|^2 <= 2^-23 |m|_a / |d'|^2),
+// so sum(b) scales the error bound of the float32 evaluation.
+template <int R> struct RowState<PASS_DMIX, R> {
+    float xh[R], yh[R], xl[R], yl[R], mx[R], my[R];
+    float dh[R], dl[R], bs[R];
+
+    __device__ void load(const f8* rows, int64_t base, int64_t rl0, int stride, int m)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t rl = rl0 + (int64_t)r * stride;
+            f8 q = (rl < m) ? rows[base + rl] : make_f8(make_float4(kFarRow32, kFarRow32, 0.f, 0.f), 0.f, 0.f);
+            xh[r] = q.p.x; yh[r] = q.p.y; xl[r] = q.p.z; yl[r] = q.p.w;
+            mx[r] = q.d.x; my[r] = q.d.y;
+            dh[r] = dl[r] = bs[r] = 0.f;
+        }
+    }
+
+    // OWN = false: snapshot sources (they stay); OWN = true: own rows (they move too).
+    template <int T, bool SELF, bool OWN>
+    __device__ __forceinline__ void tile(const f8* __restrict__ s, const int (&jself)[R], float escale)
+    {
+        float dt[R], bt[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) dt[r] = bt[r] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < T; ++j) {
+            const f8 q = s[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float dx = (xh[r] - q.p.x) + (xl[r] - q.p.z);
+                const float dy = (yh[r] - q.p.y) + (yl[r] - q.p.w);
+                const float ux = OWN ? mx[r] - q.d.x : mx[r];
+                const float uy = OWN ? my[r] - q.d.y : my[r];
+                const float px = dx + ux, py = dy + uy;
+                const float r2 = fmaf(dx, dx, dy * dy), r2n = fmaf(px, px, py * py);
+                const float i0 = rsqrt_mufu(r2), i1 = rsqrt_mufu(r2n);
+                const float num = -fmaf(ux, dx + px, uy * (dy + py));
+                const float q01 = i0 * i1;
+                float t = num * q01 * rcp_mufu(fmaf(r2, i0, r2n * i1));
+                const float ua = OWN ? (fabsf(mx[r]) + fabsf(my[r])) + (fabsf(q.d.x) + fabsf(q.d.y))
+                                     : fabsf(mx[r]) + fabsf(my[r]);
+                float b = ua * (i1 * (i0 + i1));
+                if (SELF) {
+                    t = (j == jself[r]) ? 0.f : t;
+                    b = (j == jself[r]) ? 0.f : b;
+                }
+                dt[r] += t;
+                bt[r] += b;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            df_add(dh[r], dl[r], dt[r] * escale);
+            bs[r] += bt[r] * escale;
+        }
+    }
+
+    __device__ double e(int r) const { return (double)dh[r] + (double)dl[r]; }
+    __device__ double bound(int r) const { return (double)bs[r]; }
+};
+
 // Source entry t*T + tid of a problem's tile list, with masking and padding.
 template <int KIND, int T>
 __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a, const Prob& p, int t, int tid)
@@ -184,6 +258,9 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
         }
         if constexpr (KIND == PASS_MIXED) {
             return ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
+        } else if constexpr (KIND == PASS_DMIX) {
+            return make_f8(ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f),
+                           0.f, 0.f);
         } else if constexpr (KIND == PASS_F64) {
             return ok ? static_cast<const double2*>(a.snap)[p.snap_b + j] : make_double2(kFar64, kFar64);
         } else {
@@ -195,6 +272,9 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
         bool ok = j < p.m;
         if constexpr (KIND == PASS_MIXED) {
             return ok ? static_cast<const float4*>(a.rows)[p.row_base + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
+        } else if constexpr (KIND == PASS_DMIX) {
+            return ok ? static_cast<const f8*>(a.rows)[p.row_base + j]
+                      : make_f8(make_float4(kFar32, kFar32, 0.f, 0.f), 0.f, 0.f);
         } else if constexpr (KIND == PASS_F64) {
             return ok ? static_cast<const double2*>(a.rows)[p.row_base + j] : make_double2(kFar64, kFar64);
         } else {
@@ -247,13 +327,14 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
 #pragma unroll
                 for (int r = 0; r < R; ++r) jself[r] = (int)(rl0 + r * THREADS) - tp * T;
                 const double sc = own ? 0.5 : 1.0;
-                if constexpr (KIND == PASS_DELTA) {
+                if constexpr (KIND == PASS_DELTA || KIND == PASS_DMIX) {
+                    using sc_t = typename std::conditional<KIND == PASS_DELTA, double, float>::type;
                     if (!own)
-                        rs.template tile<T, false, false>(tile[buf], jself, sc);
+                        rs.template tile<T, false, false>(tile[buf], jself, (sc_t)sc);
                     else if (self)
-                        rs.template tile<T, true, true>(tile[buf], jself, sc);
+                        rs.template tile<T, true, true>(tile[buf], jself, (sc_t)sc);
                     else
-                        rs.template tile<T, false, true>(tile[buf], jself, sc);
+                        rs.template tile<T, false, true>(tile[buf], jself, (sc_t)sc);
                 } else {
                     if (self)
                         rs.template tile<T, true, WANT_E, WANT_G>(tile[buf], jself, (float)sc);
@@ -269,8 +350,10 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
                 const int64_t rl = rl0 + (int64_t)r * THREADS;
                 if (rl < p.m) {
                     const int64_t o = slot * a.M + p.row_base + rl - row_sub;
-                    if (WANT_E || KIND == PASS_DELTA) a.part_e[o] = rs.e(r);
-                    if constexpr (KIND != PASS_DELTA) {
+                    if (WANT_E || KIND == PASS_DELTA || KIND == PASS_DMIX) a.part_e[o] = rs.e(r);
+                    if constexpr (KIND == PASS_DMIX) {
+                        if (a.part_g) a.part_g[o] = make_double2(rs.bound(r), 0.0);
+                    } else if constexpr (KIND != PASS_DELTA) {
                         if (WANT_G) a.part_g[o] = rs.g(r);
                     }
                 }

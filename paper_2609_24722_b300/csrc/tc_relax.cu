@@ -791,6 +791,47 @@ __global__ void k_rows4(RelaxDev d, const double2* __restrict__ newpos)
     }
 }
 
+// Rows of the difference-form pass: old position split hi/lo and the move
+// new - old (rounded once to float32).
+__global__ void k_rows8(RelaxDev d, const double2* __restrict__ newpos, f8* __restrict__ rows8)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const double2 o = d.pos[d.gidx[rr]];
+        const double2 nw = newpos[rr];
+        if (!isfinite(nw.x) || !isfinite(nw.y)) set_status(d.st, ST_NONFINITE);
+        rows8[rr] = make_f8(split4(o.x, o.y), (float)(nw.x - o.x), (float)(nw.y - o.y));
+    }
+}
+
+// Per problem: the difference-form energy change and its error bound.
+// |float32 evaluation - exact| <= 2^-15 sum(b), u = 2^-24: each term is within
+// about 25 u b of its exact value (separations from hi/lo differences, moves
+// rounded once, two MUFU.RSQ and one MUFU.RCP of at most ~2 ulp, a handful of
+// roundings), |term| <= b, and a tile sum of 256 float32 terms adds at most
+// 256 u sum |term|; 512 u covers both.  Valid for separations above ~1e-6 (below
+// that the absolute 2^-47 error of the lo-part differences is not covered).
+__global__ void __launch_bounds__(kUpd) k_dmix_sums(RelaxDev d, const double* __restrict__ part_e,
+                                                     const double2* __restrict__ part_b, SlotView v,
+                                                     double* __restrict__ out, double* __restrict__ bound)
+{
+    __shared__ double sh[kUpd];
+    const int s = blockIdx.x;
+    const Prob p = d.prob[s];
+    double hi = 0.0, lo = 0.0, b = 0.0;
+    TC_ROWS(p)
+    {
+        dd_add(hi, lo, sum_e(p, rl, part_e, v));
+        b += sum_g(p, rl, part_b, v).x;
+    }
+    const double t = block_sum<kUpd>(hi, sh) + block_sum<kUpd>(lo, sh);
+    b = block_sum<kUpd>(b, sh);
+    if (threadIdx.x == 0) {
+        out[s] = t;
+        if (bound) bound[s] = ldexp(b, -15);
+        if (!isfinite(t)) set_status(d.st, ST_NONFINITE);
+    }
+}
+
 // Per problem: sum of its rows' partials (compensated) into out[s].
 __global__ void __launch_bounds__(kUpd) k_problem_sums(RelaxDev d, const double* __restrict__ part_e, SlotView v,
                                                         double* out, const int* __restrict__ only)
@@ -1322,12 +1363,14 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
 }
 
 // tc_subdomain_delta_energy: every subdomain against pos, in one pass.
+// Energy change of every subdomain against pos: float64 pair differences
+// (mixed = false) or the float32 difference form with its error bound.
 static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
-                           const double* new_active, double* delta, cudaStream_t s)
+                           const double* new_active, double* delta, bool mixed, double* bound, cudaStream_t s)
 {
     if (n < 0 || n_sub < 0 || (n > 0 && !pos) || (n_sub > 0 && (!offsets || !delta)) ||
         (reinterpret_cast<uintptr_t>(pos) & 15) || (reinterpret_cast<uintptr_t>(new_active) & 15) ||
-        (reinterpret_cast<uintptr_t>(delta) & 7))
+        (reinterpret_cast<uintptr_t>(delta) & 7) || (reinterpret_cast<uintptr_t>(bound) & 7))
         return TC_ERR_INVALID_ARG;
     if (n_sub == 0) return TC_OK;
     if (n > INT32_MAX) return TC_ERR_INVALID_ARG;
@@ -1356,16 +1399,22 @@ static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, con
     P.M = off[n_sub];
     if (P.M > 0 && (!idx || !new_active)) return TC_ERR_INVALID_ARG;
     plan_units(P);
-    const int64_t G = pass_grid<PASS_DELTA, false, false>(P.W);
+    const int64_t G = mixed ? pass_grid<PASS_DMIX, false, false>(P.W) : pass_grid<PASS_DELTA, false, false>(P.W);
     const int64_t slots = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G);
     const int64_t M = P.M;
     Carver c;
+    f8* rows8 = nullptr;
+    float4* snap_split = nullptr;
+    double2* part_b = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, double*& part_e) {
         probd = cv.take<Prob>(n_sub);
         d.gidx = cv.take<int32_t>(M);
-        d.rows4 = cv.take<d4>(M);
+        d.rows4 = cv.take<d4>(mixed ? 0 : M);
+        rows8 = cv.take<f8>(mixed ? M : 0);
+        snap_split = cv.take<float4>(mixed ? n : 0);
         d.mask = cv.take<uint32_t>(mask_words);
         part_e = cv.take<double>(slots * std::max<int64_t>(M, 1));
+        part_b = cv.take<double2>(mixed ? slots * std::max<int64_t>(M, 1) : 0);
     };
     RelaxDev d{};
     Prob* probd;
@@ -1391,22 +1440,33 @@ static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, con
         d.xs = nullptr;
         k_rows_init<<<eb, 256, 0, s>>>(d, n, 1.0, 0);
         k_mask_build<<<eb, 256, 0, s>>>(d);
-        k_rows4<<<eb, 256, 0, s>>>(d, reinterpret_cast<const double2*>(new_active));
+        if (mixed) {
+            const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8L * sm_count()));
+            k_split_pos<<<nb, 256, 0, s>>>(reinterpret_cast<const double2*>(pos), n, snap_split, st);
+            k_rows8<<<eb, 256, 0, s>>>(d, reinterpret_cast<const double2*>(new_active), rows8);
+        } else {
+            k_rows4<<<eb, 256, 0, s>>>(d, reinterpret_cast<const double2*>(new_active));
+        }
     }
     PassArgs a{};
     a.prob = probd;
     a.S = n_sub;
     a.W = P.W;
     a.M = std::max<int64_t>(M, 1);
-    a.rows = d.rows4;
-    a.snap = pos;
+    a.rows = mixed ? static_cast<const void*>(rows8) : static_cast<const void*>(d.rows4);
+    a.snap = mixed ? static_cast<const void*>(snap_split) : static_cast<const void*>(pos);
     a.mask = d.mask;
     a.active = nullptr;
     a.part_e = part_e;
-    a.part_g = nullptr;
-    if ((e = launch_pass<PASS_DELTA, false, false>(a, G, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+    a.part_g = part_b;
     SlotView v{P.W, G, 0, a.M, 0};
-    k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, delta, nullptr);
+    if (mixed) {
+        if ((e = launch_pass<PASS_DMIX, false, false>(a, G, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+        k_dmix_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, part_b, v, delta, bound);
+    } else {
+        if ((e = launch_pass<PASS_DELTA, false, false>(a, G, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+        k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, delta, nullptr);
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -1431,7 +1491,16 @@ tc_status tc_relax_last_profile(tc_relax_profile* out)
 tc_status tc_subdomain_delta_energy(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
                                     int32_t n_sub, const double* new_active, double* delta, tc_stream stream)
 {
-    return tc::delta_all(pos, n, idx, offsets, n_sub, new_active, delta, reinterpret_cast<cudaStream_t>(stream));
+    return tc::delta_all(pos, n, idx, offsets, n_sub, new_active, delta, false, nullptr,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+tc_status tc_subdomain_delta_energy_mixed(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
+                                          int32_t n_sub, const double* new_active, double* delta, double* bound,
+                                          tc_stream stream)
+{
+    return tc::delta_all(pos, n, idx, offsets, n_sub, new_active, delta, true, bound,
+                         reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"
