@@ -340,8 +340,9 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
 
 def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 100, m_min: int = 200,
               m_max: int = 4000, period: int = 64, seed: int = 0, local_precision: str = "mixed") -> dict:
-    """The adaptive optimisation cycle (Sec. II C) on the GPU: per batch of `batch` subdomains, local
-    energies of all N charges, defect threshold e_i > mu - sigma_e, centres (80 % at defects, 20 %
+    """The adaptive optimisation cycle (Sec. II C) on the GPU, after the border-interior split of
+    Sec. II B (N_b pinned boundary charges, interior radius ramped from Eq. sigma to 1 over the
+    batches): per batch of `batch` subdomains, local energies of all N charges, defect threshold e_i > mu - sigma_e, centres (80 % at defects, 20 %
     uniform in the disk), zones of the m nearest charges (m a triangle wave between m_min and m_max),
     `steps` mixed projected BB steps per zone against all N, sequential float64 accept."""
     import numpy as np
@@ -353,17 +354,21 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     pos = synth.lattice_disk(n, seed)
     pos = np.ascontiguousarray(pos[synth.zorder(pos)])
     p = torch.tensor(pos, device=dev)
+    # border-interior split (Sec. II B): N_b of Eq. Nb pinned to the circle, the rest inside sigma0
+    sigma0 = 1.0 - 0.5 / math.sqrt(n)
+    flags = tc.border_split(p, tc.boundary_count(n), sigma0)
     u = torch.tensor(np.random.default_rng(seed + 7).random((n_sub, 3)), device=dev)
     eta = 1e-4 / n
     kw = dict(batch=batch, m_min=m_min, m_max=m_max, period=period, local_precision=local_precision,
-              precision="mixed", optimizer="bb", n_steps=steps, step0=eta, alpha_min=0.0, alpha_max=10 * eta)
+              precision="mixed", optimizer="bb", n_steps=steps, step0=eta, alpha_min=0.0, alpha_max=10 * eta,
+              sigma0=sigma0, sigma1=1.0)
     sizes = np.diff(tc.zone_offsets(n, n_sub, m_min=m_min, m_max=m_max, period=period))
     # warm-up on a copy (graph capture, workspace growth)
-    tc.cycle(p.clone(), u[: min(batch, n_sub)], **kw)
+    tc.cycle(p.clone(), u[: min(batch, n_sub)], flags, **kw)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    r, trace = tc.cycle(p, u, **kw)
+    r, trace = tc.cycle(p, u, flags, **kw)
     b.record()
     torch.cuda.synchronize()
     tc.sync_status()
@@ -372,9 +377,11 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     pairs = int(sizes.sum()) * (n - 1) * (steps + 1) + n_batches * n * (n - 1)
     tr = trace.cpu().numpy()
     st = r.status.cpu().numpy()
-    return {"workload": f"N={n} lattice background, {n_sub} subdomains in batches of {batch}, zones of "
-                        f"{m_min}..{m_max} nearest charges (triangle wave, period {period}), {steps} mixed BB "
-                        f"steps each, {local_precision} local energies per batch, fp64 sequential accept",
+    return {"workload": f"N={n} lattice background split into N_b={tc.boundary_count(n)} pinned boundary charges "
+                        f"and an interior disk whose radius ramps {sigma0:.5f} -> 1 over the batches; {n_sub} "
+                        f"subdomains in batches of {batch}, zones of {m_min}..{m_max} nearest charges (triangle "
+                        f"wave, period {period}), {steps} mixed BB steps each, {local_precision} local energies "
+                        f"per batch, fp64 sequential accept",
             "cycle_time_s": ms / 1e3, "ms_per_subdomain": ms / n_sub, "pairs_per_s": pairs / (ms / 1e3),
             "accepted": int((st == 1).sum()), "skipped_overlap": int((st == 2).sum()),
             "energy_start": float(tr[0]), "energy_end": float(tr[-1]), "energy_drop": float(tr[0] - tr[-1])}

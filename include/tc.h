@@ -234,8 +234,8 @@ tc_status tc_zone_offsets(const tc_zone_params* prm, int64_t n, int32_t n_sub, i
 
 /* Steps 2-3 of Sec. II C and the zone of step 4, for n_sub subdomains:
  *   mu, sigma_e = mean and population standard deviation of local_e over all n;
- *   defects D = { i : local_e[i] > mu + kappa sigma_e and |r_i| < radius - wall_tol },
- *     in ascending i;
+ *   defects D = { i : local_e[i] > mu + kappa sigma_e, |r_i| < radius - wall_tol and
+ *     flags[i] == 0 }, in ascending i;
  *   subdomain s takes u = uniforms[3s .. 3s+2]:
  *     centre = r_(D[floor(u1 |D|)]) if u0 < p_defect and D is not empty, else
  *              sqrt(u1) radius (cos 2 pi u2, sin 2 pi u2);
@@ -244,21 +244,26 @@ tc_status tc_zone_offsets(const tc_zone_params* prm, int64_t n, int32_t n_sub, i
  *              in ascending i -- a valid idx range for tc_relax_subdomains.
  *   pos      [2n]          device positions
  *   local_e  [n]           device e_i (tc_energy's local_e)
+ *   flags    [n]           device, nonzero = pinned boundary charge (never a defect); nullable
  *   uniforms [3 n_sub]     device, each in [0, 1)
  *   idx      [offsets[n_sub]] device, written (size it with tc_zone_offsets)
  *   offsets  [n_sub + 1]   device, written
  *   centres  [2 n_sub]     device, written; nullable
  *   stats    [3]           device, written (mu, sigma_e, |D|); nullable
  * Asynchronous on `stream`; TC_ERR_INVALID_ARG for bad sizes or parameters. */
-tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local_e, const tc_zone_params* prm,
-                               int32_t n_sub, const double* uniforms, int32_t* idx, int64_t* offsets,
-                               double* centres, double* stats, tc_stream stream);
+tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local_e, const uint8_t* flags,
+                               const tc_zone_params* prm, int32_t n_sub, const double* uniforms, int32_t* idx,
+                               int64_t* offsets, double* centres, double* stats, tc_stream stream);
 
 typedef struct {
-    tc_zone_params zone;    /* zone.phase is the schedule position of the cycle's first subdomain */
-    tc_relax_params relax;  /* optimiser of step 4; accept is forced to 1 */
+    tc_zone_params zone;    /* zone.phase: schedule position of the cycle's first subdomain;
+                               zone.radius is replaced by the batch's sigma */
+    tc_relax_params relax;  /* optimiser of step 4; accept is forced to 1, radius replaced by sigma */
     int32_t batch;          /* subdomains selected and relaxed together (1 = one at a time) */
     int32_t local_precision;/* tc_precision of the e_i that pick the centres */
+    double sigma0;          /* interior radius of the first batch (Sec. II B, Eq. sigma) ... */
+    double sigma1;          /* ... rising linearly to this one at the last batch;
+                               wall_tol < sigma0 <= sigma1 <= 1 (1, 1: the plain unit disk) */
 } tc_cycle_params;
 
 /* One optimisation cycle (Sec. II C) of n_sub subdomains, in batches of
@@ -268,16 +273,34 @@ typedef struct {
  * tc_relax_subdomains with the sequential float64 accept (step 4).  batch = 1
  * recomputes e_i before every subdomain, as the paper's cycle does; a larger
  * batch relaxes its zones concurrently against the configuration at the
- * batch's start and accepts them in order.
- *   pos      [2n]          in/out configuration (device)
+ * batch's start and accepts them in order.  Batch b of n_batches uses the
+ * interior radius sigma_b = sigma0 + (sigma1 - sigma0) b / (n_batches - 1)
+ * (sigma1 for one batch) for the free charges and for the zone centres and
+ * boundary test; pinned charges (flags) move along the unit circle and are
+ * never defects (Sec. II B).
+ *   pos      [2n]          in/out configuration (device); free charges within sigma0
+ *   flags    [n]           device, nonzero = pinned to the unit circle; nullable
  *   uniforms [3 n_sub]     device, each in [0, 1)
  *   out      [n_sub]       device results, as tc_relax_subdomains
  *   energy   [n_batches+1] device; E (in local_precision) before each batch and
  *                          after the last; nullable
  * Synchronises the stream once per batch (the zone sizes are host-known, the
  * relaxation reads its offsets back).  Device errors as tc_relax_subdomains. */
-tc_status tc_cycle(double* pos, int64_t n, const tc_cycle_params* prm, int32_t n_sub, const double* uniforms,
-                   tc_subdomain_result* out, double* energy, tc_stream stream);
+tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_params* prm, int32_t n_sub,
+                   const double* uniforms, tc_subdomain_result* out, double* energy, tc_stream stream);
+
+/* Eq. Nb (Sec. II B): the number of boundary charges,
+ *   N_b = round(2.84328 N^(2/3) - 0.530196 N^(1/3) - 2.32866), within [0, n].
+ * Host-only. */
+int64_t tc_boundary_count(int64_t n);
+
+/* The border-interior split of Sec. II B: ordering the charges by (|r|^2, i)
+ * ascending, the last n_b become boundary charges pinned to the unit circle
+ * (flags = 1, r <- r/|r|; unchanged at the origin) and the others interior
+ * charges confined to radius sigma (flags = 0, r <- r min(1, sigma/|r|)).
+ *   pos   [2n] device, in/out;  flags [n] device, written;
+ *   0 <= n_b <= n;  0 < sigma <= 1.  Asynchronous on `stream`. */
+tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uint8_t* flags, tc_stream stream);
 
 /* Total energy (and local energies) exactly as tc_energy computes them, but
  * without allocating any device memory.  The paper has no counterpart; this

@@ -15,6 +15,7 @@ Paper passages followed (Lavrov & Nikonov, Thomson problem in a disk):
   lbfgs / bb / pgd  projected descent on E (the paper's local optimiser is
                   L-BFGS-B, Sec. II C step 4; see the function docs for the
                   variant written here)
+  border_split    the border-interior split of Sec. II B (Eq. Nb, radius sigma)
   zone_select     steps 1-3 of the optimisation cycle of Sec. II C (defect
                   threshold, centre choice) and the zone of step 4
   cycle           the optimisation cycle of Sec. II C, in batches
@@ -57,12 +58,13 @@ def lib(openmp: bool = False) -> C.CDLL:
             "tco_project": [vp, i64, d, vp],
             "tco_projected_grad": [vp, vp, i64, d, vp, vp, vp, vp],
             "tco_pgd": [vp, i64, d, i64, d, vp, vp],
-            "tco_subdomain_bb": [vp, i64, vp, i64, d, d, d, i64, d, vp],
+            "tco_subdomain_bb": [vp, i64, vp, i64, d, d, d, i64, d, vp, vp],
             "tco_accept_sequential": [vp, i64, vp, vp, i64, vp, vp, vp],
             "tco_lbfgs": [vp, i64, i64, i64, d, d, d, d, vp, vp, vp],
             "tco_threads": [],
-            "tco_zone_select": [vp, i64, vp, d, d, d, d, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp],
-            "tco_cycle": [vp, i64, d, d, d, d, i64, i64, i64, i64, i64, vp, d, d, d, i64, vp, vp, vp],
+            "tco_zone_select": [vp, i64, vp, vp, d, d, d, d, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp],
+            "tco_cycle": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, vp, d, d, d, i64, vp, vp, vp],
+            "tco_border_split": [vp, i64, i64, d, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -70,6 +72,10 @@ def lib(openmp: bool = False) -> C.CDLL:
             f.restype = C.c_int
         L.tco_zone_size.argtypes = [i64, i64, i64, i64, i64]
         L.tco_zone_size.restype = i64
+        L.tco_boundary_count.argtypes = [i64]
+        L.tco_boundary_count.restype = i64
+        L.tco_sigma_ramp.argtypes = [d, d, i64, i64]
+        L.tco_sigma_ramp.restype = d
         _libs[openmp] = L
     return _libs[openmp]
 
@@ -177,14 +183,21 @@ def pgd(pos, eta: float, steps: int, radius: float = 1.0, flags=None):
     return p, tr
 
 
+def _flags(flags):
+    return None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+
+
 def subdomain_bb(snap, idx, step0: float, alpha_min: float, alpha_max: float, steps: int,
-                 radius: float = 1.0) -> np.ndarray:
-    """Projected BB gradient descent of one subdomain against the snapshot; returns x (m, 2)."""
+                 radius: float = 1.0, flags=None) -> np.ndarray:
+    """Projected BB gradient descent of one subdomain against the snapshot; returns x (m, 2).
+
+    flags (n, nullable): pinned charges, projected to the unit circle."""
     s = _pos(snap)
     ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    f = _flags(flags)
     out = np.zeros((ix.size, 2))
     _check(lib().tco_subdomain_bb(_p(s), s.shape[0], _p(ix), ix.size, float(step0), float(alpha_min),
-                                  float(alpha_max), int(steps), float(radius), _p(out)), "subdomain_bb")
+                                  float(alpha_max), int(steps), float(radius), _p(f), _p(out)), "subdomain_bb")
     return out
 
 
@@ -220,7 +233,8 @@ def zone_size(q: int, m_min: int, m_max: int, period: int, n: int) -> int:
 
 
 def zone_select(pos, local_e, uniforms, m_min: int, m_max: int, period: int, phase: int = 0,
-                kappa: float = -1.0, p_defect: float = 0.8, radius: float = 1.0, wall_tol: float = 1e-9):
+                kappa: float = -1.0, p_defect: float = 0.8, radius: float = 1.0, wall_tol: float = 1e-9,
+                flags=None):
     """Defects, centres and nearest-m zones of Sec. II C; returns (idx, offsets, centres, stats).
 
     uniforms: (n_sub, 3) in [0, 1); stats = (mu, sigma_e, number of defects)."""
@@ -234,27 +248,52 @@ def zone_select(pos, local_e, uniforms, m_min: int, m_max: int, period: int, pha
     off = np.zeros(ns + 1, dtype=np.int64)
     cen = np.zeros((ns, 2))
     stats = np.zeros(3)
-    _check(lib().tco_zone_select(_p(p), n, _p(e), float(kappa), float(p_defect), float(radius), float(wall_tol),
+    f = _flags(flags)
+    _check(lib().tco_zone_select(_p(p), n, _p(e), _p(f), float(kappa), float(p_defect), float(radius),
+                                 float(wall_tol),
                                  int(m_min), int(m_max), int(period), int(phase), ns, _p(u), _p(idx), _p(off),
                                  _p(cen), _p(stats)), "zone_select")
     return idx[:cap], off, cen, stats
 
 
 def cycle(pos, uniforms, m_min: int, m_max: int, period: int, batch: int, step0: float, alpha_min: float,
-          alpha_max: float, steps: int, kappa: float = -1.0, p_defect: float = 0.8, radius: float = 1.0,
-          wall_tol: float = 1e-9):
-    """One optimisation cycle (Sec. II C) in batches; returns (pos, trace, delta, accepted)."""
+          alpha_max: float, steps: int, kappa: float = -1.0, p_defect: float = 0.8, sigma0: float = 1.0,
+          sigma1: float = 1.0, wall_tol: float = 1e-9, flags=None):
+    """One optimisation cycle (Sec. II C) in batches; returns (pos, trace, delta, accepted).
+
+    sigma0 -> sigma1: interior radius ramp over the batches; flags: pinned boundary charges."""
     p = _pos(pos).copy()
+    f = _flags(flags)
     u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1, 3))
     ns = u.shape[0]
     nb = -(-ns // batch) if ns else 0
     trace = np.zeros(nb + 1)
     d = np.zeros(max(ns, 1))
     acc = np.zeros(max(ns, 1), dtype=np.uint8)
-    _check(lib().tco_cycle(_p(p), p.shape[0], float(kappa), float(p_defect), float(radius), float(wall_tol),
+    _check(lib().tco_cycle(_p(p), p.shape[0], _p(f), float(kappa), float(p_defect), float(sigma0), float(sigma1),
+                           float(wall_tol),
                            int(m_min), int(m_max), int(period), ns, int(batch), _p(u), float(step0),
                            float(alpha_min), float(alpha_max), int(steps), _p(trace), _p(d), _p(acc)), "cycle")
     return p, trace, d[:ns], acc[:ns]
+
+
+def boundary_count(n: int) -> int:
+    """Eq. Nb: N_b = round(2.84328 N^(2/3) - 0.530196 N^(1/3) - 2.32866), within [0, n]."""
+    return int(lib().tco_boundary_count(int(n)))
+
+
+def sigma_ramp(sigma0: float, sigma1: float, b: int, n_batches: int) -> float:
+    """Interior radius of batch b (linear ramp from sigma0 to sigma1)."""
+    return float(lib().tco_sigma_ramp(float(sigma0), float(sigma1), int(b), int(n_batches)))
+
+
+def border_split(pos, n_b: int, sigma: float):
+    """Sec. II B split: the n_b outermost charges (by (|r|^2, i)) pinned to the unit circle, the rest
+    confined to radius sigma; returns (pos, flags)."""
+    p = _pos(pos).copy()
+    f = np.zeros(p.shape[0], dtype=np.uint8)
+    _check(lib().tco_border_split(_p(p), p.shape[0], int(n_b), float(sigma), _p(f)), "border_split")
+    return p, f
 
 
 def library_path() -> str:

@@ -368,17 +368,25 @@ static double dot(const double* a, const double* b, int64_t len)
  * at snap.  Step k: g_k = grad E_sub(x_k) (tco_subdomain_grad),
  *   alpha_0 = step0;  alpha_k = s^T y / y^T y (BB2, s = x_k - x_{k-1},
  *   y = g_k - g_{k-1}) when s^T y > 0, else alpha_max; clamped to
- *   [alpha_min, alpha_max];  x_{k+1} = P(x_k - alpha_k g_k).
+ *   [alpha_min, alpha_max];  x_{k+1} = P(x_k - alpha_k g_k), P the projection of
+ *   tco_project (charges with flags[idx[k]] != 0 pinned to the unit circle;
+ *   flags over all n, nullable).
  * act_out (2m): x after `steps` steps. */
 int tco_subdomain_bb(const double* snap, int64_t n, const int32_t* idx, int64_t m,
                      double step0, double alpha_min, double alpha_max, int64_t steps,
-                     double radius, double* act_out)
+                     double radius, const unsigned char* flags, double* act_out)
 {
     if (n < 0 || m < 0 || steps < 0 || (m > 0 && (!snap || !idx || !act_out))) return TCO_ERR_INVALID_ARG;
     size_t sz = sizeof(double) * 2 * (size_t)(m > 0 ? m : 1);
     double *x = act_out, *g = (double*)malloc(sz), *xp = (double*)malloc(sz), *gp = (double*)malloc(sz);
     double *s = (double*)malloc(sz), *y = (double*)malloc(sz);
-    if (!g || !xp || !gp || !s || !y) { free(g); free(xp); free(gp); free(s); free(y); return TCO_ERR_NO_MEMORY; }
+    unsigned char* fa = flags ? (unsigned char*)malloc((size_t)(m > 0 ? m : 1)) : NULL;
+    if (!g || !xp || !gp || !s || !y || (flags && !fa)) {
+        free(g); free(xp); free(gp); free(s); free(y); free(fa);
+        return TCO_ERR_NO_MEMORY;
+    }
+    if (fa)
+        for (int64_t k = 0; k < m; ++k) fa[k] = flags[idx[k]];
     for (int64_t k = 0; k < m; ++k) {
         x[2 * k] = snap[2 * idx[k]];
         x[2 * k + 1] = snap[2 * idx[k] + 1];
@@ -398,9 +406,9 @@ int tco_subdomain_bb(const double* snap, int64_t n, const int32_t* idx, int64_t 
         memcpy(xp, x, sz);
         memcpy(gp, g, sz);
         for (int64_t i = 0; i < 2 * m; ++i) x[i] = x[i] - alpha * g[i];
-        tco_project(x, m, radius, NULL);
+        tco_project(x, m, radius, fa);
     }
-    free(g); free(xp); free(gp); free(s); free(y);
+    free(g); free(xp); free(gp); free(s); free(y); free(fa);
     return st;
 }
 
@@ -667,9 +675,10 @@ static int int_cmp(const void* a, const void* b)
  * for n_sub subdomains at schedule positions phase, phase+1, ...:
  *   local_e: e_i of step 1 (tco_energy with local_e);
  *   mu = mean of e_i, sigma_e = its population standard deviation, over all n;
- *   defects D = { i : e_i > mu + kappa sigma_e and |r_i| < radius - wall_tol }
- *     in ascending i (the paper's rule is kappa = -1; charges at the wall are
- *     the boundary population that step 2 does not target);
+ *   defects D = { i : e_i > mu + kappa sigma_e, |r_i| < radius - wall_tol and
+ *     flags[i] == 0 } in ascending i (the paper's rule is kappa = -1; charges
+ *     at the wall and pinned charges (flags nullable) are the boundary
+ *     population that step 2 does not target);
  *   subdomain s draws u = uniforms[3s .. 3s+2] in [0,1):
  *     centre = r_{D[floor(u1 |D|)]} when u0 < p_defect and D is not empty,
  *     otherwise the area-uniform point sqrt(u1) radius (cos 2 pi u2, sin 2 pi u2);
@@ -677,10 +686,10 @@ static int int_cmp(const void* a, const void* b)
  *     (d^2, i), d^2 = (x_i - c_x)^2 + (y_i - c_y)^2, listed in ascending i.
  * offsets (n_sub + 1) are written; idx holds offsets[n_sub] entries;
  * centres (2 n_sub), stats (3: mu, sigma_e, |D|) are nullable. */
-int tco_zone_select(const double* pos, int64_t n, const double* local_e, double kappa, double p_defect,
-                    double radius, double wall_tol, int64_t m_min, int64_t m_max, int64_t period,
-                    int64_t phase, int64_t n_sub, const double* uniforms, int32_t* idx, int64_t* offsets,
-                    double* centres, double* stats)
+int tco_zone_select(const double* pos, int64_t n, const double* local_e, const unsigned char* flags,
+                    double kappa, double p_defect, double radius, double wall_tol, int64_t m_min, int64_t m_max,
+                    int64_t period, int64_t phase, int64_t n_sub, const double* uniforms, int32_t* idx,
+                    int64_t* offsets, double* centres, double* stats)
 {
     if (n < 0 || n_sub < 0 || m_min < 0 || m_max < m_min || period < 1 || phase < 0 || !(radius > 0.0) ||
         (n_sub > 0 && (!uniforms || !offsets || n < 1 || !pos || !local_e || !idx)))
@@ -704,7 +713,7 @@ int tco_zone_select(const double* pos, int64_t n, const double* local_e, double 
     int64_t nd = 0;
     for (int64_t i = 0; i < n; ++i) {
         double x = pos[2 * i], y = pos[2 * i + 1];
-        if (local_e[i] > thr && x * x + y * y < rin * rin) D[nd++] = (int32_t)i;
+        if (local_e[i] > thr && x * x + y * y < rin * rin && !(flags && flags[i])) D[nd++] = (int32_t)i;
     }
     if (stats) { stats[0] = mu; stats[1] = sigma; stats[2] = (double)nd; }
     offsets[0] = 0;
@@ -742,23 +751,70 @@ int tco_zone_select(const double* pos, int64_t n, const double* local_e, double 
     return TCO_OK;
 }
 
+/* Interior radius of batch b of n_batches (Sec. II B, Eq. sigma: sigma rises
+ * gradually from its initial value to 1; the law is not given, so it is read
+ * as linear in the batch index): sigma0 + (sigma1 - sigma0) b / (n_batches - 1),
+ * sigma1 for a single batch. */
+double tco_sigma_ramp(double sigma0, double sigma1, int64_t b, int64_t n_batches)
+{
+    if (n_batches <= 1) return sigma1;
+    return sigma0 + (sigma1 - sigma0) * (double)b / (double)(n_batches - 1);
+}
+
+/* Eq. Nb: the number of boundary charges, N_b = 2.84328 N^(2/3) -
+ * 0.530196 N^(1/3) - 2.32866 rounded to the nearest integer, within [0, n]. */
+int64_t tco_boundary_count(int64_t n)
+{
+    if (n <= 0) return 0;
+    double c = cbrt((double)n);
+    double nb = 2.84328 * c * c - 0.530196 * c - 2.32866;
+    int64_t k = (int64_t)floor(nb + 0.5);
+    return k < 0 ? 0 : (k > n ? n : k);
+}
+
+/* The border-interior split of Sec. II B: ordering the charges by (|r|^2, i)
+ * ascending, the last n_b become boundary charges pinned to the unit circle
+ * (flags = 1, r <- r/|r|) and the others interior charges confined to radius
+ * sigma (flags = 0, r <- r min(1, sigma/|r|)).  pos in/out, flags out (n). */
+int tco_border_split(double* pos, int64_t n, int64_t n_b, double sigma, unsigned char* flags)
+{
+    if (n < 0 || n_b < 0 || n_b > n || !(sigma > 0.0) || (n > 0 && (!pos || !flags))) return TCO_ERR_INVALID_ARG;
+    near_t* nr = (near_t*)malloc(sizeof(near_t) * (size_t)(n > 0 ? n : 1));
+    if (!nr) return TCO_ERR_NO_MEMORY;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[2 * i], y = pos[2 * i + 1];
+        nr[i].d2 = x * x + y * y;
+        nr[i].i = (int32_t)i;
+    }
+    qsort(nr, (size_t)n, sizeof(near_t), near_cmp);
+    for (int64_t k = 0; k < n; ++k) flags[nr[k].i] = k >= n - n_b ? 1 : 0;
+    free(nr);
+    tco_project(pos, n, sigma, flags);
+    return TCO_OK;
+}
+
 /* One optimisation cycle of Sec. II C over n_sub subdomains, taken in batches
  * of `batch` consecutive subdomains (batch = 1 is the paper's one-at-a-time
- * cycle).  For each batch b:
+ * cycle).  For each batch b, with sigma_b = tco_sigma_ramp(sigma0, sigma1, b, .)
+ * the interior radius (Sec. II B; flags, nullable, marks the pinned boundary
+ * charges):
  *   E_b, e_i = tco_energy(pos)                       (step 1; trace[b] = E_b)
- *   zones    = tco_zone_select(pos, e, ..., phase = b batch)   (steps 2-3)
+ *   zones    = tco_zone_select(pos, e, flags, ..., radius = sigma_b,
+ *                              phase = b batch)      (steps 2-3)
  *   each zone relaxes against the batch-start snapshot with tco_subdomain_bb
- *   (step 4, projected gradient descent with BB steps, `steps` steps)
+ *   (step 4, projected gradient descent with BB steps, `steps` steps, free
+ *   charges confined to sigma_b, pinned ones to the unit circle)
  *   tco_accept_sequential applies the relaxed zones in order (dE < 0, no clash).
  * trace (nullable, n_batches + 1): E before each batch and after the last.
  * delta, accepted (n_sub): per subdomain, as tco_accept_sequential. */
-int tco_cycle(double* pos, int64_t n, double kappa, double p_defect, double radius, double wall_tol,
-              int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub, int64_t batch,
-              const double* uniforms, double step0, double alpha_min, double alpha_max, int64_t steps,
-              double* trace, double* delta, unsigned char* accepted)
+int tco_cycle(double* pos, int64_t n, const unsigned char* flags, double kappa, double p_defect, double sigma0,
+              double sigma1, double wall_tol, int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub,
+              int64_t batch, const double* uniforms, double step0, double alpha_min, double alpha_max,
+              int64_t steps, double* trace, double* delta, unsigned char* accepted)
 {
     if (n < 1 || n_sub < 0 || batch < 1 || !pos || (n_sub > 0 && (!uniforms || !delta || !accepted)))
         return TCO_ERR_INVALID_ARG;
+    int64_t n_batches = (n_sub + batch - 1) / batch;
     int64_t cap = (m_max < n ? m_max : n) * (batch < n_sub ? batch : (n_sub > 0 ? n_sub : 1));
     double* e = (double*)malloc(sizeof(double) * (size_t)n);
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
@@ -769,15 +825,16 @@ int tco_cycle(double* pos, int64_t n, double kappa, double p_defect, double radi
     int64_t nb = 0;
     for (int64_t b0 = 0; b0 < n_sub && !st; b0 += batch, ++nb) {
         int64_t k = n_sub - b0 < batch ? n_sub - b0 : batch;
+        double radius = tco_sigma_ramp(sigma0, sigma1, nb, n_batches);
         double E;
         st = tco_energy(pos, n, &E, e);
         if (st) break;
         if (trace) trace[nb] = E;
-        st = tco_zone_select(pos, n, e, kappa, p_defect, radius, wall_tol, m_min, m_max, period, b0, k,
+        st = tco_zone_select(pos, n, e, flags, kappa, p_defect, radius, wall_tol, m_min, m_max, period, b0, k,
                              uniforms + 3 * b0, idx, off, NULL, NULL);
         for (int64_t s = 0; s < k && !st; ++s)
             st = tco_subdomain_bb(pos, n, idx + off[s], off[s + 1] - off[s], step0, alpha_min, alpha_max,
-                                  steps, radius, act + 2 * off[s]);
+                                  steps, radius, flags, act + 2 * off[s]);
         if (!st) st = tco_accept_sequential(pos, n, idx, off, k, act, delta + b0, accepted + b0);
     }
     if (!st && trace) st = tco_energy(pos, n, &trace[nb], NULL);

@@ -28,6 +28,7 @@ __all__ = [
     "energy", "grad", "local_energy", "project_disk", "subdomain_delta_energy", "relax_subdomains",
     "coulomb_energy", "CoulombEnergy", "sync_status", "probe_pipes", "relax_last_profile", "TCError", "RelaxParams",
     "library_path", "zone_params", "zone_offsets", "select_subdomains", "cycle", "subdomain_delta_energy_mixed",
+    "boundary_count", "border_split",
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED}
@@ -202,7 +203,7 @@ def _vec(t, dtype, name):
     return t
 
 
-def select_subdomains(pos, local_e, uniforms, **zone):
+def select_subdomains(pos, local_e, uniforms, flags=None, **zone):
     """Defect threshold, centres and nearest-m zones (Sec. II C steps 2-4).
 
     uniforms: (n_sub, 3) CUDA float64 in [0, 1).  Returns (idx int32, offsets int64,
@@ -217,34 +218,59 @@ def select_subdomains(pos, local_e, uniforms, **zone):
     offsets = torch.empty(n_sub + 1, dtype=torch.int64, device=pos.device)
     centres = torch.empty((max(n_sub, 1), 2), dtype=torch.float64, device=pos.device)
     stats = torch.empty(3, dtype=torch.float64, device=pos.device)
-    L.check(L.lib().tc_select_subdomains(_p(pos), pos.shape[0], _p(local_e), C.byref(prm), n_sub, _p(uniforms),
-                                         _p(idx), _p(offsets), _p(centres), _p(stats), _stream()),
+    if flags is not None:
+        _vec(flags, torch.uint8, "flags")
+    L.check(L.lib().tc_select_subdomains(_p(pos), pos.shape[0], _p(local_e), _p(flags), C.byref(prm), n_sub,
+                                         _p(uniforms), _p(idx), _p(offsets), _p(centres), _p(stats), _stream()),
             "tc_select_subdomains")
     return idx[:off_h[-1]], offsets, centres[:n_sub], stats
 
 
-def cycle(pos, uniforms, *, batch: int, m_min: int, m_max: int, period: int, phase: int = 0, kappa: float = -1.0,
-          p_defect: float = 0.8, wall_tol: float = 1e-9, local_precision="mixed", precision="mixed",
-          optimizer="bb", n_steps=200, memory=8, step0=1e-9, alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0,
-          radius=1.0, polish_steps=0, polish_gtol=0.0, want_energy=False, profile=False):
+def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, period: int, phase: int = 0,
+          kappa: float = -1.0, p_defect: float = 0.8, wall_tol: float = 1e-9, sigma0: float = 1.0, sigma1: float = 1.0,
+          local_precision="mixed", precision="mixed", optimizer="bb", n_steps=200, memory=8, step0=1e-9,
+          alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0, polish_steps=0, polish_gtol=0.0,
+          want_energy=False, profile=False):
     """One optimisation cycle (Sec. II C) of uniforms.shape[0] subdomains in batches, in place on pos.
 
+    flags (uint8, nullable): pinned boundary charges; sigma0 -> sigma1: interior radius ramp.
     Returns (RelaxResult per subdomain, energy trace: E before each batch and after the last)."""
     _pos(pos)
     _vec(uniforms, torch.float64, "uniforms")
+    if flags is not None:
+        _vec(flags, torch.uint8, "flags")
     n_sub = uniforms.numel() // 3
     prm = L.CycleParams()
-    prm.zone = zone_params(m_min, m_max, period, phase, kappa, p_defect, radius, wall_tol)
+    prm.zone = zone_params(m_min, m_max, period, phase, kappa, p_defect, 1.0, wall_tol)
     prm.relax = _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol,
-                              radius, polish_steps, polish_gtol, True, want_energy, profile)
+                              1.0, polish_steps, polish_gtol, True, want_energy, profile)
     prm.batch = int(batch)
     prm.local_precision = _prec(local_precision)
+    prm.sigma0 = float(sigma0)
+    prm.sigma1 = float(sigma1)
     n_batches = -(-n_sub // max(int(batch), 1)) if n_sub else 0
     raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
     trace = torch.full((n_batches + 1,), float("nan"), dtype=torch.float64, device=pos.device)
-    L.check(L.lib().tc_cycle(_p(pos), pos.shape[0], C.byref(prm), n_sub, _p(uniforms), _p(raw), _p(trace),
-                             _stream()), "tc_cycle")
+    L.check(L.lib().tc_cycle(_p(pos), pos.shape[0], _p(flags), C.byref(prm), n_sub, _p(uniforms), _p(raw),
+                             _p(trace), _stream()), "tc_cycle")
     return _results(raw, n_sub), trace
+
+
+def boundary_count(n: int) -> int:
+    """Eq. Nb: the number of boundary charges for n charges."""
+    return int(L.lib().tc_boundary_count(int(n)))
+
+
+def border_split(pos, n_b: int | None = None, sigma: float | None = None) -> torch.Tensor:
+    """Sec. II B split in place: the n_b outermost charges pinned to the unit circle, the rest confined
+    to sigma.  Defaults: n_b from Eq. Nb, sigma = 1 - 1/(2 sqrt(n)) (Eq. sigma).  Returns the uint8 flags."""
+    _pos(pos)
+    n = pos.shape[0]
+    n_b = boundary_count(n) if n_b is None else int(n_b)
+    sigma = 1.0 - 0.5 / max(n, 1) ** 0.5 if sigma is None else float(sigma)
+    flags = torch.empty(n, dtype=torch.uint8, device=pos.device)
+    L.check(L.lib().tc_border_split(_p(pos), n, n_b, sigma, _p(flags), _stream()), "tc_border_split")
+    return flags
 
 
 def relax_last_profile() -> dict:

@@ -94,6 +94,8 @@ class CycleParams(C.Structure):
         ("relax", RelaxParams),
         ("batch", C.c_int32),
         ("local_precision", C.c_int32),
+        ("sigma0", C.c_double),
+        ("sigma1", C.c_double),
     ]
 
 
@@ -127,8 +129,11 @@ def _lib() -> C.CDLL:
             "tc_probe_pipes": ([vp, vp], C.c_int),
             "tc_relax_last_profile": ([C.POINTER(RelaxProfile)], C.c_int),
             "tc_zone_offsets": ([C.POINTER(ZoneParams), i64, i32, vp], C.c_int),
-            "tc_select_subdomains": ([vp, i64, vp, C.POINTER(ZoneParams), i32, vp, vp, vp, vp, vp, vp], C.c_int),
-            "tc_cycle": ([vp, i64, C.POINTER(CycleParams), i32, vp, vp, vp, vp], C.c_int),
+            "tc_select_subdomains": ([vp, i64, vp, vp, C.POINTER(ZoneParams), i32, vp, vp, vp, vp, vp, vp],
+                                     C.c_int),
+            "tc_cycle": ([vp, i64, vp, C.POINTER(CycleParams), i32, vp, vp, vp, vp], C.c_int),
+            "tc_boundary_count": ([i64], i64),
+            "tc_border_split": ([vp, i64, i64, d, vp, vp], C.c_int),
         }
         for name, (args, res) in sigs.items():
             f = getattr(L, name)

@@ -14,7 +14,7 @@
 #include "tc_plan.cuh"
 
 static_assert(sizeof(tc_zone_params) == 48, "tc_zone_params layout");
-static_assert(sizeof(tc_cycle_params) == 144, "tc_cycle_params layout");
+static_assert(sizeof(tc_cycle_params) == 160, "tc_cycle_params layout");
 
 namespace tc {
 
@@ -93,11 +93,12 @@ template <int THREADS> __device__ double block_dd_sum(double hi, double lo, doub
 }
 
 // Step 2: mu, sigma_e (population) of e over all n, and the defect list
-// D = { i : e_i > mu + kappa sigma_e and |r_i|^2 < rin2 } in ascending i.
+// D = { i : e_i > mu + kappa sigma_e, |r_i|^2 < rin2, not pinned } in ascending i.
 // stats = (mu, sigma_e, |D|).  One CTA.
 __global__ void __launch_bounds__(kStatThreads) k_zone_stats(const double2* __restrict__ pos,
-                                                             const double* __restrict__ e, int64_t n, double kappa,
-                                                             double rin2, int32_t* __restrict__ D,
+                                                             const double* __restrict__ e,
+                                                             const uint8_t* __restrict__ flags, int64_t n,
+                                                             double kappa, double rin2, int32_t* __restrict__ D,
                                                              double* __restrict__ stats)
 {
     __shared__ double sh_hi[kStatThreads], sh_lo[kStatThreads];
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(kStatThreads) k_zone_stats(const double2* __re
         if (i < n) {
             const double2 p = pos[i];
             const double r2 = __dadd_rn(__dmul_rn(p.x, p.x), __dmul_rn(p.y, p.y));
-            flag = (e[i] > thr) && (r2 < rin2);
+            flag = (e[i] > thr) && (r2 < rin2) && !(flags && flags[i]);
         }
         int tot = 0;
         const int r = block_excl_count<kStatThreads>(flag, warp_tot, &tot);
@@ -134,11 +135,13 @@ __global__ void __launch_bounds__(kStatThreads) k_zone_stats(const double2* __re
     }
 }
 
-// Step 3 and the zone of step 4 for subdomain s = blockIdx.x.
+// Step 3 and the zone of step 4 for subdomain s = blockIdx.x (fixed, nullable,
+// replaces the drawn centres).
 __global__ void __launch_bounds__(kSelThreads) k_zone_select(const double2* __restrict__ pos, int64_t n,
                                                              const int32_t* __restrict__ D,
                                                              const double* __restrict__ stats,
-                                                             const double* __restrict__ uni, ZoneArgs z,
+                                                             const double* __restrict__ uni,
+                                                             const double2* __restrict__ fixed, ZoneArgs z,
                                                              int32_t* __restrict__ idx, int64_t* __restrict__ offsets,
                                                              double2* __restrict__ centres)
 {
@@ -158,14 +161,17 @@ __global__ void __launch_bounds__(kSelThreads) k_zone_select(const double2* __re
     for (int d = 16; d > 0; d >>= 1) part += __shfl_down_sync(0xffffffffu, part, d);
     if (lane == 0) red[w] = part;
     if (tid == 0) {
-        const double u0 = uni[3 * s], u1 = uni[3 * s + 1], u2 = uni[3 * s + 2];
-        const int64_t nd = (int64_t)stats[2];
         double2 c;
-        if (u0 < z.p_defect && nd > 0) {
+        if (fixed) {
+            c = fixed[s];
+        } else if (uni[3 * s] < z.p_defect && (int64_t)stats[2] > 0) {
+            const double u1 = uni[3 * s + 1];
+            const int64_t nd = (int64_t)stats[2];
             int64_t k = (int64_t)__dmul_rn(u1, (double)nd);
             k = k > nd - 1 ? nd - 1 : (k < 0 ? 0 : k);
             c = pos[D[k]];
         } else {
+            const double u1 = uni[3 * s + 1], u2 = uni[3 * s + 2];
             const double r = __dmul_rn(sqrt(u1), z.radius), t = __dmul_rn(2.0 * kPi, u2);
             double sn, cs;
             sincos(t, &sn, &cs);
@@ -266,6 +272,21 @@ __global__ void __launch_bounds__(kSelThreads) k_zone_select(const double2* __re
     }
 }
 
+// Border-interior split: every charge is a boundary charge except the listed
+// interior ones; then the projection (pinned to the unit circle, the others
+// confined to sigma).
+__global__ void k_border_flags(const int32_t* __restrict__ interior, int64_t m, uint8_t* __restrict__ flags)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        flags[interior[k]] = 0;
+}
+
+__global__ void k_border_project(double2* __restrict__ pos, int64_t n, double sigma, const uint8_t* __restrict__ flags)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pos[i] = project1(pos[i], sigma, flags[i] != 0);
+}
+
 tc_status check_zone(const tc_zone_params* z)
 {
     if (!z || z->m_min < 0 || z->m_max < z->m_min || z->period < 1 || z->phase < 0 || !(z->radius > 0.0) ||
@@ -299,9 +320,9 @@ void zone_offsets(const tc_zone_params* z, int64_t phase, int64_t n, int32_t n_s
 }
 
 // Steps 2-3 and the zones; the defect list lives in the slot-0 workspace.
-tc_status select_zones(const double* pos, int64_t n, const double* local_e, const tc_zone_params* z, int64_t phase,
-                       int32_t n_sub, const double* uniforms, int32_t* idx, int64_t* offsets, double* centres,
-                       double* stats, cudaStream_t s)
+tc_status select_zones(const double* pos, int64_t n, const double* local_e, const uint8_t* flags,
+                       const tc_zone_params* z, double radius, int64_t phase, int32_t n_sub, const double* uniforms,
+                       int32_t* idx, int64_t* offsets, double* centres, double* stats, cudaStream_t s)
 {
     tc_status err = TC_OK;
     Carver c;
@@ -314,11 +335,13 @@ tc_status select_zones(const double* pos, int64_t n, const double* local_e, cons
     int32_t* D = c.take<int32_t>(n);
     double* st = c.take<double>(4);
     if (!stats) stats = st;
-    const double rin = z->radius - z->wall_tol;
+    const double rin = radius - z->wall_tol;
     const double2* p2 = reinterpret_cast<const double2*>(pos);
-    k_zone_stats<<<1, kStatThreads, 0, s>>>(p2, local_e, n, z->kappa, rin * rin, D, stats);
-    k_zone_select<<<(unsigned)n_sub, kSelThreads, 0, s>>>(p2, n, D, stats, uniforms, zone_args(z, phase), idx,
-                                                         offsets, reinterpret_cast<double2*>(centres));
+    ZoneArgs za = zone_args(z, phase);
+    za.radius = radius;
+    k_zone_stats<<<1, kStatThreads, 0, s>>>(p2, local_e, flags, n, z->kappa, rin * rin, D, stats);
+    k_zone_select<<<(unsigned)n_sub, kSelThreads, 0, s>>>(p2, n, D, stats, uniforms, nullptr, za, idx, offsets,
+                                                         reinterpret_cast<double2*>(centres));
     return cuda_status(cudaGetLastError(), "zone selection launch");
 }
 
@@ -344,9 +367,9 @@ tc_status tc_zone_offsets(const tc_zone_params* prm, int64_t n, int32_t n_sub, i
     return TC_OK;
 }
 
-tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local_e, const tc_zone_params* prm,
-                               int32_t n_sub, const double* uniforms, int32_t* idx, int64_t* offsets,
-                               double* centres, double* stats, tc_stream stream)
+tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local_e, const uint8_t* flags,
+                               const tc_zone_params* prm, int32_t n_sub, const double* uniforms, int32_t* idx,
+                               int64_t* offsets, double* centres, double* stats, tc_stream stream)
 {
     tc_status err = check_zone(prm);
     if (err != TC_OK) return err;
@@ -362,19 +385,22 @@ tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local
         zone_offsets(prm, prm->phase, n, n_sub, off.data());
         if (off[n_sub] > 0) return TC_ERR_INVALID_ARG;
     }
-    return select_zones(pos, n, local_e, prm, prm->phase, n_sub, uniforms, idx, offsets, centres, stats, s);
+    return select_zones(pos, n, local_e, flags, prm, prm->radius, prm->phase, n_sub, uniforms, idx, offsets, centres,
+                        stats, s);
 }
 
-tc_status tc_cycle(double* pos, int64_t n, const tc_cycle_params* prm, int32_t n_sub, const double* uniforms,
-                   tc_subdomain_result* out, double* energy, tc_stream stream)
+tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_params* prm, int32_t n_sub,
+                   const double* uniforms, tc_subdomain_result* out, double* energy, tc_stream stream)
 {
     if (!prm) return TC_ERR_INVALID_ARG;
     tc_status err = check_zone(&prm->zone);
     if (err != TC_OK) return err;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const tc_precision lp = static_cast<tc_precision>(prm->local_precision);
-    if (n_sub < 0 || prm->batch < 1 || (lp != TC_FP64 && lp != TC_MIXED) || misaligned(energy, 8)) {
-        set_last_error("tc_cycle: need n_sub >= 0, batch >= 1 and a valid local_precision");
+    if (n_sub < 0 || prm->batch < 1 || (lp != TC_FP64 && lp != TC_MIXED) || misaligned(energy, 8) ||
+        !(prm->sigma0 > prm->zone.wall_tol) || !(prm->sigma0 <= prm->sigma1) || !(prm->sigma1 <= 1.0)) {
+        set_last_error("tc_cycle: need n_sub >= 0, batch >= 1, a valid local_precision and "
+                       "wall_tol < sigma0 <= sigma1 <= 1");
         return TC_ERR_INVALID_ARG;
     }
     if (n_sub == 0) return TC_OK;
@@ -410,16 +436,70 @@ tc_status tc_cycle(double* pos, int64_t n, const tc_cycle_params* prm, int32_t n
     int64_t b = 0;
     for (int64_t b0 = 0; b0 < n_sub; b0 += B, ++b) {
         const int32_t k = (int32_t)std::min<int64_t>(B, n_sub - b0);
+        // interior radius of this batch: linear ramp sigma0 -> sigma1 over the batches
+        const double sigma = n_batches <= 1
+                                 ? prm->sigma1
+                                 : prm->sigma0 + (prm->sigma1 - prm->sigma0) * (double)b / (double)(n_batches - 1);
+        rp.radius = sigma;
         err = allpairs(pos, n, lp, nullptr, energy ? energy + b : e_tot, e_loc, s);
         if (err != TC_OK) return err;
-        err = select_zones(pos, n, e_loc, &prm->zone, prm->zone.phase + b0, k, uniforms + 3 * b0, idx, offs,
-                           nullptr, nullptr, s);
+        err = select_zones(pos, n, e_loc, flags, &prm->zone, sigma, prm->zone.phase + b0, k, uniforms + 3 * b0, idx,
+                           offs, nullptr, nullptr, s);
         if (err != TC_OK) return err;
-        err = relax(pos, n, idx, offs, k, nullptr, nullptr, &rp, out + b0, s);
+        err = relax(pos, n, idx, offs, k, nullptr, flags, &rp, out + b0, s);
         if (err != TC_OK) return err;
     }
     if (energy) return allpairs(pos, n, lp, nullptr, energy + n_batches, nullptr, s);
     return TC_OK;
+}
+
+int64_t tc_boundary_count(int64_t n)
+{
+    if (n <= 0) return 0;
+    const double c = std::cbrt((double)n);
+    const double nb = 2.84328 * c * c - 0.530196 * c - 2.32866;
+    const int64_t k = (int64_t)std::floor(nb + 0.5);
+    return k < 0 ? 0 : (k > n ? n : k);
+}
+
+tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uint8_t* flags, tc_stream stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n < 0 || n > INT32_MAX || n_b < 0 || n_b > n || !(sigma > 0.0) || !(sigma <= 1.0) ||
+        (n > 0 && (!pos || !flags)) || misaligned(pos, 16))
+        return TC_ERR_INVALID_ARG;
+    if (n == 0) return TC_OK;
+    tc_status err = TC_OK;
+    const int64_t m = n - n_b;  // interior charges: the m nearest to the centre
+    Carver c;
+    c.take<int32_t>(std::max<int64_t>(m, 1));
+    c.take<int64_t>(2);
+    c.take<double2>(1);
+    c.take<double>(4);
+    void* ws = workspace(s, c.off, &err);
+    if (!ws) return err;
+    c.base = static_cast<char*>(ws);
+    c.off = kCounterBytes;
+    int32_t* interior = c.take<int32_t>(std::max<int64_t>(m, 1));
+    int64_t* offs = c.take<int64_t>(2);
+    double2* origin = c.take<double2>(1);
+    double* stats = c.take<double>(4);
+    ZoneArgs za{};
+    za.p_defect = 0.0;
+    za.radius = 1.0;
+    za.m_min = za.m_max = m;
+    za.period = 1;
+    za.phase = 0;
+    cudaError_t e = cudaMemsetAsync(origin, 0, sizeof(double2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, 4 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 1, (size_t)n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "border split set-up");
+    double2* p2 = reinterpret_cast<double2*>(pos);
+    k_zone_select<<<1, kSelThreads, 0, s>>>(p2, n, nullptr, stats, nullptr, origin, za, interior, offs, nullptr);
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8L * sm_count()));
+    if (m > 0) k_border_flags<<<nb, 256, 0, s>>>(interior, m, flags);
+    k_border_project<<<nb, 256, 0, s>>>(p2, n, sigma, flags);
+    return cuda_status(cudaGetLastError(), "border split launch");
 }
 
 }  // extern "C"

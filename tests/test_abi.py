@@ -31,7 +31,8 @@ def test_struct_layouts_match_header(lib):
     assert C.sizeof(L.RelaxProfile) == 56
     # tc_zone_params: 4 double, 4 int32; tc_cycle_params: zone, relax, 2 int32
     assert C.sizeof(L.ZoneParams) == 48 and L.ZoneParams.m_min.offset == 32
-    assert C.sizeof(L.CycleParams) == 144 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 136
+    assert C.sizeof(L.CycleParams) == 160 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 136
+    assert L.CycleParams.sigma0.offset == 144
 
 
 def test_status_strings(lib):
@@ -50,9 +51,22 @@ def test_argument_errors_are_synchronous_without_touching_a_device(lib):
     prm = L.RelaxParams(precision=7)
     assert lib.tc_relax_subdomains(None, 10, None, None, 1, None, None, C.byref(prm), None, None) == 1
     z = L.ZoneParams(kappa=-1.0, p_defect=0.8, radius=1.0, wall_tol=1e-9, m_min=5, m_max=3, period=4)
-    assert lib.tc_select_subdomains(None, 10, None, C.byref(z), 1, None, None, None, None, None, None) == 1
+    assert lib.tc_select_subdomains(None, 10, None, None, C.byref(z), 1, None, None, None, None, None, None) == 1
     cp = L.CycleParams(zone=z, batch=0)
-    assert lib.tc_cycle(None, 10, C.byref(cp), 1, None, None, None, None) == 1
+    assert lib.tc_cycle(None, 10, None, C.byref(cp), 1, None, None, None, None) == 1
+    z.m_max = 7
+    cp = L.CycleParams(zone=z, batch=1, sigma0=0.5, sigma1=0.4)  # sigma must not fall
+    assert lib.tc_cycle(None, 10, None, C.byref(cp), 1, None, None, None, None) == 1
+    assert lib.tc_border_split(None, 10, 11, 0.9, None, None) == 1  # n_b > n
+
+
+def test_boundary_count_host_only_matches_oracle(lib):
+    """Eq. Nb on the host: the library's N_b equals the oracle's for every n up to 3000 and at 1e5."""
+    import oracle
+
+    for n in list(range(0, 3001)) + [12345, 100000, 10 ** 7]:
+        assert lib.tc_boundary_count(n) == oracle.boundary_count(n)
+    assert lib.tc_boundary_count(100000) == 6099
 
 
 def test_zone_offsets_host_only_matches_oracle(lib):

@@ -154,3 +154,75 @@ def test_cycle_mixed_lowers_energy_and_books_it():
         sl = slice(8 * b, 8 * b + 8)
         assert abs((tr[b + 1] - tr[b]) - d[sl][st[sl] == 1].sum()) <= 1e-12 * tr[b]
     assert abs(tr[-1] - oracle.energy(p.cpu().numpy())) <= 1e-13 * tr[-1]
+
+
+# ------------------------------------------------ border-interior split (Sec. II B) ---
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (7, 1), (2000, 2), (100_000, 3)])
+def test_border_split_matches_oracle(n, seed):
+    pos = synth.arcsine_disk(n, seed)
+    nb = oracle.boundary_count(n)
+    sigma = 1 - 1 / (2 * np.sqrt(n))
+    po, fo = oracle.border_split(pos, nb, sigma)
+    p = T(pos.copy())
+    f = tc.border_split(p, nb, sigma)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(f.cpu().numpy(), fo)
+    np.testing.assert_array_equal(p.cpu().numpy(), po)
+
+
+def test_border_split_defaults_and_ties():
+    g = np.array([[1, 0], [0, 1], [-1, 0], [0, -1], [0.5, 0], [0, 0.25]], dtype=float) * 0.75
+    po, fo = oracle.border_split(g, 2, 0.9)
+    p = T(g.copy())
+    f = tc.border_split(p, 2, 0.9)
+    torch.cuda.synchronize()
+    assert f.cpu().tolist() == fo.tolist() == [0, 0, 1, 1, 0, 0]
+    np.testing.assert_array_equal(p.cpu().numpy(), po)
+    pos = synth.arcsine_disk(5000, 6)
+    p = T(pos.copy())
+    f = tc.border_split(p)
+    torch.cuda.synchronize()
+    assert int(f.sum()) == oracle.boundary_count(5000)
+    for nb in [0, 5000]:
+        q = T(pos.copy())
+        assert int(tc.border_split(q, nb, 0.99).sum()) == nb
+
+
+def test_select_with_flags_matches_oracle():
+    n = 3000
+    pos = synth.arcsine_disk(n, 15)
+    _, f = oracle.border_split(pos, oracle.boundary_count(n), 1.0)  # flags only; positions as drawn
+    _, e = oracle.energy(pos, local=True)
+    u = np.random.default_rng(16).random((30, 3))
+    kw = dict(m_min=10, m_max=400, period=7, p_defect=0.9)
+    io, oo, co, so = oracle.zone_select(pos, e, u, flags=f, **kw)
+    idx, off, cen, st = tc.select_subdomains(T(pos), T(e), T(u), flags=T(f), **kw)
+    torch.cuda.synchronize()
+    assert margin_ok(pos, e, u, oo, io, co, so, -1.0)
+    assert st.cpu().numpy()[2] == so[2]
+    np.testing.assert_array_equal(off.cpu().numpy(), oo)
+    np.testing.assert_array_equal(idx.cpu().numpy(), io)
+
+
+@pytest.mark.parametrize("batch", [2, 5])
+def test_cycle_pinned_sigma_ramp_fp64_matches_oracle(batch):
+    n = 1500
+    pos = synth.arcsine_disk(n, 13)
+    s0 = 1 - 1 / (2 * np.sqrt(n))
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
+    u = np.random.default_rng(14).random((10, 3))
+    eta = 1e-4 / n
+    kw = dict(m_min=20, m_max=150, period=4)
+    po, trace_o, do, ao = oracle.cycle(p0, u, batch=batch, step0=eta, alpha_min=0.0, alpha_max=10 * eta, steps=8,
+                                       sigma0=s0, sigma1=1.0, flags=f, **kw)
+    p = T(p0.copy())
+    r, trace = tc.cycle(p, T(u), T(f), batch=batch, local_precision="fp64", precision="fp64", optimizer="bb",
+                        n_steps=8, step0=eta, alpha_min=0.0, alpha_max=10 * eta, sigma0=s0, sigma1=1.0, **kw)
+    tc.sync_status()
+    np.testing.assert_array_equal(r.status.cpu().numpy(), ao)
+    np.testing.assert_allclose(p.cpu().numpy(), po, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(trace.cpu().numpy(), trace_o, rtol=1e-13)
+    x = p.cpu().numpy()
+    rr = np.hypot(x[:, 0], x[:, 1])
+    assert np.all(np.abs(rr[f == 1] - 1.0) <= 4.5e-16)

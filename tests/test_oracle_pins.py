@@ -511,3 +511,80 @@ def test_cycle_energy_bookkeeping():
         assert (acc == 1).sum() >= 1
         if batch == 1:
             assert not np.any(acc == 2)
+
+
+# ------------------------------------------------ border-interior split (Sec. II B) ---
+
+def test_boundary_count_is_the_papers():
+    """Eq. Nb at N = 1e5 gives the paper's N_b (Table I); small N clamp at 0; N_b grows with N."""
+    gd = golden()
+    assert oracle.boundary_count(100_000) == gd["N_b_best"]
+    assert oracle.boundary_count(0) == 0 and oracle.boundary_count(1) == 0
+    seq = [oracle.boundary_count(n) for n in range(1, 5000)]
+    assert all(a <= b <= a + 2 for a, b in zip(seq, seq[1:]))
+    assert all(0 <= b <= n for n, b in zip(range(1, 5000), seq))
+
+
+def test_sigma_ramp_endpoints_and_linearity():
+    s0 = 1 - 1 / (2 * math.sqrt(1e5))  # Eq. sigma
+    assert oracle.sigma_ramp(s0, 1.0, 0, 9) == s0 and oracle.sigma_ramp(s0, 1.0, 8, 9) == 1.0
+    assert oracle.sigma_ramp(s0, 1.0, 0, 1) == 1.0
+    mid = oracle.sigma_ramp(s0, 1.0, 4, 9)
+    assert abs(mid - (s0 + 1.0) / 2) <= 1e-16
+
+
+def test_border_split_pins_the_outermost():
+    """The n_b charges of largest |r| (ties: larger index first) end on the unit circle with flags set;
+    the others end inside sigma, unchanged where they already were."""
+    n = 2000
+    pos = synth.arcsine_disk(n, 8)
+    nb = oracle.boundary_count(n)
+    sigma = 1 - 1 / (2 * math.sqrt(n))
+    p, f = oracle.border_split(pos, nb, sigma)
+    r0 = np.hypot(pos[:, 0], pos[:, 1])
+    assert f.sum() == nb
+    assert r0[f == 1].min() >= r0[f == 0].max()
+    r1 = np.hypot(p[:, 0], p[:, 1])
+    assert np.all(np.abs(r1[f == 1] - 1.0) <= 4.5e-16)
+    assert np.all(r1[f == 0] <= sigma * (1 + 4.5e-16))
+    keep = (f == 0) & (r0 <= sigma)
+    assert np.array_equal(p[keep], pos[keep])
+    # direction preserved
+    cross = pos[:, 0] * p[:, 1] - pos[:, 1] * p[:, 0]
+    assert np.all(np.abs(cross) <= 1e-15)
+    # exact ties on a dyadic ring: the larger indices become boundary charges
+    g = np.array([[1, 0], [0, 1], [-1, 0], [0, -1], [0.5, 0], [0, 0.25]], dtype=float) * 0.75
+    _, f2 = oracle.border_split(g, 2, 0.9)
+    assert f2.tolist() == [0, 0, 1, 1, 0, 0]
+
+
+def test_cycle_with_pinned_boundary_and_sigma_ramp():
+    """With the split and a sigma ramp, the cycle keeps its bookkeeping, pinned charges stay on the unit
+    circle and never become centres' defects, and free charges stay within the final sigma."""
+    n = 1500
+    pos = synth.arcsine_disk(n, 13)
+    nb = oracle.boundary_count(n)
+    s0 = 1 - 1 / (2 * math.sqrt(n))
+    p0, f = oracle.border_split(pos, nb, s0)
+    u = np.random.default_rng(14).random((9, 3))
+    eta = 1e-4 / n
+    # pinned charges are never defects: on the unprojected input they are not excluded by radius
+    _, e = oracle.energy(pos, local=True)
+    _, _, cen, st = oracle.zone_select(pos, e, u, m_min=20, m_max=150, period=4, flags=f, p_defect=1.0)
+    _, _, _, st_nf = oracle.zone_select(pos, e, u, m_min=20, m_max=150, period=4, p_defect=1.0)
+    thr = st[0] - st[1]
+    r0 = np.hypot(pos[:, 0], pos[:, 1])
+    assert st_nf[2] - st[2] == np.sum((e > thr) & (f == 1) & (r0 < 1 - 1e-9)) > 0
+    for c in cen:
+        k = np.flatnonzero((pos == c).all(1))
+        assert len(k) == 1 and f[k[0]] == 0
+    p, trace, d, acc = oracle.cycle(p0, u, m_min=20, m_max=150, period=4, batch=3, step0=eta, alpha_min=0.0,
+                                    alpha_max=10 * eta, steps=8, sigma0=s0, sigma1=1.0, flags=f)
+    assert np.all(np.diff(trace) <= 0)
+    for b in range(3):
+        sl = slice(3 * b, 3 * b + 3)
+        assert abs((trace[b + 1] - trace[b]) - d[sl][acc[sl] == 1].sum()) <= 1e-12 * trace[b]
+    r = np.hypot(p[:, 0], p[:, 1])
+    assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
+    assert np.all(r[f == 0] <= 1.0 + 1e-15)
+    assert (acc == 1).sum() >= 1
