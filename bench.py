@@ -377,6 +377,16 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     pairs = int(sizes.sum()) * (n - 1) * (steps + 1) + n_batches * n * (n - 1)
     tr = trace.cpu().numpy()
     st = r.status.cpu().numpy()
+    # structure analysis of the cycle's end configuration (Sec. III C-D)
+    tc.voronoi_order(p)
+    torch.cuda.synchronize()
+    a.record()
+    _, _, summ, _ = tc.voronoi_order(p)
+    b.record()
+    torch.cuda.synchronize()
+    tc.sync_status()
+    structure = {"ms": a.elapsed_time(b), "P_z6": float(summ["P_z"][6]), "mean_abs_psi6": summ["mean_abs_psi6"],
+                 "abs_mean_psi6": summ["abs_mean_psi6"]}
     return {"workload": f"N={n} lattice background split into N_b={tc.boundary_count(n)} pinned boundary charges "
                         f"and an interior disk whose radius ramps {sigma0:.5f} -> 1 over the batches; {n_sub} "
                         f"subdomains in batches of {batch}, zones of {m_min}..{m_max} nearest charges (triangle "
@@ -384,7 +394,8 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
                         f"per batch, fp64 sequential accept",
             "cycle_time_s": ms / 1e3, "ms_per_subdomain": ms / n_sub, "pairs_per_s": pairs / (ms / 1e3),
             "accepted": int((st == 1).sum()), "skipped_overlap": int((st == 2).sum()),
-            "energy_start": float(tr[0]), "energy_end": float(tr[-1]), "energy_drop": float(tr[0] - tr[-1])}
+            "energy_start": float(tr[0]), "energy_end": float(tr[-1]), "energy_drop": float(tr[0] - tr[-1]),
+            "structure": structure}
 
 
 def run_reference(args):

@@ -302,6 +302,28 @@ int64_t tc_boundary_count(int64_t n);
  *   0 <= n_b <= n;  0 < sigma <= 1.  Asynchronous on `stream`. */
 tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uint8_t* flags, tc_stream stream);
 
+/* Structure analysis of Sec. III C-D: Voronoi neighbours, the coordination
+ * number z_i (the number of neighbours) and the sixfold bond-orientational
+ * order of Eq. (psi6), psi6_i = (1/z_i) sum_{j in N(i)} exp(6 i theta_ij),
+ * theta_ij the angle of the bond i -> j against the x axis.  Two charges are
+ * Voronoi neighbours when their cells share an edge (equivalently, a Delaunay
+ * edge joins them).  Each cell is built in float64 by clipping the square
+ * [-1e6, 1e6]^2 with the bisectors of the charges that can still cut it, so
+ * cells of charges on the convex hull are cut off at that square; a Voronoi
+ * edge lying wholly outside it (three hull charges collinear to ~1e-6) would
+ * be missed.
+ *   pos     [2n]          device positions
+ *   z       [n]           device int32, written
+ *   psi6    [2n]          device (re, im) pairs, written; 0 for z_i = 0
+ *   nbr     [n max_nbr]   device int32, nullable: neighbours of i ascending at
+ *                         nbr[i max_nbr ..], -1 padded
+ *   summary [18]          device, nullable: <|psi6|>, |<psi6>|, then P(z) for
+ *                         z = 0 .. 15 (the last bin holds z >= 15)
+ * Device errors: TC_ERR_NONFINITE (coincident charges), TC_ERR_INVALID_ARG
+ * (a cell with more than 40 vertices while clipping, or z_i > max_nbr). */
+tc_status tc_voronoi_order(const double* pos, int64_t n, int32_t* z, double* psi6, int32_t* nbr, int32_t max_nbr,
+                           double* summary, tc_stream stream);
+
 /* Total energy (and local energies) exactly as tc_energy computes them, but
  * without allocating any device memory.  The paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc: code that runs

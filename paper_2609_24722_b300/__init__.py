@@ -28,7 +28,7 @@ __all__ = [
     "energy", "grad", "local_energy", "project_disk", "subdomain_delta_energy", "relax_subdomains",
     "coulomb_energy", "CoulombEnergy", "sync_status", "probe_pipes", "relax_last_profile", "TCError", "RelaxParams",
     "library_path", "zone_params", "zone_offsets", "select_subdomains", "cycle", "subdomain_delta_energy_mixed",
-    "boundary_count", "border_split",
+    "boundary_count", "border_split", "voronoi_order",
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED}
@@ -306,3 +306,20 @@ class CoulombEnergy(torch.autograd.Function):
 
 def coulomb_energy(pos: torch.Tensor, precision="fp64") -> torch.Tensor:
     return CoulombEnergy.apply(pos, precision)
+
+
+def voronoi_order(pos, max_nbr: int = 0):
+    """Voronoi coordination numbers and psi6 (Sec. III C-D, Eq. psi6).
+
+    Returns (z int32 (n,), psi6 complex128 (n,), summary dict, neighbours (n, max_nbr) int32 or None)."""
+    _pos(pos)
+    n = pos.shape[0]
+    z = torch.empty(n, dtype=torch.int32, device=pos.device)
+    psi = torch.empty((n, 2), dtype=torch.float64, device=pos.device)
+    nbr = torch.empty((n, max_nbr), dtype=torch.int32, device=pos.device) if max_nbr > 0 else None
+    summ = torch.empty(18, dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_voronoi_order(_p(pos), n, _p(z), _p(psi), _p(nbr), int(max_nbr), _p(summ), _stream()),
+            "tc_voronoi_order")
+    sm = summ.cpu()
+    summary = {"mean_abs_psi6": float(sm[0]), "abs_mean_psi6": float(sm[1]), "P_z": sm[2:].numpy()}
+    return z, torch.view_as_complex(psi), summary, nbr

@@ -133,6 +133,7 @@ def _lib() -> C.CDLL:
                                      C.c_int),
             "tc_cycle": ([vp, i64, vp, C.POINTER(CycleParams), i32, vp, vp, vp, vp], C.c_int),
             "tc_boundary_count": ([i64], i64),
+            "tc_voronoi_order": ([vp, i64, vp, vp, vp, i32, vp, vp], C.c_int),
             "tc_border_split": ([vp, i64, i64, d, vp, vp], C.c_int),
         }
         for name, (args, res) in sigs.items():

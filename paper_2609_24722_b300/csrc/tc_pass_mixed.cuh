@@ -71,14 +71,18 @@ template <int R> struct MixedRows {
     // One tile of T sources.  hi[j] = (-x_hi, -x_hi, -y_hi, -y_hi), lo[j] the
     // same for the lo parts.  The tile sums (sum dx r^-3 = -grad, sum 1/r) are
     // folded into the shared accumulators acc[6R][stride] with TwoSum.
-    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G>
+    // Only the first PA pairs are computed: the caller passes PA < P when every
+    // row of the later pairs lies past the end of the problem (a partial last
+    // row block), so the CTA skips them together.
+    template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G, int PA = P>
     __device__ __forceinline__ void tile(const float4* __restrict__ hi, const float4* __restrict__ lo,
                                          const float2* lo2, float* acc, int stride, int tid, int jself0,
                                          float escale)
     {
-        float2 et[P], gxt[P], gyt[P], xl[P], yl[P], xh[P], yh[P];
+        static_assert(PA >= 1 && PA <= P, "active pairs");
+        float2 et[PA], gxt[PA], gyt[PA], xl[PA], yl[PA], xh[PA], yh[PA];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
+        for (int p = 0; p < PA; ++p) {
             et[p] = gxt[p] = gyt[p] = make_float2(0.f, 0.f);
             xh[p] = lo2[(2 * P + p) * stride + tid];
             yh[p] = lo2[(3 * P + p) * stride + tid];
@@ -98,7 +102,7 @@ template <int R> struct MixedRows {
                 ly = make_float2(l.z, l.w);
             }
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
+            for (int p = 0; p < PA; ++p) {
                 float2 dx = __fadd2_rn(xh[p], qx);
                 float2 dy = __fadd2_rn(yh[p], qy);
                 if (NEAR) {
@@ -121,7 +125,7 @@ template <int R> struct MixedRows {
             }
         }
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
+        for (int p = 0; p < PA; ++p) {
             const float ev[2] = {et[p].x, et[p].y}, gxv[2] = {gxt[p].x, gxt[p].y}, gyv[2] = {gyt[p].x, gyt[p].y};
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
@@ -289,15 +293,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
                 // memory base is a compile-time address and every source load
                 // uses an immediate offset
                 const int kind = self ? 2 : (boxes_far(rb4, tbox) ? 0 : 1);
+                // far tiles of a row block whose rows all lie in its first half
+                // skip the second half's pairs (CTA-uniform)
+                constexpr int PH = P >= 2 ? P / 2 : P;
+                const bool half = P >= 2 && (int64_t)rb * RB + 2 * PH * THREADS >= sprob.m;
                 if (buf == 0) {
-                    if (kind == 0)
+                    if (kind == 0 && half)
+                        rs.template tile<T, false, false, WANT_E, WANT_G, PH>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
+                    else if (kind == 0)
                         rs.template tile<T, false, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
                     else if (kind == 1)
                         rs.template tile<T, true, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
                     else
                         rs.template tile<T, true, true, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
                 } else {
-                    if (kind == 0)
+                    if (kind == 0 && half)
+                        rs.template tile<T, false, false, WANT_E, WANT_G, PH>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
+                    else if (kind == 0)
                         rs.template tile<T, false, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
                     else if (kind == 1)
                         rs.template tile<T, true, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);

@@ -588,3 +588,58 @@ def test_cycle_with_pinned_boundary_and_sigma_ramp():
     assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
     assert np.all(r[f == 0] <= 1.0 + 1e-15)
     assert (acc == 1).sum() >= 1
+
+
+# ------------------------------------------------ structure analysis (Sec. III C-D) ---
+
+def _tri_lattice(k, h=0.05, angle=0.0):
+    pts = []
+    for a in range(-k, k + 1):
+        for b in range(-k, k + 1):
+            x, y = h * (a + 0.5 * b), h * (b * math.sqrt(3) / 2)
+            pts.append((x, y))
+    p = np.array(pts)
+    c, s = math.cos(angle), math.sin(angle)
+    return p @ np.array([[c, s], [-s, c]])
+
+
+def test_structure_triangular_lattice():
+    """Interior sites of a triangular lattice have six neighbours and |psi6| = 1; rotating the lattice
+    by alpha turns psi6 into exp(6 i alpha)."""
+    from oracle import structure as S
+
+    # a small in-plane jitter breaks the lattice's cocircular degeneracy without changing neighbours
+    rng = np.random.default_rng(3)
+    for alpha in [0.0, 0.1, 0.37]:
+        p = _tri_lattice(6, angle=alpha)
+        p = p + rng.normal(0, 1e-9, p.shape)
+        z, psi = S.order(p)
+        inner = np.hypot(p[:, 0], p[:, 1]) < 0.15
+        assert np.all(z[inner] == 6)
+        assert np.allclose(np.abs(psi[inner]), 1.0, atol=1e-6)
+        assert np.allclose(psi[inner], np.exp(6j * alpha), atol=1e-6)
+
+
+def test_structure_polygon_centres_and_euler():
+    """A charge at the centre of a regular k-gon has k neighbours and psi6 = (1/k) sum exp(6 i 2 pi m/k)
+    (1 for k = 6, 0 for k = 7); every triangulation has sum z = 2 (3N - 3 - h), h the hull size."""
+    from oracle import structure as S
+
+    for k, want in [(6, 1.0 + 0j), (7, 0j), (12, 0j)]:
+        ang = 2 * math.pi * np.arange(k) / k + 0.05
+        ring = 0.8 * np.stack([np.cos(ang), np.sin(ang)], 1)
+        p = np.vstack([[0.0, 0.0], ring])
+        z, psi = S.order(p)
+        assert z[0] == k
+        ref = np.exp(6j * 2 * math.pi * np.arange(k) / k).mean() * np.exp(6j * 0.05)
+        assert abs(psi[0] - ref) <= 1e-12 and abs(abs(psi[0]) - abs(want)) <= 1e-12
+    # ring of h charges on the circle + random interior: the hull is exactly the ring
+    h = 40
+    ang = 2 * math.pi * (np.arange(h) + 0.3) / h
+    ring = np.stack([np.cos(ang), np.sin(ang)], 1)
+    inner = synth.arcsine_disk(300, 4) * 0.9
+    p = np.vstack([ring, inner])
+    z, _ = S.order(p)
+    assert z.sum() == 2 * (3 * len(p) - 3 - h)
+    nb = S.neighbours(p)
+    assert all(i in nb[j] for i in range(len(p)) for j in nb[i])  # symmetric
