@@ -2,8 +2,9 @@
 """Benchmark: Coulomb pair interactions per second at N = 100 000 (one adaptive-cycle step).
 
 One step is one pass of the whole hot path over one batch of synthetic input:
-  1. float64 local energies e_i of all N charges (Sec. II C step 1: N(N-1)
-     ordered pair interactions),
+  1. float64-grade local energies e_i of all N charges (Sec. II C step 1:
+     N(N-1) ordered pair interactions; the fp64x pass: double-float terms on
+     the float32 pipes, held to the float64 tolerances),
   2. 256 subdomains (m ~ U{200..5000}, the m nearest charges to a centre)
      relaxed together against all N for 200 mixed-precision projected
      Barzilai-Borwein steps (Sec. II C step 4, Sec. II E: m(N-1) pair
@@ -38,9 +39,10 @@ N = 100_000
 N_SUB = 256
 M_LO, M_HI = 200, 5000
 RELAX_STEPS = 200
+LOCAL_PREC = "fp64x"  # float64-grade local energies (double-float on the float32 pipes)
 METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
 UNIT = "pair-interactions/s"
-WORKLOAD = ("adaptive-cycle step at N=1e5: fp64 local energies of all charges + 256 subdomains "
+WORKLOAD = ("adaptive-cycle step at N=1e5: fp64x (float64-grade) local energies of all charges + 256 subdomains "
             "(m~U[200,5000], nearest charges to a centre) x 200 mixed BB steps against all N + fp64 "
             "sequential accept; triangular-lattice background mapped to the arcsine density, 0.5% jitter, "
             "charges stored in Hilbert-curve order")
@@ -58,7 +60,7 @@ def parse():
     ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle"], default=None)
     ap.add_argument("--batch", type=int, default=64, help="cycle case: subdomains per batch")
     ap.add_argument("--zone-steps", type=int, default=100, help="cycle case: relaxation steps per zone")
-    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--prec", choices=["mixed", "fp64", "fp64x"], default="mixed")
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--nsub", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
@@ -239,9 +241,9 @@ def cpu_baseline(pos, idx, off, seconds: float = 12.0) -> dict:
 
 
 def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
-                  polish: int = 20, fp64_steps: int = 10):
+                  polish: int = 50, fp64_steps: int = 10):
     """Config C5: 512 independent instances (N_k ~ U{100..5000}, arcsine init each), relaxed in one
-    batched call per round (mixed L-BFGS, memory 8, then float64 polish), 3 perturbation restarts
+    batched call per round (mixed L-BFGS, memory 8, then a float64-grade fp64x polish), 3 perturbation restarts
     (Gaussian kicks of 0.05 x the instance's lattice spacing) keeping each instance's best energy;
     then the same instances with float64 pair terms for a few steps (throughput side by side)."""
     import numpy as np
@@ -260,6 +262,7 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
     best_e = np.full(n_inst, np.inf)
     kw = dict(precision="mixed", optimizer="lbfgs", n_steps=steps, memory=8, step0=1e-5,
               maxstep=0.1 * float(h.min()), polish_steps=polish, polish_gtol=0.0, accept=False,
+              polish_precision="fp64x",
               want_energy=True)
     ms_total, pairs_total, launches = 0.0, 0, 0
     for r in range(rounds):
@@ -294,17 +297,17 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
     ms64 = a.elapsed_time(b)
     pairs64 = int((sizes * (sizes - 1)).sum()) * fp64_steps
     return {"workload": f"{n_inst} instances, N_k~U[100,5000] (sum {int(sizes.sum())}), arcsine init, "
-                        f"{rounds - 1} kick restarts, mixed L-BFGS(8) {steps} steps + fp64 polish {polish}",
+                        f"{rounds - 1} kick restarts, mixed L-BFGS(8) {steps} steps + fp64x polish {polish}",
             "relax_time_s": ms_total / 1e3, "pairs_per_s_mixed_with_polish": pairs_total / (ms_total / 1e3),
             "pairs_per_s_fp64": pairs64 / (ms64 / 1e3), "fp64_steps": fp64_steps,
             "best_energy_sum": float(best_e.sum()),
             "fp64_energy_vs_oracle_max_rel": parity}
 
 
-def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 200) -> dict:
+def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 1000) -> dict:
     """Config C4: one configuration of N = 1e5 charges (arcsine init, Hilbert order) relaxed by
     mixed-precision L-BFGS(8) on the wall map until the RMS of dE/dz falls below 1e-4 x the initial
-    mean force, then float64 L-BFGS to 1e-8 x that (step caps max_mixed / max_polish)."""
+    mean force, then float64-grade (fp64x) L-BFGS to 1e-8 x that (step caps max_mixed / max_polish)."""
     import numpy as np
     import torch
 
@@ -325,13 +328,15 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
                              step0=1e-6, maxstep=0.1 * h, gtol=1e-4 * f_ref, accept=False)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    r2 = tc.relax_subdomains(p, world=world, precision="fp64", optimizer="lbfgs", n_steps=max_polish, memory=8,
+    r2 = tc.relax_subdomains(p, world=world, precision="fp64x", optimizer="lbfgs", n_steps=max_polish, memory=8,
                              step0=1e-6, maxstep=0.1 * h, gtol=1e-8 * f_ref, accept=False, want_energy=True)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     tc.sync_status()
     e = r2.energy[0].item()
-    return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, fp64 polish to 1e-8",
+    return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, fp64x polish to 1e-8 "
+                        f"(caps {max_mixed} / {max_polish} steps)",
+            "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
             "mixed_steps": int(r1.steps[0]), "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
             "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1,
             "relax_time_s": t2 - t0, "mean_force_initial": f_ref, "energy_initial": e0, "energy_final": e,
@@ -465,7 +470,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(p):
-        e, loc = tc.local_energy(p, "fp64")
+        e, loc = tc.local_energy(p, LOCAL_PREC)
         r = tc.relax_subdomains(p, idx, off, **relax_kw)
         return e, r
 
@@ -516,7 +521,7 @@ def main():
         p_d = pos_h.to(dev, non_blocking=True)
         i_d = idx_h.to(dev, non_blocking=True)
         o_d = off_h.to(dev, non_blocking=True)
-        e_d, _ = tc.local_energy(p_d, "fp64")
+        e_d, _ = tc.local_energy(p_d, LOCAL_PREC)
         r = tc.relax_subdomains(p_d, i_d, o_d, **{**relax_kw, "profile": False})
         out_h.copy_(p_d, non_blocking=True)
         res_h[:, 0].copy_(r.delta_e, non_blocking=True)
@@ -545,6 +550,7 @@ def main():
 
     ms_mixed = time_allpairs("mixed", 5)
     ms_f64 = time_allpairs("fp64", 3)
+    ms_f64x = time_allpairs("fp64x", 3)
     c5 = run_instances(dev) if not args.no_instances else None
     cyc = run_cycle(dev) if not args.no_instances else None
     pipes = tc.probe_pipes()
@@ -571,7 +577,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulation (mixed); f64 energies/accept",
+        "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulation (mixed); float64-grade double-float local energies (fp64x); f64 accept",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "n_sub": N_SUB, "m_range": [M_LO, M_HI],
                    "relax_steps": RELAX_STEPS, "optimizer": "projected BB, step0 1e-4/N, alpha_max 1e-3/N",
@@ -583,7 +589,8 @@ def main():
                          "relax_loop": prof["relax_ms"], "accept": prof["accept_ms"], "setup": prof["setup_ms"]},
         "accepted_subdomains": accepted[-1],
         "allpairs_n1e5": {"mixed_pairs_per_s": N * (N - 1) / (ms_mixed / 1e3), "mixed_ms": ms_mixed,
-                          "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64},
+                          "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64,
+                          "fp64x_pairs_per_s": N * (N - 1) / (ms_f64x / 1e3), "fp64x_ms": ms_f64x},
         "instances_c5": c5,
         "adaptive_cycle": cyc,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -55,8 +55,12 @@ typedef enum {
 
 typedef enum {
     TC_FP64 = 0,  /* every pair term and sum in float64 */
-    TC_MIXED = 1  /* pair terms in float32 from hi/lo-split positions, tile sums
+    TC_MIXED = 1, /* pair terms in float32 from hi/lo-split positions, tile sums
                      in float32, cross-tile sums double-float, rows combined in float64 */
+    TC_F64X = 2   /* float64-grade results from float32 arithmetic: positions split in
+                     three float32 parts (exact separations), pair terms and tile sums in
+                     double-float (~2^-46 relative per term), rows combined in float64;
+                     held to the float64 tolerances (1e-13 energy, 1e-12 gradient) */
 } tc_precision;
 
 /* Launch shapes of the pair passes (tuning; the paper has no counterpart).
@@ -87,7 +91,7 @@ void tc_shutdown(void);
 /* Total energy, Eq. (hamiltonian):  E = sum_{i<j} 1/|r_i - r_j|.
  *   pos      [2n]  positions (read)
  *   n              number of charges, n >= 0
- *   prec           TC_FP64 or TC_MIXED
+ *   prec           TC_FP64, TC_F64X or TC_MIXED
  *   energy   [1]   E (written)
  *   local_e  [n]   nullable; e_i = 1/2 sum_{j != i} 1/|r_i - r_j|
  *                  (Sec. II C step 1), so sum_i e_i = E
@@ -152,7 +156,7 @@ typedef enum {
 } tc_optimizer;
 
 typedef struct {
-    int32_t precision;   /* tc_precision of the bulk steps */
+    int32_t precision;   /* tc_precision of the bulk steps (TC_MIXED, TC_FP64 or TC_F64X) */
     int32_t optimizer;   /* tc_optimizer */
     int32_t n_steps;     /* bulk steps per problem (>= 0) */
     int32_t memory;      /* L-BFGS history pairs, 1..16 */
@@ -169,6 +173,7 @@ typedef struct {
     int32_t want_energy; /* 1: also report each problem's final float64 E_sub / E */
     int32_t profile;     /* 1: launch the step loop directly (no CUDA graph) and time each
                             launch with CUDA events (see tc_relax_last_profile) */
+    int32_t polish_precision; /* TC_FP64 (0, the default) or TC_F64X for the polish steps */
 } tc_relax_params;
 
 typedef struct {

@@ -17,6 +17,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "tc.h")
 TC_OK = 0
 TC_FP64 = 0
 TC_MIXED = 1
+TC_F64X = 2
 TC_OPT_GD, TC_OPT_BB, TC_OPT_LBFGS = 0, 1, 2
 STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_CUDA", 3: "TC_ERR_NONFINITE",
                 4: "TC_ERR_OUTSIDE_DISK", 5: "TC_ERR_TIMEOUT", 6: "TC_ERR_NOT_CONVERGED", 7: "TC_ERR_NO_MEMORY"}
@@ -53,6 +54,7 @@ class RelaxParams(C.Structure):
         ("polish_gtol", C.c_double),
         ("want_energy", C.c_int32),
         ("profile", C.c_int32),
+        ("polish_precision", C.c_int32),
     ]
 
 

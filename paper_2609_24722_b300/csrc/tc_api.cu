@@ -147,7 +147,7 @@ const char* tc_status_string(tc_status s)
 
 int32_t tc_pass_config_count(tc_precision prec)
 {
-    return prec == TC_MIXED ? tc::kMixedConfigs : (prec == TC_FP64 ? 1 : 0);
+    return prec == TC_MIXED ? tc::kMixedConfigs : ((prec == TC_FP64 || prec == TC_F64X) ? 1 : 0);
 }
 
 tc_status tc_set_pass_config(tc_precision prec, int32_t config)
@@ -156,7 +156,7 @@ tc_status tc_set_pass_config(tc_precision prec, int32_t config)
         tc::g_mixed_config = config;
         return TC_OK;
     }
-    if (prec == TC_FP64 && config == 0) return TC_OK;
+    if ((prec == TC_FP64 || prec == TC_F64X) && config == 0) return TC_OK;
     return TC_ERR_INVALID_ARG;
 }
 

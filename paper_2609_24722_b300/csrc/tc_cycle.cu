@@ -14,7 +14,7 @@
 #include "tc_plan.cuh"
 
 static_assert(sizeof(tc_zone_params) == 48, "tc_zone_params layout");
-static_assert(sizeof(tc_cycle_params) == 160, "tc_cycle_params layout");
+static_assert(sizeof(tc_cycle_params) == 168, "tc_cycle_params layout");
 
 namespace tc {
 

@@ -186,14 +186,65 @@ __host__ __device__ __forceinline__ f8 make_f8(float4 p, float dx, float dy)
     return r;
 }
 
+// A coordinate pair split into three float32 parts for the float64-grade
+// float32 pass: x = hi + mid + lo with hi on the grid 2^-21, mid on the grid
+// 2^-44 and lo the float32 rounding of the rest (|lo| <= 2^-45, error <= 2^-69).
+// For |x| <= 1 the differences of two his and of two mids are exact in
+// float32 (at most 23 and 24 significant bits), so a separation is known to
+// ~2^-69 before any arithmetic.  Values beyond the disk (far sentinels) keep
+// hi = (float)x and zero mid and lo.
+struct alignas(32) fx3 {
+    float4 hm;  // (x_hi, y_hi, x_mid, y_mid)
+    float2 lo;  // (x_lo, y_lo)
+    float2 pad;
+};
+
+__host__ __device__ __forceinline__ void split3_1(double x, float& h, float& m, float& l)
+{
+    if (!(fabs(x) <= 2.0)) {
+        h = (float)x;
+        m = 0.f;
+        l = 0.f;
+        return;
+    }
+    const double hd = rint(x * 2097152.0) * (1.0 / 2097152.0);   // 2^21
+    const double r1 = x - hd;                                      // exact, |r1| <= 2^-22
+    const double md = rint(r1 * 17592186044416.0) * (1.0 / 17592186044416.0);  // 2^44
+    h = (float)hd;
+    m = (float)md;
+    l = (float)(r1 - md);
+}
+
+__host__ __device__ __forceinline__ fx3 split3(double x, double y)
+{
+    fx3 r;
+    float xh, xm, xl, yh, ym, yl;
+    split3_1(x, xh, xm, xl);
+    split3_1(y, yh, ym, yl);
+    r.hm = make_float4(xh, yh, xm, ym);
+    r.lo = make_float2(xl, yl);
+    r.pad = make_float2(0.f, 0.f);
+    return r;
+}
+
+__host__ __device__ __forceinline__ fx3 far3(float v)
+{
+    fx3 r;
+    r.hm = make_float4(v, v, 0.f, 0.f);
+    r.lo = make_float2(0.f, 0.f);
+    r.pad = make_float2(0.f, 0.f);
+    return r;
+}
+
 // Pass flavours.
-enum PassKind { PASS_MIXED = 0, PASS_F64 = 1, PASS_DELTA = 2, PASS_DMIX = 3 };
+enum PassKind { PASS_MIXED = 0, PASS_F64 = 1, PASS_DELTA = 2, PASS_DMIX = 3, PASS_F64X = 4 };
 
 template <int KIND> struct SrcT;
 template <> struct SrcT<PASS_MIXED> { using type = float4; };   // (x_hi, y_hi, x_lo, y_lo)
 template <> struct SrcT<PASS_F64> { using type = double2; };    // (x, y)
 template <> struct SrcT<PASS_DELTA> { using type = d4; };  // (x_old, y_old, x_new, y_new)
 template <> struct SrcT<PASS_DMIX> { using type = f8; };   // old split + move
+template <> struct SrcT<PASS_F64X> { using type = fx3; };  // three-part split
 
 // Arguments of one pass launch.
 struct PassArgs {

@@ -29,6 +29,18 @@ __global__ void k_split(const double2* __restrict__ pos, int64_t n, float4* __re
     }
 }
 
+__global__ void k_split3(const double2* __restrict__ pos, int64_t n, fx3* __restrict__ out, int* st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 p = pos[i];
+        if (!isfinite(p.x) || !isfinite(p.y))
+            set_status(st, ST_NONFINITE);
+        else if (!inside(p.x, p.y))
+            set_status(st, ST_OUTSIDE);
+        out[i] = split3(p.x, p.y);
+    }
+}
+
 __global__ void k_check(const double2* __restrict__ pos, int64_t n, int* st)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -110,7 +122,7 @@ __global__ void k_project(double2* __restrict__ pos, int64_t n, double radius, c
 tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad, double* energy,
                           double* local_e, cudaStream_t s)
 {
-    if (n < 0 || (n > 0 && !pos) || (prec != TC_FP64 && prec != TC_MIXED)) return TC_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !pos) || (prec != TC_FP64 && prec != TC_MIXED && prec != TC_F64X)) return TC_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(pos) & 15) || (grad && (reinterpret_cast<uintptr_t>(grad) & 15)) ||
         (energy && (reinterpret_cast<uintptr_t>(energy) & 7)) || (local_e && (reinterpret_cast<uintptr_t>(local_e) & 7)))
         return TC_ERR_INVALID_ARG;
@@ -140,6 +152,8 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
     int64_t G;
     if (prec == TC_MIXED)
         G = want_g ? pass_grid<PASS_MIXED, true, true>(P.W) : pass_grid<PASS_MIXED, true, false>(P.W);
+    else if (prec == TC_F64X)
+        G = want_g ? pass_grid<PASS_F64X, true, true>(P.W) : pass_grid<PASS_F64X, true, false>(P.W);
     else
         G = want_g ? pass_grid<PASS_F64, true, true>(P.W) : pass_grid<PASS_F64, true, false>(P.W);
     P.G = G;
@@ -148,6 +162,7 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
 
     Carver c;
     c.take<float4>(prec == TC_MIXED ? n : 0);
+    c.take<fx3>(prec == TC_F64X ? n : 0);
     c.take<double>(P.slots * n);
     c.take<double2>(want_g ? P.slots * n : 0);
     c.take<double>(nb);
@@ -156,6 +171,7 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
     c.base = static_cast<char*>(ws);
     c.off = kCounterBytes;
     float4* split = c.take<float4>(prec == TC_MIXED ? n : 0);
+    fx3* split3v = c.take<fx3>(prec == TC_F64X ? n : 0);
     double* part_e = c.take<double>(P.slots * n);
     double2* part_g = c.take<double2>(want_g ? P.slots * n : 0);
     double* block_e = c.take<double>(nb);
@@ -180,6 +196,12 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
         a.snap = split;
         e = want_g ? launch_pass<PASS_MIXED, true, true>(a, G, 0, 0, s)
                    : launch_pass<PASS_MIXED, true, false>(a, G, 0, 0, s);
+    } else if (prec == TC_F64X) {
+        k_split3<<<cb, 256, 0, s>>>(pos2, n, split3v, st);
+        a.rows = split3v;
+        a.snap = split3v;
+        e = want_g ? launch_pass<PASS_F64X, true, true>(a, G, 0, 0, s)
+                   : launch_pass<PASS_F64X, true, false>(a, G, 0, 0, s);
     } else {
         k_check<<<cb, 256, 0, s>>>(pos2, n, st);
         a.rows = pos2;

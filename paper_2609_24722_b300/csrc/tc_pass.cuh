@@ -244,6 +244,122 @@ template <int R> struct RowState<PASS_DMIX, R> {
     __device__ double bound(int r) const { return (double)bs[r]; }
 };
 
+// ---- float64-grade pair terms from float32 arithmetic ---------------------------
+// Positions come as three-part float32 splits (fx3): the hi and mid differences
+// are exact, so each separation is formed as a double-float (a, b) with
+// |b| <= 2^-23 |a| and error ~2^-69.  r^2, 1/r (a MUFU.RSQ seed y0 and one
+// correction step y = y0 + y0 (e/2 + 3e^2/8), e = 1 - r^2 y0^2 evaluated in
+// double-float), r^-3 = y^3 and dx r^-3 follow in double-float (TwoProd via
+// fma); each term is accurate to ~2^-46 relative.  Sums run in double-float
+// (TwoSum) over chunks of 16 sources and are folded into float64 row sums.
+__device__ __forceinline__ void df_acc(float& h, float& l, float vh, float vl)
+{
+    const float s = h + vh;
+    const float bb = s - h;
+    const float err = (h - (s - bb)) + (vh - bb);
+    h = s;
+    l += err + vl;
+}
+
+template <int R> struct RowState<PASS_F64X, R> {
+    float hx[R], hy[R], mx[R], my[R], lx[R], ly[R];
+    double es[R], gs_x[R], gs_y[R];
+
+    __device__ void load(const fx3* rows, int64_t base, int64_t rl0, int stride, int m)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t rl = rl0 + (int64_t)r * stride;
+            fx3 q = (rl < m) ? rows[base + rl] : far3(kFarRow32);
+            hx[r] = q.hm.x; hy[r] = q.hm.y; mx[r] = q.hm.z; my[r] = q.hm.w; lx[r] = q.lo.x; ly[r] = q.lo.y;
+            es[r] = gs_x[r] = gs_y[r] = 0.0;
+        }
+    }
+
+    // Sources go in chunks of kChunk: each chunk is summed in double-float and
+    // folded into the float64 row sums, so no double-float sum runs over more
+    // than kChunk terms (a double-float sum of n terms drifts by ~sqrt(n) 2^-48
+    // of its value; over a 256-source tile that reached 1e-13 of a row's energy).
+    static constexpr int kChunk = 16;
+
+    template <int T, bool SELF, bool WANT_E, bool WANT_G>
+    __device__ __forceinline__ void tile(const fx3* __restrict__ s, const int (&jself)[R], double escale)
+    {
+        static_assert(T % kChunk == 0, "whole chunks per tile");
+#pragma unroll 1
+        for (int j0 = 0; j0 < T; j0 += kChunk) {
+        float eh[R], el[R], xh[R], xl[R], yh[R], yl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) eh[r] = el[r] = xh[r] = xl[r] = yh[r] = yl[r] = 0.f;
+#pragma unroll 2
+        for (int j = j0; j < j0 + kChunk; ++j) {
+            const fx3 q = s[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                // separation (ax + bx, ay + by): exact hi and mid differences, Fast2Sum
+                const float dhx = hx[r] - q.hm.x, dmx = mx[r] - q.hm.z;
+                const float ax = dhx + dmx, bx = (dmx - (ax - dhx)) + (lx[r] - q.lo.x);
+                const float dhy = hy[r] - q.hm.y, dmy = my[r] - q.hm.w;
+                const float ay = dhy + dmy, by = (dmy - (ay - dhy)) + (ly[r] - q.lo.y);
+                // r^2 = R2 + R2l
+                const float p1 = ax * ax;
+                float e1 = fmaf(ax, ax, -p1);
+                e1 = fmaf(ax + ax, bx, e1);
+                e1 = fmaf(bx, bx, e1);
+                const float p2 = ay * ay;
+                float e2 = fmaf(ay, ay, -p2);
+                e2 = fmaf(ay + ay, by, e2);
+                e2 = fmaf(by, by, e2);
+                const float R2 = p1 + p2;
+                const float bb = R2 - p1;
+                const float R2l = ((p1 - (R2 - bb)) + (p2 - bb)) + (e1 + e2);
+                // 1/r = y0 + c
+                float y0 = rsqrt_mufu(R2);
+                if (SELF) y0 = (j == jself[r]) ? 0.f : y0;
+                const float th = y0 * y0, tl = fmaf(y0, y0, -th);
+                const float qh = R2 * th;
+                float ql = fmaf(R2, th, -qh);
+                ql = fmaf(R2, tl, ql);
+                ql = fmaf(R2l, th, ql);
+                const float ee = (1.f - qh) - ql;
+                const float c = y0 * (ee * fmaf(0.375f, ee, 0.5f));
+                if (WANT_E) df_acc(eh[r], el[r], y0, c);
+                if (WANT_G) {
+                    // r^-3 = y^3 = (th + sl) y
+                    float sl = fmaf(y0 + y0, c, tl);
+                    sl = fmaf(c, c, sl);
+                    const float uh = th * y0;
+                    float ul = fmaf(th, y0, -uh);
+                    ul = fmaf(th, c, ul);
+                    ul = fmaf(sl, y0, ul);
+                    const float gxh = ax * uh;
+                    float gxl = fmaf(ax, uh, -gxh);
+                    gxl = fmaf(ax, ul, gxl);
+                    gxl = fmaf(bx, uh, gxl);
+                    const float gyh = ay * uh;
+                    float gyl = fmaf(ay, uh, -gyh);
+                    gyl = fmaf(ay, ul, gyl);
+                    gyl = fmaf(by, uh, gyl);
+                    df_acc(xh[r], xl[r], gxh, gxl);
+                    df_acc(yh[r], yl[r], gyh, gyl);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (WANT_E) es[r] += ((double)eh[r] + (double)el[r]) * escale;
+            if (WANT_G) {
+                gs_x[r] -= (double)xh[r] + (double)xl[r];
+                gs_y[r] -= (double)yh[r] + (double)yl[r];
+            }
+        }
+        }
+    }
+
+    __device__ double e(int r) const { return es[r]; }
+    __device__ double2 g(int r) const { return make_double2(gs_x[r], gs_y[r]); }
+};
+
 // Source entry t*T + tid of a problem's tile list, with masking and padding.
 template <int KIND, int T>
 __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a, const Prob& p, int t, int tid)
@@ -261,6 +377,8 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
         } else if constexpr (KIND == PASS_DMIX) {
             return make_f8(ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f),
                            0.f, 0.f);
+        } else if constexpr (KIND == PASS_F64X) {
+            return ok ? static_cast<const fx3*>(a.snap)[p.snap_b + j] : far3(kFar32);
         } else if constexpr (KIND == PASS_F64) {
             return ok ? static_cast<const double2*>(a.snap)[p.snap_b + j] : make_double2(kFar64, kFar64);
         } else {
@@ -275,6 +393,8 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
         } else if constexpr (KIND == PASS_DMIX) {
             return ok ? static_cast<const f8*>(a.rows)[p.row_base + j]
                       : make_f8(make_float4(kFar32, kFar32, 0.f, 0.f), 0.f, 0.f);
+        } else if constexpr (KIND == PASS_F64X) {
+            return ok ? static_cast<const fx3*>(a.rows)[p.row_base + j] : far3(kFar32);
         } else if constexpr (KIND == PASS_F64) {
             return ok ? static_cast<const double2*>(a.rows)[p.row_base + j] : make_double2(kFar64, kFar64);
         } else {

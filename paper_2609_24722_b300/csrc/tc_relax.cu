@@ -33,6 +33,7 @@ struct RelaxDev {
     int32_t* gidx;         // per row: charge index
     double2* x;            // per row: position (float64 master copy)
     float4* xs;            // per row: hi/lo split of x
+    fx3* x3;               // per row: three-part split of x (float64-grade float32 pass), nullable
     double2* g;            // per row: reduced dE/dx
     double2* xp;           // per row: previous x (BB) / previous z (L-BFGS)
     double2* gp;           // per row: previous g (BB) / current dE/dz (L-BFGS)
@@ -189,6 +190,7 @@ __global__ void k_rows_init(RelaxDev d, int64_t n, double radius, int lbfgs)
         }
         if (d.x) d.x[rr] = x;
         if (d.xs) d.xs[rr] = split4(x.x, x.y);
+        if (d.x3) d.x3[rr] = split3(x.x, x.y);
     }
 }
 
@@ -214,6 +216,12 @@ __global__ void k_split_pos(const double2* __restrict__ pos, int64_t n, float4* 
             set_status(st, ST_OUTSIDE);
         out[i] = split4(p.x, p.y);
     }
+}
+
+__global__ void k_split3_pos(const double2* __restrict__ pos, int64_t n, fx3* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = split3(pos[i].x, pos[i].y);
 }
 
 // ------------------------------------------------------------ updates ---
@@ -277,6 +285,7 @@ __global__ void __launch_bounds__(kUpd) k_update_gdbb(RelaxDev d, const double2*
         xn = project1(xn, sp.radius, pinned);
         d.x[row] = xn;
         d.xs[row] = split4(xn.x, xn.y);
+        if (d.x3) d.x3[row] = split3(xn.x, xn.y);
     }
     if (threadIdx.x == 0) {
         d.steps[s] = k + 1;
@@ -456,6 +465,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
         double2 xn = z_to_x(zn, sp.radius, pinned);
         d.x[row] = xn;
         d.xs[row] = split4(xn.x, xn.y);
+        if (d.x3) d.x3[row] = split3(xn.x, xn.y);
     }
     if (threadIdx.x == 0) {
         d.steps[s] = k + 1;
@@ -755,6 +765,7 @@ __global__ void __launch_bounds__(kUpd) k_lb_step(RelaxDev d, LbArgs la, StepPar
         const double2 xn = z_to_x(zn, sp.radius, pinned);
         d.x[row] = xn;
         d.xs[row] = split4(xn.x, xn.y);
+        if (d.x3) d.x3[row] = split3(xn.x, xn.y);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) d.steps[la.s] = d.steps[la.s] + 1;
 }
@@ -925,7 +936,8 @@ __global__ void k_results(RelaxDev d, tc_subdomain_result* out, int mode_instanc
 static tc_status check_params(const tc_relax_params* prm)
 {
     if (!prm) return TC_ERR_INVALID_ARG;
-    if (prm->precision != TC_FP64 && prm->precision != TC_MIXED) return TC_ERR_INVALID_ARG;
+    if (prm->precision != TC_FP64 && prm->precision != TC_MIXED && prm->precision != TC_F64X) return TC_ERR_INVALID_ARG;
+    if (prm->polish_precision != TC_FP64 && prm->polish_precision != TC_F64X) return TC_ERR_INVALID_ARG;
     if (prm->optimizer < TC_OPT_GD || prm->optimizer > TC_OPT_LBFGS) return TC_ERR_INVALID_ARG;
     if (prm->n_steps < 0 || prm->polish_steps < 0) return TC_ERR_INVALID_ARG;
     if (prm->optimizer == TC_OPT_LBFGS && (prm->memory < 1 || prm->memory > kMaxMem)) return TC_ERR_INVALID_ARG;
@@ -971,7 +983,7 @@ static double elapsed(cudaEvent_t a, cudaEvent_t b)
 }
 
 static_assert(sizeof(tc_subdomain_result) == 32, "tc_subdomain_result layout");
-static_assert(sizeof(tc_relax_params) == 88, "tc_relax_params layout");
+static_assert(sizeof(tc_relax_params) == 96, "tc_relax_params layout");
 static_assert(sizeof(tc_relax_profile) == 56, "tc_relax_profile layout");
 
 // One relaxation phase: `steps` x (pass, update), captured into a CUDA graph.
@@ -1144,8 +1156,12 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int prec = prm->precision;
     const bool lbfgs = prm->optimizer == TC_OPT_LBFGS;
     const int mem = lbfgs ? prm->memory : 0;
-    const int64_t G_bulk = prec == TC_MIXED ? pass_grid<PASS_MIXED, false, true>(P.W) : pass_grid<PASS_F64, false, true>(P.W);
-    const int64_t G_f64 = pass_grid<PASS_F64, false, true>(P.W);
+    const int64_t G_bulk = prec == TC_MIXED  ? pass_grid<PASS_MIXED, false, true>(P.W)
+                           : prec == TC_F64X ? pass_grid<PASS_F64X, false, true>(P.W)
+                                             : pass_grid<PASS_F64, false, true>(P.W);
+    const bool polish_x = prm->polish_precision == TC_F64X;
+    const int64_t G_f64 = polish_x ? pass_grid<PASS_F64X, false, true>(P.W) : pass_grid<PASS_F64, false, true>(P.W);
+    const bool use_x = prec == TC_F64X || (polish_x && prm->polish_steps > 0);
     const int64_t G_e = pass_grid<PASS_F64, true, false>(P.W);
     const int64_t G_d = pass_grid<PASS_DELTA, false, false>(P.W);
     int64_t slots = 1;
@@ -1169,6 +1185,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
             if (P.prob[k].m > kLargeRows) large.ids.push_back(k);
 
     Carver c;
+    fx3* snap3 = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
         probd = cv.take<Prob>(n_sub);
@@ -1176,6 +1193,8 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         d.gidx = cv.take<int32_t>(M);
         d.x = cv.take<double2>(M);
         d.xs = cv.take<float4>(M);
+        d.x3 = use_x ? cv.take<fx3>(M) : nullptr;
+        snap3 = cv.take<fx3>(use_x && !inst ? n : 0);
         d.g = cv.take<double2>(M);
         d.xp = cv.take<double2>(M);
         d.gp = cv.take<double2>(M);
@@ -1253,6 +1272,10 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8L * sm_count()));
         k_split_pos<<<nb, 256, 0, s>>>(reinterpret_cast<const double2*>(pos), n, snap_split, st);
         ++launches;
+        if (use_x) {
+            k_split3_pos<<<nb, 256, 0, s>>>(reinterpret_cast<const double2*>(pos), n, snap3);
+            ++launches;
+        }
     }
     if (prof) cudaEventRecord(ev_b, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "launch");
@@ -1284,6 +1307,10 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         a.rows = d.xs;
         a.snap = snap_split;
         rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
+    } else if (prec == TC_F64X) {
+        a.rows = d.x3;
+        a.snap = snap3;
+        rs = run_phase<PASS_F64X>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
     } else {
         a.rows = d.x;
         a.snap = pos;
@@ -1295,9 +1322,15 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         if (cudaError_t e_ = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s); e_ != cudaSuccess) return cuda_fail(e_, "cudaMemcpyAsync");
         StepParams sp2 = sp;
         sp2.gtol = prm->polish_gtol;
-        a.rows = d.x;
-        a.snap = pos;
-        rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large);
+        if (polish_x) {
+            a.rows = d.x3;
+            a.snap = snap3;
+            rs = run_phase<PASS_F64X>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large);
+        } else {
+            a.rows = d.x;
+            a.snap = pos;
+            rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large);
+        }
         if (rs != TC_OK) return rs;
     }
     a.active = nullptr;

@@ -23,16 +23,16 @@ def test_exports_every_declared_function(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # tc_relax_params: 4 int32, 6 double, 2 int32, 1 double, 2 int32 -> 88 bytes
-    assert C.sizeof(L.RelaxParams) == 88
+    # tc_relax_params: 4 int32, 6 double, 2 int32, 1 double, 3 int32 (+4 padding) -> 96 bytes
+    assert C.sizeof(L.RelaxParams) == 96 and L.RelaxParams.polish_precision.offset == 88
     assert L.RelaxParams.step0.offset == 16 and L.RelaxParams.polish_steps.offset == 64
     assert L.RelaxParams.want_energy.offset == 80
     assert L.RESULT_BYTES == 32
     assert C.sizeof(L.RelaxProfile) == 56
     # tc_zone_params: 4 double, 4 int32; tc_cycle_params: zone, relax, 2 int32
     assert C.sizeof(L.ZoneParams) == 48 and L.ZoneParams.m_min.offset == 32
-    assert C.sizeof(L.CycleParams) == 160 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 136
-    assert L.CycleParams.sigma0.offset == 144
+    assert C.sizeof(L.CycleParams) == 168 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 144
+    assert L.CycleParams.sigma0.offset == 152
 
 
 def test_status_strings(lib):
