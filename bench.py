@@ -2,9 +2,8 @@
 """Benchmark: Coulomb pair interactions per second at N = 100 000 (one adaptive-cycle step).
 
 One step is one pass of the whole hot path over one batch of synthetic input:
-  1. float64-grade local energies e_i of all N charges (Sec. II C step 1:
-     N(N-1) ordered pair interactions; the fp64x pass: double-float terms on
-     the float32 pipes, held to the float64 tolerances),
+  1. float64 local energies e_i of all N charges (Sec. II C step 1: N(N-1)
+     ordered pair interactions),
   2. 256 subdomains (m ~ U{200..5000}, the m nearest charges to a centre)
      relaxed together against all N for 200 mixed-precision projected
      Barzilai-Borwein steps (Sec. II C step 4, Sec. II E: m(N-1) pair
@@ -39,10 +38,10 @@ N = 100_000
 N_SUB = 256
 M_LO, M_HI = 200, 5000
 RELAX_STEPS = 200
-LOCAL_PREC = "fp64x"  # float64-grade local energies (double-float on the float32 pipes)
+LOCAL_PREC = "fp64"  # the total energy needs 12+ digits: float64
 METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
 UNIT = "pair-interactions/s"
-WORKLOAD = ("adaptive-cycle step at N=1e5: fp64x (float64-grade) local energies of all charges + 256 subdomains "
+WORKLOAD = ("adaptive-cycle step at N=1e5: fp64 local energies of all charges + 256 subdomains "
             "(m~U[200,5000], nearest charges to a centre) x 200 mixed BB steps against all N + fp64 "
             "sequential accept; triangular-lattice background mapped to the arcsine density, 0.5% jitter, "
             "charges stored in Hilbert-curve order")
@@ -78,6 +77,7 @@ def run_case(args):
     dev = torch.device("cuda", 0)
     if args.case == "full-relax":
         print(json.dumps(run_full_relax(dev, n=args.n)))
+        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=1000, polish_precision="fp64x")))
         return
     if args.case == "cycle":
         # cycle time against N at a fixed number of subdomain optimisations (Sec. II E)
@@ -241,9 +241,10 @@ def cpu_baseline(pos, idx, off, seconds: float = 12.0) -> dict:
 
 
 def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
-                  polish: int = 50, fp64_steps: int = 10):
+                  polish: int = 20, fp64_steps: int = 10, polish_precision: str = "fp64"):
     """Config C5: 512 independent instances (N_k ~ U{100..5000}, arcsine init each), relaxed in one
-    batched call per round (mixed L-BFGS, memory 8, then a float64-grade fp64x polish), 3 perturbation restarts
+    batched call per round (mixed L-BFGS, memory 8, then a float64 polish; polish_precision="fp64x"
+    runs it as float64-grade double-float on the float32 pipes), 3 perturbation restarts
     (Gaussian kicks of 0.05 x the instance's lattice spacing) keeping each instance's best energy;
     then the same instances with float64 pair terms for a few steps (throughput side by side)."""
     import numpy as np
@@ -262,9 +263,10 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
     best_e = np.full(n_inst, np.inf)
     kw = dict(precision="mixed", optimizer="lbfgs", n_steps=steps, memory=8, step0=1e-5,
               maxstep=0.1 * float(h.min()), polish_steps=polish, polish_gtol=0.0, accept=False,
-              polish_precision="fp64x",
+              polish_precision=polish_precision,
               want_energy=True)
     ms_total, pairs_total, launches = 0.0, 0, 0
+    ms_rounds = []
     for r in range(rounds):
         start = pos_np if r == 0 else synth.jitter_inside(best, sig, seed + 100 + r)
         p = torch.tensor(start, device=dev)
@@ -276,6 +278,7 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
         torch.cuda.synchronize()
         tc.sync_status()
         ms_total += a.elapsed_time(b)
+        ms_rounds.append(a.elapsed_time(b))
         pairs_total += int((sizes * (sizes - 1)).sum()) * (steps + polish)
         e = res.energy.cpu().numpy()
         x = p.cpu().numpy()
@@ -286,6 +289,15 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
     # the float64-polished energies against the oracle's evaluation of the same configurations
     check = [0, int(np.argmax(sizes)), n_inst - 1]
     parity = max(abs(best_e[k] - oracle.energy(best[off[k]:off[k + 1]])) / best_e[k] for k in check)
+    # the first round again with the step loop launched directly instead of as a CUDA graph
+    p = torch.tensor(pos_np, device=dev)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    tc.relax_subdomains(p, world=world, **{**kw, "profile": True})
+    b.record()
+    torch.cuda.synchronize()
+    ms_nograph = a.elapsed_time(b)
     # float64 pair terms, same instances, a few steps
     p = torch.tensor(pos_np, device=dev)
     torch.cuda.synchronize()
@@ -297,17 +309,20 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
     ms64 = a.elapsed_time(b)
     pairs64 = int((sizes * (sizes - 1)).sum()) * fp64_steps
     return {"workload": f"{n_inst} instances, N_k~U[100,5000] (sum {int(sizes.sum())}), arcsine init, "
-                        f"{rounds - 1} kick restarts, mixed L-BFGS(8) {steps} steps + fp64x polish {polish}",
+                        f"{rounds - 1} kick restarts, mixed L-BFGS(8) {steps} steps + {polish_precision} polish {polish}",
             "relax_time_s": ms_total / 1e3, "pairs_per_s_mixed_with_polish": pairs_total / (ms_total / 1e3),
+            "round0_s_graph": ms_rounds[0] / 1e3, "round0_s_no_graph": ms_nograph / 1e3,
             "pairs_per_s_fp64": pairs64 / (ms64 / 1e3), "fp64_steps": fp64_steps,
             "best_energy_sum": float(best_e.sum()),
             "fp64_energy_vs_oracle_max_rel": parity}
 
 
-def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 1000) -> dict:
+def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 200,
+                   polish_precision: str = "fp64") -> dict:
     """Config C4: one configuration of N = 1e5 charges (arcsine init, Hilbert order) relaxed by
     mixed-precision L-BFGS(8) on the wall map until the RMS of dE/dz falls below 1e-4 x the initial
-    mean force, then float64-grade (fp64x) L-BFGS to 1e-8 x that (step caps max_mixed / max_polish)."""
+    mean force, then float64 L-BFGS (or the float64-grade fp64x pass) to 1e-8 x that (step caps
+    max_mixed / max_polish)."""
     import numpy as np
     import torch
 
@@ -328,13 +343,13 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
                              step0=1e-6, maxstep=0.1 * h, gtol=1e-4 * f_ref, accept=False)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    r2 = tc.relax_subdomains(p, world=world, precision="fp64x", optimizer="lbfgs", n_steps=max_polish, memory=8,
+    r2 = tc.relax_subdomains(p, world=world, precision=polish_precision, optimizer="lbfgs", n_steps=max_polish, memory=8,
                              step0=1e-6, maxstep=0.1 * h, gtol=1e-8 * f_ref, accept=False, want_energy=True)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     tc.sync_status()
     e = r2.energy[0].item()
-    return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, fp64x polish to 1e-8 "
+    return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, {polish_precision} polish to 1e-8 "
                         f"(caps {max_mixed} / {max_polish} steps)",
             "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
             "mixed_steps": int(r1.steps[0]), "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
@@ -453,10 +468,17 @@ def main():
     torch.cuda.set_device(dev)
     tc_build.build()
 
-    # pick the launch shape of the mixed pass on this GPU (timed, results identical across shapes)
+    # pick the launch shape of the mixed pass on this GPU (timed, results identical across shapes);
+    # --config fixes it instead (profiler runs)
     from paper_2609_24722_b300 import autotune
 
-    tuned = autotune.tune(n=N, nsub=64, reps=2, seed=rank, cache=None)
+    if args.config is not None:
+        from paper_2609_24722_b300 import _lib
+
+        _lib.check(_lib.lib().tc_set_pass_config(_lib.TC_MIXED, args.config), "tc_set_pass_config")
+        tuned = {"best": args.config, "shapes": []}
+    else:
+        tuned = autotune.tune(n=N, nsub=64, reps=2, seed=rank, cache=None)
 
     pos_np, idx_np, off_np = make_inputs(rank)
     pos0 = torch.tensor(pos_np, device=dev)
@@ -552,6 +574,10 @@ def main():
     ms_f64 = time_allpairs("fp64", 3)
     ms_f64x = time_allpairs("fp64x", 3)
     c5 = run_instances(dev) if not args.no_instances else None
+    if c5 is not None:
+        c5x = run_instances(dev, polish=50, polish_precision="fp64x")
+        c5["fp64x_polish_variant"] = {k: c5x[k] for k in ("workload", "relax_time_s", "pairs_per_s_mixed_with_polish",
+                                                            "best_energy_sum", "fp64_energy_vs_oracle_max_rel")}
     cyc = run_cycle(dev) if not args.no_instances else None
     pipes = tc.probe_pipes()
     tc.sync_status()
@@ -577,7 +603,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulation (mixed); float64-grade double-float local energies (fp64x); f64 accept",
+        "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulation (mixed); f64 energies/accept",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "n_sub": N_SUB, "m_range": [M_LO, M_HI],
                    "relax_steps": RELAX_STEPS, "optimizer": "projected BB, step0 1e-4/N, alpha_max 1e-3/N",
