@@ -39,6 +39,10 @@ N_SUB = 256
 M_LO, M_HI = 200, 5000
 RELAX_STEPS = 200
 LOCAL_PREC = "fp64"  # the total energy needs 12+ digits: float64
+# DRAM bytes of one relaxation-pass launch of this workload, from an ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/relax_pass_traffic_n1e5.md); it must be
+# retaken (or set to None) whenever k_pass_mixed changes.
+RELAX_PASS_DRAM_BYTES = 16.3e6
 METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
 UNIT = "pair-interactions/s"
 WORKLOAD = ("adaptive-cycle step at N=1e5: fp64 local energies of all charges + 256 subdomains "
@@ -589,7 +593,8 @@ def main():
     achieved = prof["pass_pairs"] / (pass_ms / 1e3)
     peak = min(pipes["ffma_per_s"] / 8.0, pipes["mufu_per_s"])
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": RELAX_PASS_DRAM_BYTES,
+                "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)",
                 "kernel": "k_pass<mixed, grad> (relaxation pair pass)",
                 "peak_source": "measured: tc_probe_pipes FFMA lane-ops/s / 8 and MUFU.RSQ/s, this run",
                 "frac_of_pairmix_ceiling": achieved / pipes["pairmix_per_s"],

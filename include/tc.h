@@ -174,6 +174,11 @@ typedef struct {
     int32_t profile;     /* 1: launch the step loop directly (no CUDA graph) and time each
                             launch with CUDA events (see tc_relax_last_profile) */
     int32_t polish_precision; /* TC_FP64 (0, the default) or TC_F64X for the polish steps */
+    int32_t line_search; /* L-BFGS only: at most this many Armijo halvings per step, 0..30
+                            (0: none).  A trial z + alpha d is kept once E(new) - E(old)
+                            <= 1e-4 alpha (dE/dz . d), the energy change summed as pair
+                            differences (float32 difference form in a TC_MIXED phase,
+                            float64 otherwise); else alpha halves; the last trial is kept */
 } tc_relax_params;
 
 typedef struct {

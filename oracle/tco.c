@@ -539,13 +539,44 @@ static void grad_z(const double* z, const double* g, int64_t n, double sigma, co
  *   the pair s = z_new - z, y = gz_new - gz is kept iff s^T y > 1e-12 |s||y|
  *   (the oldest drops out beyond M).
  * pos (in/out, 2n): x of the final z.  Reports iterations and final RMS |gz|. */
+int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                 double step0, double maxstep, double sigma, const unsigned char* flags,
+                 int64_t max_halvings, int64_t* iters_out, double* rms_out);
+
+/* Energy change E(xn) - E(x) of moving every charge from x to xn, summed as
+ * pair differences (compensated), not as a difference of totals. */
+static double instance_delta(const double* x, const double* xn, int64_t n)
+{
+    acc_t a = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            acc_add(&a, inv_dist(xn[2 * i], xn[2 * i + 1], xn[2 * j], xn[2 * j + 1]) -
+                            inv_dist(x[2 * i], x[2 * i + 1], x[2 * j], x[2 * j + 1]));
+    return acc_get(&a);
+}
+
 int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
               double step0, double maxstep, double sigma, const unsigned char* flags,
               int64_t* iters_out, double* rms_out)
 {
-    if (n < 0 || memory < 1 || max_iter < 0 || (n > 0 && !pos) || !(sigma > 0.0)) return TCO_ERR_INVALID_ARG;
+    return tco_lbfgs_ls(pos, n, memory, max_iter, gtol, step0, maxstep, sigma, flags, 0, iters_out, rms_out);
+}
+
+/* tco_lbfgs with an Armijo backtracking line search (max_halvings > 0): the
+ * trial z + alpha d (alpha from the max-step cap) is kept once
+ *     E(x(z + alpha d)) - E(x(z)) <= 1e-4 alpha (dE/dz . d),
+ * the energy change summed as pair differences; otherwise alpha is halved, at
+ * most max_halvings times, and the last trial is taken.  max_halvings = 0 is
+ * the plain iteration. */
+int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                 double step0, double maxstep, double sigma, const unsigned char* flags,
+                 int64_t max_halvings, int64_t* iters_out, double* rms_out)
+{
+    if (n < 0 || memory < 1 || max_iter < 0 || max_halvings < 0 || (n > 0 && !pos) || !(sigma > 0.0))
+        return TCO_ERR_INVALID_ARG;
     int64_t L = 2 * n;
     size_t sz = sizeof(double) * (size_t)(L > 0 ? L : 1);
+    double* xk = (double*)malloc(sz);
     double* z = (double*)malloc(sz);
     double* zn = (double*)malloc(sz);
     double* g = (double*)malloc(sz);
@@ -556,8 +587,8 @@ int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double g
     double* Y = (double*)malloc(sz * (size_t)memory);
     double* rho = (double*)malloc(sizeof(double) * (size_t)memory);
     double* al = (double*)malloc(sizeof(double) * (size_t)memory);
-    if (!z || !zn || !g || !gz || !gzn || !d || !S || !Y || !rho || !al) {
-        free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
+    if (!xk || !z || !zn || !g || !gz || !gzn || !d || !S || !Y || !rho || !al) {
+        free(xk); free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
         return TCO_ERR_NO_MEMORY;
     }
     memset(z, 0, sz);
@@ -603,7 +634,18 @@ int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double g
         }
         double alpha = (dmax > maxstep) ? maxstep / dmax : 1.0;
         for (int64_t i = 0; i < L; ++i) zn[i] = z[i] + alpha * d[i];
-        z_to_x(zn, n, sigma, flags, pos);
+        if (max_halvings > 0) {
+            memcpy(xk, pos, sz);
+            const double gd = dot(gz, d, L);
+            for (int64_t h = 0;; ++h) {
+                z_to_x(zn, n, sigma, flags, pos);
+                if (instance_delta(xk, pos, n) <= 1e-4 * alpha * gd || h == max_halvings) break;
+                alpha *= 0.5;
+                for (int64_t i = 0; i < L; ++i) zn[i] = z[i] + alpha * d[i];
+            }
+        } else {
+            z_to_x(zn, n, sigma, flags, pos);
+        }
         st = tco_grad(pos, n, g);
         if (st) break;
         grad_z(zn, g, n, sigma, flags, gzn);
@@ -631,7 +673,7 @@ int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double g
     }
     if (iters_out) *iters_out = it;
     if (rms_out) *rms_out = rms;
-    free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
+    free(xk); free(z); free(zn); free(g); free(gz); free(gzn); free(d); free(S); free(Y); free(rho); free(al);
     return st;
 }
 

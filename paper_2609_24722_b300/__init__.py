@@ -146,7 +146,7 @@ class RelaxResult:
 def relax_subdomains(pos, idx=None, offsets=None, world=None, flags=None, *, precision="mixed", optimizer="bb",
                      n_steps=200, memory=8, step0=1e-9, alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0,
                      radius=1.0, polish_steps=0, polish_gtol=0.0, accept=True, want_energy=False,
-                     profile=False, polish_precision="fp64") -> RelaxResult:
+                     profile=False, polish_precision="fp64", line_search=0) -> RelaxResult:
     """Relax subdomains (idx/offsets given) or independent instances (idx None, world given)."""
     _pos(pos)
     if idx is not None:
@@ -159,7 +159,7 @@ def relax_subdomains(pos, idx=None, offsets=None, world=None, flags=None, *, pre
     if world is not None and (world.dtype != torch.int64 or not world.is_cuda or not world.is_contiguous()):
         raise TypeError("world must be a contiguous CUDA int64 tensor of shape (n_sub, 2)")
     prm = _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol, radius,
-                        polish_steps, polish_gtol, accept, want_energy, profile, polish_precision)
+                        polish_steps, polish_gtol, accept, want_energy, profile, polish_precision, line_search)
     raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
     L.check(L.lib().tc_relax_subdomains(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub, _p(world), _p(flags),
                                         C.byref(prm), _p(raw), _stream()), "tc_relax_subdomains")
@@ -167,13 +167,14 @@ def relax_subdomains(pos, idx=None, offsets=None, world=None, flags=None, *, pre
 
 
 def _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol, radius,
-                  polish_steps, polish_gtol, accept, want_energy, profile, polish_precision="fp64") -> RelaxParams:
+                  polish_steps, polish_gtol, accept, want_energy, profile, polish_precision="fp64",
+                  line_search=0) -> RelaxParams:
     return RelaxParams(precision=_prec(precision), optimizer=_OPT[optimizer] if isinstance(optimizer, str) else optimizer,
                        n_steps=int(n_steps), memory=int(memory), step0=float(step0), alpha_min=float(alpha_min),
                        alpha_max=float(alpha_max), maxstep=float(maxstep), gtol=float(gtol), radius=float(radius),
                        polish_steps=int(polish_steps), accept=int(bool(accept)), polish_gtol=float(polish_gtol),
                        want_energy=int(bool(want_energy)), profile=int(bool(profile)),
-                       polish_precision=_prec(polish_precision))
+                       polish_precision=_prec(polish_precision), line_search=int(line_search))
 
 
 def _results(raw: torch.Tensor, n_sub: int) -> RelaxResult:

@@ -55,6 +55,7 @@ class RelaxParams(C.Structure):
         ("want_energy", C.c_int32),
         ("profile", C.c_int32),
         ("polish_precision", C.c_int32),
+        ("line_search", C.c_int32),
     ]
 
 

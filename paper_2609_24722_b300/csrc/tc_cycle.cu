@@ -371,6 +371,7 @@ tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local
                                const tc_zone_params* prm, int32_t n_sub, const double* uniforms, int32_t* idx,
                                int64_t* offsets, double* centres, double* stats, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_select_subdomains");
     tc_status err = check_zone(prm);
     if (err != TC_OK) return err;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -392,6 +393,7 @@ tc_status tc_select_subdomains(const double* pos, int64_t n, const double* local
 tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_params* prm, int32_t n_sub,
                    const double* uniforms, tc_subdomain_result* out, double* energy, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_cycle");
     if (!prm) return TC_ERR_INVALID_ARG;
     tc_status err = check_zone(&prm->zone);
     if (err != TC_OK) return err;
@@ -464,6 +466,7 @@ int64_t tc_boundary_count(int64_t n)
 
 tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uint8_t* flags, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_border_split");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (n < 0 || n > INT32_MAX || n_b < 0 || n_b > n || !(sigma > 0.0) || !(sigma <= 1.0) ||
         (n > 0 && (!pos || !flags)) || misaligned(pos, 16))

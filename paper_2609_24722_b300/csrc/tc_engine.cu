@@ -227,18 +227,21 @@ extern "C" {
 tc_status tc_energy(const double* pos, int64_t n, tc_precision prec, double* energy, double* local_e,
                     tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_energy");
     if (!energy) return TC_ERR_INVALID_ARG;
     return tc::allpairs(pos, n, prec, nullptr, energy, local_e, reinterpret_cast<cudaStream_t>(stream));
 }
 
 tc_status tc_grad(const double* pos, int64_t n, tc_precision prec, double* grad, double* energy, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_grad");
     if (!grad) return TC_ERR_INVALID_ARG;
     return tc::allpairs(pos, n, prec, grad, energy, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
 tc_status tc_project_disk(double* pos, int64_t n, double radius, const uint8_t* flags, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_project_disk");
     if (n < 0 || (n > 0 && !pos) || !(radius > 0.0) || (reinterpret_cast<uintptr_t>(pos) & 15))
         return TC_ERR_INVALID_ARG;
     if (n == 0) return TC_OK;

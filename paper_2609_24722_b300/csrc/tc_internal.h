@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/tc.h"
 
@@ -36,6 +37,15 @@ inline tc_status cuda_status(cudaError_t e, const char* where = "CUDA call") { r
 void set_last_error(const char* msg);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// NVTX range around one public call (visible to ncu --nvtx and other
+// profilers; costs nothing when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // The first kCounterBytes of every workspace hold zero-initialised counters
 // for last-block reductions (each user resets its counter to zero); the rest

@@ -97,6 +97,7 @@ __global__ void k_noalloc_finish(Prob p, int64_t W, int64_t G, const double* __r
 static tc_status energy_noalloc(const double* pos, int64_t n, tc_precision prec, double* energy, double* local_e,
                                 cudaStream_t s)
 {
+    tc::NvtxRange nvtx_range("tc_energy_noalloc");
     if (n < 0 || (n > 0 && !pos) || !energy || (prec != TC_FP64 && prec != TC_MIXED)) return TC_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(pos) & 15) || (reinterpret_cast<uintptr_t>(energy) & 7) ||
         (reinterpret_cast<uintptr_t>(local_e) & 7))

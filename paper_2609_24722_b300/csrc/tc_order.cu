@@ -250,6 +250,7 @@ extern "C" {
 tc_status tc_voronoi_order(const double* pos, int64_t n, int32_t* z, double* psi6, int32_t* nbr, int32_t max_nbr,
                            double* summary, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_voronoi_order");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (n < 0 || n > INT32_MAX || (n > 0 && (!pos || !z || !psi6)) || (nbr && max_nbr < 1) ||
         (reinterpret_cast<uintptr_t>(pos) & 15) || (reinterpret_cast<uintptr_t>(psi6) & 15) ||

@@ -14,67 +14,9 @@
 
 namespace tc {
 
-// Rows of one thread and their accumulators, per pass flavour.
+// Rows of one thread and their accumulators, per pass flavour (the float32
+// pass has its own kernel, tc_pass_mixed.cuh).
 template <int KIND, int R> struct RowState;
-
-// ---- mixed: float32 pair terms from hi/lo-split positions -------------------
-template <int R> struct RowState<PASS_MIXED, R> {
-    float xh[R], yh[R], xl[R], yl[R];
-    float eh[R], el[R], gxh[R], gxl[R], gyh[R], gyl[R];
-
-    __device__ void load(const float4* rows, int64_t base, int64_t rl0, int stride, int m)
-    {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            int64_t rl = rl0 + (int64_t)r * stride;
-            float4 q = (rl < m) ? rows[base + rl] : make_float4(kFarRow32, kFarRow32, 0.f, 0.f);
-            xh[r] = q.x; yh[r] = q.y; xl[r] = q.z; yl[r] = q.w;
-            eh[r] = el[r] = gxh[r] = gxl[r] = gyh[r] = gyl[r] = 0.f;
-        }
-    }
-
-    // One tile: s[0..T) against the R rows; jself[r] is the tile position of
-    // row r's own charge (only checked when SELF).
-    template <int T, bool SELF, bool WANT_E, bool WANT_G>
-    __device__ __forceinline__ void tile(const float4* __restrict__ s, const int (&jself)[R], float escale)
-    {
-        float et[R], gxt[R], gyt[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) et[r] = gxt[r] = gyt[r] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < T; ++j) {
-            const float4 q = s[j];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float dx = (xh[r] - q.x) + (xl[r] - q.z);
-                float dy = (yh[r] - q.y) + (yl[r] - q.w);
-                float r2 = fmaf(dx, dx, dy * dy);
-                float inv = rsqrt_mufu(r2);
-                if (SELF) inv = (j == jself[r]) ? 0.f : inv;
-                if (WANT_E) et[r] += inv;
-                if (WANT_G) {
-                    float inv3 = inv * inv * inv;
-                    gxt[r] = fmaf(-dx, inv3, gxt[r]);
-                    gyt[r] = fmaf(-dy, inv3, gyt[r]);
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (WANT_E) df_add(eh[r], el[r], et[r] * escale);
-            if (WANT_G) {
-                df_add(gxh[r], gxl[r], gxt[r]);
-                df_add(gyh[r], gyl[r], gyt[r]);
-            }
-        }
-    }
-
-    __device__ double e(int r) const { return (double)eh[r] + (double)el[r]; }
-    __device__ double2 g(int r) const
-    {
-        return make_double2((double)gxh[r] + (double)gxl[r], (double)gyh[r] + (double)gyl[r]);
-    }
-};
 
 // ---- float64 pair terms --------------------------------------------------------
 template <int R> struct RowState<PASS_F64, R> {
@@ -372,9 +314,7 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
             uint32_t w = a.mask[p.mask_off + (j >> 5)];
             ok = ((w >> (j & 31)) & 1u) == 0u;
         }
-        if constexpr (KIND == PASS_MIXED) {
-            return ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
-        } else if constexpr (KIND == PASS_DMIX) {
+        if constexpr (KIND == PASS_DMIX) {
             return make_f8(ok ? static_cast<const float4*>(a.snap)[p.snap_b + j] : make_float4(kFar32, kFar32, 0.f, 0.f),
                            0.f, 0.f);
         } else if constexpr (KIND == PASS_F64X) {
@@ -388,9 +328,7 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
     } else {
         int64_t j = (int64_t)(t - p.n_t_snap) * T + tid;
         bool ok = j < p.m;
-        if constexpr (KIND == PASS_MIXED) {
-            return ok ? static_cast<const float4*>(a.rows)[p.row_base + j] : make_float4(kFar32, kFar32, 0.f, 0.f);
-        } else if constexpr (KIND == PASS_DMIX) {
+        if constexpr (KIND == PASS_DMIX) {
             return ok ? static_cast<const f8*>(a.rows)[p.row_base + j]
                       : make_f8(make_float4(kFar32, kFar32, 0.f, 0.f), 0.f, 0.f);
         } else if constexpr (KIND == PASS_F64X) {

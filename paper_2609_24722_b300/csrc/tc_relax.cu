@@ -42,6 +42,11 @@ struct RelaxDev {
     double2* Sh;           // [mem][M] L-BFGS s history
     double2* Yh;           // [mem][M] L-BFGS y history
     d4* rows4;             // per row: (old, new) for the float64 energy change
+    f8* rows8;             // per row: old split + move for the float32 difference form (line search)
+    double2* xold;         // per row: x before the step (line search), nullable
+    double* ls_alpha;      // per problem: current trial step scale (line search)
+    double* ls_gd;         // per problem: dE/dz . d at the start of the step
+    int* ls_active;        // per problem: 1 while its trial step is being tested
     uint32_t* mask;        // per problem: own-charge bit mask over its world range
     uint32_t* taken;       // over all n charges: charges moved by an accepted problem
     int* active;           // per problem: still stepping
@@ -231,6 +236,7 @@ struct StepParams {
     int memory;
     double step0, alpha_min, alpha_max, maxstep, gtol, radius;
     int measure;  // 1: only record the RMS stationarity of the current rows (no step)
+    int line_search = 0;  // L-BFGS: at most this many Armijo halvings per step (0: none)
 };
 
 // Projected gradient descent (fixed or Barzilai-Borwein step), one CTA per problem.
@@ -454,12 +460,14 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
     }
     dmax = block_max(dmax, sh);
     const double alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
+    if (threadIdx.x == 0 && d.ls_alpha) d.ls_alpha[s] = alpha;
     TC_ROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
         double2 z = d.z[row], dv = d.q[row];
         d.xp[row] = z;
+        if (d.xold) d.xold[row] = d.x[row];
         double2 zn = make_double2(z.x + alpha * dv.x, z.y + alpha * dv.y);
         d.z[row] = zn;
         double2 xn = z_to_x(zn, sp.radius, pinned);
@@ -745,6 +753,7 @@ __global__ void k_lb_dir_fin(RelaxDev d, LbArgs la, StepParams sp)
     }
     const double dmax = c.reset ? sp.step0 * gmax : qmax;
     c.alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
+    if (d.ls_alpha) d.ls_alpha[la.s] = c.alpha;
 }
 
 // 8. the step z += alpha d, then x and its split
@@ -760,6 +769,10 @@ __global__ void __launch_bounds__(kUpd) k_lb_step(RelaxDev d, LbArgs la, StepPar
         const double2 z = d.z[row], q = d.q[row], gz = d.gp[row];
         const double2 dv = c.reset ? make_double2(-sp.step0 * gz.x, -sp.step0 * gz.y) : make_double2(-q.x, -q.y);
         d.xp[row] = z;
+        if (d.xold) {
+            d.xold[row] = d.x[row];
+            d.q[row] = dv;  // the line search moves along dv
+        }
         const double2 zn = make_double2(z.x + c.alpha * dv.x, z.y + c.alpha * dv.y);
         d.z[row] = zn;
         const double2 xn = z_to_x(zn, sp.radius, pinned);
@@ -811,6 +824,93 @@ __global__ void k_rows8(RelaxDev d, const double2* __restrict__ newpos, f8* __re
         const double2 nw = newpos[rr];
         if (!isfinite(nw.x) || !isfinite(nw.y)) set_status(d.st, ST_NONFINITE);
         rows8[rr] = make_f8(split4(o.x, o.y), (float)(nw.x - o.x), (float)(nw.y - o.y));
+    }
+}
+
+// ---- Armijo backtracking for the L-BFGS step (prm->line_search halvings) ----
+// After an L-BFGS update has placed problem s at the trial z = z_k + alpha d
+// (z_k in xp, d in q, x before the step in xold), the energy change of the
+// move is computed as pair differences (float64, or the float32 difference
+// form in the mixed phase) and the trial kept once
+//     E(x(z)) - E(x(z_k)) <= 1e-4 alpha (dE/dz . d);
+// otherwise alpha is halved and the rows move again.  The last trial is kept.
+
+// Per problem: dE/dz . d of the step just proposed; the problem is tested iff
+// it stepped.
+__global__ void __launch_bounds__(kUpd) k_ls_begin(RelaxDev d)
+{
+    __shared__ double sh[kUpd];
+    const int s = blockIdx.x;
+    const bool stepped = d.active[s] != 0;
+    if (!stepped) {
+        if (threadIdx.x == 0) d.ls_active[s] = 0;
+        return;
+    }
+    const Prob p = d.prob[s];
+    double gd = 0.0;
+    TC_ROWS(p)
+    {
+        const int64_t row = p.row_base + rl;
+        const double2 gz = d.gp[row], dv = d.q[row];
+        gd += gz.x * dv.x + gz.y * dv.y;
+    }
+    gd = block_sum<kUpd>(gd, sh);
+    if (threadIdx.x == 0) {
+        d.ls_gd[s] = gd;
+        d.ls_active[s] = 1;
+    }
+}
+
+// Rows of the energy-change pass for the problems still testing a trial.
+__global__ void k_ls_rows(RelaxDev d, int mixed)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_row_prob(d.prob, d.S, rr);
+        if (!d.ls_active[s]) continue;
+        const double2 o = d.xold[rr], nw = d.x[rr];
+        if (mixed)
+            d.rows8[rr] = make_f8(split4(o.x, o.y), (float)(nw.x - o.x), (float)(nw.y - o.y));
+        else
+            d.rows4[rr] = make_d4(o.x, o.y, nw.x, nw.y);
+    }
+}
+
+// Armijo test of problem s (one CTA per problem); a failed test halves alpha.
+__global__ void __launch_bounds__(kUpd) k_ls_check(RelaxDev d, const double* __restrict__ part_e, SlotView v, int last)
+{
+    __shared__ double sh[kUpd];
+    const int s = blockIdx.x;
+    if (!d.ls_active[s]) return;
+    const Prob p = d.prob[s];
+    double hi = 0.0, lo = 0.0;
+    TC_ROWS(p) dd_add(hi, lo, sum_e(p, rl, part_e, v));
+    const double dE = block_sum<kUpd>(hi, sh) + block_sum<kUpd>(lo, sh);
+    if (threadIdx.x == 0) {
+        const double alpha = d.ls_alpha[s];
+        if (!isfinite(dE)) set_status(d.st, ST_NONFINITE);
+        if (last || dE <= 1e-4 * alpha * d.ls_gd[s]) {
+            d.ls_active[s] = 0;
+        } else {
+            d.ls_alpha[s] = 0.5 * alpha;
+        }
+    }
+}
+
+// Move the rows of the problems whose trial failed to z_k + alpha d.
+__global__ void k_ls_move(RelaxDev d, double radius)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_row_prob(d.prob, d.S, rr);
+        if (!d.ls_active[s]) continue;
+        const double alpha = d.ls_alpha[s];
+        const bool pinned = d.flags && d.flags[d.gidx[rr]];
+        const double2 zk = d.xp[rr], dv = d.q[rr];
+        const double2 zn = make_double2(zk.x + alpha * dv.x, zk.y + alpha * dv.y);
+        d.z[rr] = zn;
+        const double2 xn = z_to_x(zn, radius, pinned);
+        d.x[rr] = xn;
+        d.xs[rr] = split4(xn.x, xn.y);
+        if (d.x3) d.x3[rr] = split3(xn.x, xn.y);
     }
 }
 
@@ -938,6 +1038,7 @@ static tc_status check_params(const tc_relax_params* prm)
     if (!prm) return TC_ERR_INVALID_ARG;
     if (prm->precision != TC_FP64 && prm->precision != TC_MIXED && prm->precision != TC_F64X) return TC_ERR_INVALID_ARG;
     if (prm->polish_precision != TC_FP64 && prm->polish_precision != TC_F64X) return TC_ERR_INVALID_ARG;
+    if (prm->line_search < 0 || prm->line_search > 30) return TC_ERR_INVALID_ARG;
     if (prm->optimizer < TC_OPT_GD || prm->optimizer > TC_OPT_LBFGS) return TC_ERR_INVALID_ARG;
     if (prm->n_steps < 0 || prm->polish_steps < 0) return TC_ERR_INVALID_ARG;
     if (prm->optimizer == TC_OPT_LBFGS && (prm->memory < 1 || prm->memory > kMaxMem)) return TC_ERR_INVALID_ARG;
@@ -994,9 +1095,38 @@ struct LargeSet {
     LbScal* sc = nullptr;  // one per entry of ids
 };
 
+// The energy-change pass of the line search: float32 difference form in the
+// mixed phase, float64 pair differences otherwise.
+struct LsArgs {
+    PassArgs a;       // rows: rows8 (mixed) or rows4; active: ls_active
+    int64_t G = 1;    // CTAs of that pass
+    bool mixed = false;
+};
+
+static cudaError_t line_search(RelaxDev& d, const LsArgs& ls, const Plan& P, const StepParams& sp, cudaStream_t s,
+                               int& launches)
+{
+    const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((d.M + 255) / 256, 8L * sm_count()));
+    SlotView v{P.W, ls.G, 0, P.M, 0};
+    k_ls_begin<<<d.S, kUpd, 0, s>>>(d);
+    cudaError_t e = cudaGetLastError();
+    for (int t = 0; t < sp.line_search && e == cudaSuccess; ++t) {
+        k_ls_rows<<<eb, 256, 0, s>>>(d, ls.mixed ? 1 : 0);
+        e = ls.mixed ? launch_pass<PASS_DMIX, false, false>(ls.a, ls.G, 0, 0, s)
+                     : launch_pass<PASS_DELTA, false, false>(ls.a, ls.G, 0, 0, s);
+        if (e != cudaSuccess) break;
+        k_ls_check<<<d.S, kUpd, 0, s>>>(d, ls.a.part_e, v, t == sp.line_search - 1 ? 1 : 0);
+        k_ls_move<<<eb, 256, 0, s>>>(d, sp.radius);
+        e = cudaGetLastError();
+        launches += 4;
+    }
+    return e;
+}
+
 template <int KIND>
 static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, const StepParams& sp, int steps,
-                           cudaStream_t s, bool prof, int& launches, const LargeSet& large)
+                           cudaStream_t s, bool prof, int& launches, const LargeSet& large,
+                           const LsArgs* ls = nullptr)
 {
     if (steps <= 0) return TC_OK;
     size_t ev0 = 0;  // events 0 .. 2 steps: [pass k] between 2k and 2k+1, [update k] between 2k+1 and 2k+2
@@ -1028,6 +1158,7 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
                 if (e == cudaSuccess) e = lbfgs_large(d, la, a.part_g, v, sp, cap);
                 launches += 2 * (2 * sp.memory + 1) + 6;
             }
+            if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, cap, launches);
         } else {
             k_update_gdbb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
         }
@@ -1164,8 +1295,10 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const bool use_x = prec == TC_F64X || (polish_x && prm->polish_steps > 0);
     const int64_t G_e = pass_grid<PASS_F64, true, false>(P.W);
     const int64_t G_d = pass_grid<PASS_DELTA, false, false>(P.W);
+    const bool ls_on = lbfgs && prm->line_search > 0;
+    const int64_t G_dm = pass_grid<PASS_DMIX, false, false>(P.W);
     int64_t slots = 1;
-    for (int64_t G : {G_bulk, G_f64, G_e, G_d}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
+    for (int64_t G : {G_bulk, G_f64, G_e, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
     // single-problem passes of the sequential accept
     int64_t slots1 = 1;
     std::vector<int64_t> G1(n_sub);
@@ -1203,6 +1336,11 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         d.Sh = cv.take<double2>(lbfgs ? (size_t)mem * M : 0);
         d.Yh = cv.take<double2>(lbfgs ? (size_t)mem * M : 0);
         d.rows4 = cv.take<d4>(M);
+        d.rows8 = ls_on ? cv.take<f8>(M) : nullptr;
+        d.xold = ls_on ? cv.take<double2>(M) : nullptr;
+        d.ls_alpha = ls_on ? cv.take<double>(n_sub) : nullptr;
+        d.ls_gd = ls_on ? cv.take<double>(n_sub) : nullptr;
+        d.ls_active = ls_on ? cv.take<int>(n_sub) : nullptr;
         d.mask = cv.take<uint32_t>(mask_words);
         d.taken = cv.take<uint32_t>(taken_words);
         d.active = cv.take<int>(n_sub);
@@ -1302,19 +1440,36 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     a.part_e = part_e;
     a.part_g = part_g;
     StepParams sp{prm->optimizer, mem, prm->step0, prm->alpha_min, prm->alpha_max, prm->maxstep, prm->gtol, prm->radius, 0};
+    sp.line_search = ls_on ? prm->line_search : 0;
+    // energy-change passes of the line search: float32 difference form in the mixed phase,
+    // float64 pair differences otherwise (rows: rows8 / rows4; snapshot as the relaxation's)
+    LsArgs ls_mixed, ls_f64;
+    ls_mixed.a = a;
+    ls_mixed.a.rows = d.rows8;
+    ls_mixed.a.snap = snap_split;
+    ls_mixed.a.active = d.ls_active;
+    ls_mixed.a.part_g = nullptr;
+    ls_mixed.G = G_dm;
+    ls_mixed.mixed = true;
+    ls_f64.a = a;
+    ls_f64.a.rows = d.rows4;
+    ls_f64.a.snap = pos;
+    ls_f64.a.active = d.ls_active;
+    ls_f64.a.part_g = nullptr;
+    ls_f64.G = G_d;
     tc_status rs;
     if (prec == TC_MIXED) {
         a.rows = d.xs;
         a.snap = snap_split;
-        rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
+        rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
     } else if (prec == TC_F64X) {
         a.rows = d.x3;
         a.snap = snap3;
-        rs = run_phase<PASS_F64X>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
+        rs = run_phase<PASS_F64X>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_f64);
     } else {
         a.rows = d.x;
         a.snap = pos;
-        rs = run_phase<PASS_F64>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large);
+        rs = run_phase<PASS_F64>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_f64);
     }
     if (rs != TC_OK) return rs;
     if (prm->polish_steps > 0) {
@@ -1325,11 +1480,11 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         if (polish_x) {
             a.rows = d.x3;
             a.snap = snap3;
-            rs = run_phase<PASS_F64X>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large);
+            rs = run_phase<PASS_F64X>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large, &ls_f64);
         } else {
             a.rows = d.x;
             a.snap = pos;
-            rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large);
+            rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large, &ls_f64);
         }
         if (rs != TC_OK) return rs;
     }
@@ -1511,6 +1666,7 @@ tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const 
                               const int64_t* world, const uint8_t* flags, const tc_relax_params* prm,
                               tc_subdomain_result* out, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_relax_subdomains");
     return tc::relax(pos, n, idx, offsets, n_sub, world, flags, prm, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -1524,6 +1680,7 @@ tc_status tc_relax_last_profile(tc_relax_profile* out)
 tc_status tc_subdomain_delta_energy(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
                                     int32_t n_sub, const double* new_active, double* delta, tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_subdomain_delta_energy");
     return tc::delta_all(pos, n, idx, offsets, n_sub, new_active, delta, false, nullptr,
                          reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1532,6 +1689,7 @@ tc_status tc_subdomain_delta_energy_mixed(const double* pos, int64_t n, const in
                                           int32_t n_sub, const double* new_active, double* delta, double* bound,
                                           tc_stream stream)
 {
+    tc::NvtxRange nvtx_range("tc_subdomain_delta_energy_mixed");
     return tc::delta_all(pos, n, idx, offsets, n_sub, new_active, delta, true, bound,
                          reinterpret_cast<cudaStream_t>(stream));
 }

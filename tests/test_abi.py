@@ -23,8 +23,9 @@ def test_exports_every_declared_function(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # tc_relax_params: 4 int32, 6 double, 2 int32, 1 double, 3 int32 (+4 padding) -> 96 bytes
+    # tc_relax_params: 4 int32, 6 double, 2 int32, 1 double, 4 int32 -> 96 bytes
     assert C.sizeof(L.RelaxParams) == 96 and L.RelaxParams.polish_precision.offset == 88
+    assert L.RelaxParams.line_search.offset == 92
     assert L.RelaxParams.step0.offset == 16 and L.RelaxParams.polish_steps.offset == 64
     assert L.RelaxParams.want_energy.offset == 80
     assert L.RESULT_BYTES == 32

@@ -1,0 +1,88 @@
+"""GPU parity of the L-BFGS Armijo line search (tc_relax_params.line_search) against the oracle.
+
+float64 phases test the energy change as float64 pair differences, like the oracle, so the
+accept/halve decisions agree and the trajectories match to 1e-9 (as without the line search).
+The mixed phase tests with the float32 difference form: checked by the energy it reaches.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2609_24722_b300 as tc
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64x"])
+def test_line_search_instances_match_oracle(prec):
+    sizes = [60, 150, 333]
+    pos = np.concatenate([synth.arcsine_disk(m, 40 + m) for m in sizes])
+    world = np.array([[0, 60], [60, 210], [210, 543]], dtype=np.int64)
+    p = T(pos.copy())
+    iters = 30
+    # a large first step makes the first trials fail, so the halving path runs
+    r = tc.relax_subdomains(p, world=T(world), precision=prec, optimizer="lbfgs", n_steps=iters, memory=8,
+                            step0=1e-1, maxstep=0.2, accept=False, want_energy=True, line_search=10)
+    tc.sync_status()
+    x = p.cpu().numpy()
+    changed = 0
+    for k, (b, e) in enumerate(world):
+        xo, it, rms = oracle.lbfgs(pos[b:e], memory=8, max_iter=iters, gtol=0.0, step0=1e-1, maxstep=0.2,
+                                   line_search=10)
+        xn, _, _ = oracle.lbfgs(pos[b:e], memory=8, max_iter=iters, gtol=0.0, step0=1e-1, maxstep=0.2)
+        changed += np.abs(xo - xn).max() > 1e-6  # the line search changed the path
+        assert np.abs(x[b:e] - xo).max() <= 1e-9
+        assert abs(r.energy[k].item() - oracle.energy(xo)) <= 1e-12 * oracle.energy(xo)
+    assert changed >= 2
+
+
+def test_line_search_large_instance_matches_oracle():
+    """An instance above 16384 charges (grid-wide L-BFGS update) with the line search."""
+    n = 17000
+    pos = synth.arcsine_disk(n, 78)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    world = T(np.array([[0, n]], dtype=np.int64))
+    # start near equilibrium, where a 0.05 step overshoots and the halvings run
+    q = T(pos.copy())
+    tc.relax_subdomains(q, world=world, precision="fp64", optimizer="lbfgs", n_steps=20, memory=8, step0=1e-3,
+                        maxstep=0.01, accept=False)
+    tc.sync_status()
+    x1 = q.cpu().numpy()
+    p = T(x1.copy())
+    iters = 2
+    r = tc.relax_subdomains(p, world=world, precision="fp64", optimizer="lbfgs", n_steps=iters, memory=8,
+                            step0=1e-3, maxstep=0.05, accept=False, line_search=6)
+    tc.sync_status()
+    xo, it, rms = oracle.lbfgs(x1, memory=8, max_iter=iters, gtol=0.0, step0=1e-3, maxstep=0.05, line_search=6)
+    xn, _, _ = oracle.lbfgs(x1, memory=8, max_iter=iters, gtol=0.0, step0=1e-3, maxstep=0.05)
+    assert np.abs(xo - xn).max() > 1e-6
+    assert int(r.steps[0]) == iters
+    assert np.abs(p.cpu().numpy() - xo).max() <= 1e-9
+
+
+def test_line_search_mixed_subdomains_lower_energy():
+    """Mixed L-BFGS with the float32 difference-form Armijo test: every subdomain's E_sub drops."""
+    n = 20000
+    pos = synth.lattice_disk(n, 3)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    subs = synth.subdomains(pos, 6, 100, 900, 4)
+    idx, off = synth.to_csr(subs)
+    p = T(pos.copy())
+    r = tc.relax_subdomains(p, T(idx), T(off), precision="mixed", optimizer="lbfgs", n_steps=40, memory=8,
+                            step0=1e-6, maxstep=5e-4, accept=True, want_energy=True, line_search=8)
+    tc.sync_status()
+    st = r.status.cpu().numpy()
+    d = r.delta_e.cpu().numpy()
+    assert np.all(d[st != 2] < 0)
+    assert (st == 1).sum() >= 1

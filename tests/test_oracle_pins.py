@@ -643,3 +643,20 @@ def test_structure_polygon_centres_and_euler():
     assert z.sum() == 2 * (3 * len(p) - 3 - h)
     nb = S.neighbours(p)
     assert all(i in nb[j] for i in range(len(p)) for j in nb[i])  # symmetric
+
+
+def test_lbfgs_line_search_is_monotone_and_converges():
+    """With the Armijo line search every iteration lowers the energy (checked by rerunning the
+    deterministic iteration for 1..25 steps), and the N = 8 ring relaxes to a float64-stationary point."""
+    pos = synth.arcsine_disk(120, 21)
+    es = []
+    for k in range(1, 26):
+        x, it, _ = oracle.lbfgs(pos, max_iter=k, step0=1e-3, maxstep=0.05, line_search=10)
+        assert it == k
+        es.append(oracle.energy(x))
+    assert all(b <= a for a, b in zip(es, es[1:]))
+    x, it, rms = oracle.lbfgs(synth.arcsine_disk(8, 2), max_iter=2000, gtol=1e-10, step0=1e-3, maxstep=0.05,
+                              line_search=10)
+    assert rms < 1e-10
+    _, rms_c, _ = oracle.projected_grad(x, oracle.grad(x))
+    assert rms_c < 1e-9
