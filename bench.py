@@ -82,6 +82,7 @@ def run_case(args):
     if args.case == "full-relax":
         print(json.dumps(run_full_relax(dev, n=args.n)))
         print(json.dumps(run_full_relax(dev, n=args.n, max_polish=1000, polish_precision="fp64x")))
+        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=1000, polish_precision="fp64x", line_search=8)))
         return
     if args.case == "cycle":
         # cycle time against N at a fixed number of subdomain optimisations (Sec. II E)
@@ -322,7 +323,7 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
 
 
 def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 200,
-                   polish_precision: str = "fp64") -> dict:
+                   polish_precision: str = "fp64", line_search: int = 0) -> dict:
     """Config C4: one configuration of N = 1e5 charges (arcsine init, Hilbert order) relaxed by
     mixed-precision L-BFGS(8) on the wall map until the RMS of dE/dz falls below 1e-4 x the initial
     mean force, then float64 L-BFGS (or the float64-grade fp64x pass) to 1e-8 x that (step caps
@@ -344,17 +345,18 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r1 = tc.relax_subdomains(p, world=world, precision="mixed", optimizer="lbfgs", n_steps=max_mixed, memory=8,
-                             step0=1e-6, maxstep=0.1 * h, gtol=1e-4 * f_ref, accept=False)
+                             step0=1e-6, maxstep=0.1 * h, gtol=1e-4 * f_ref, accept=False, line_search=line_search)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    r2 = tc.relax_subdomains(p, world=world, precision=polish_precision, optimizer="lbfgs", n_steps=max_polish, memory=8,
+    r2 = tc.relax_subdomains(p, world=world, precision=polish_precision, optimizer="lbfgs", n_steps=max_polish,
+                             line_search=line_search, memory=8,
                              step0=1e-6, maxstep=0.1 * h, gtol=1e-8 * f_ref, accept=False, want_energy=True)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     tc.sync_status()
     e = r2.energy[0].item()
     return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, {polish_precision} polish to 1e-8 "
-                        f"(caps {max_mixed} / {max_polish} steps)",
+                        f"(caps {max_mixed} / {max_polish} steps), Armijo halvings per step: {line_search}",
             "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
             "mixed_steps": int(r1.steps[0]), "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
             "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1,
