@@ -242,7 +242,30 @@ def cpu_baseline(pos, idx, off, seconds: float = 12.0) -> dict:
     out["all_cores"] = {"value": n_omp * (N - 1) / dt, "unit": UNIT, "cores": threads, "kind": "oracle-openmp",
                         "sample": f"the first {n_omp} subdomain rows against all {N} charges "
                                   f"(tco_rows_grad built with -fopenmp, bit-identical rows), {dt:.1f} s"}
+    # one full float64 E + gradient of the single-thread oracle at small N (N = 1e5 would take ~1 min)
+    import synth
+
+    full = {}
+    for nn in (1000, 20000):
+        pp = synth.arcsine_disk(nn, 0)
+        t0 = time.perf_counter()
+        oracle.grad(pp)
+        oracle.energy(pp)
+        full[str(nn)] = time.perf_counter() - t0
+    out["full_energy_grad_s"] = full
+    out["host"] = {"nproc": os.cpu_count(), "cpu_model": _cpu_model()}
     return out
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
@@ -349,14 +372,14 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     r2 = tc.relax_subdomains(p, world=world, precision=polish_precision, optimizer="lbfgs", n_steps=max_polish,
-                             line_search=line_search, memory=8,
+                             memory=8,
                              step0=1e-6, maxstep=0.1 * h, gtol=1e-8 * f_ref, accept=False, want_energy=True)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     tc.sync_status()
     e = r2.energy[0].item()
     return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, {polish_precision} polish to 1e-8 "
-                        f"(caps {max_mixed} / {max_polish} steps), Armijo halvings per step: {line_search}",
+                        f"(caps {max_mixed} / {max_polish} steps), Armijo halvings per mixed step: {line_search}",
             "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
             "mixed_steps": int(r1.steps[0]), "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
             "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1,
@@ -576,6 +599,16 @@ def main():
             ts.append(a.elapsed_time(b))
         return statistics.mean(ts)
 
+    # the C3 relaxation pass in each precision (two profiled steps each, no accept)
+    c3_pass = {}
+    for prec_name in ("fp64", "fp64x"):
+        pc = pos0.clone()
+        tc.relax_subdomains(pc, idx, off, **{**relax_kw, "precision": prec_name, "n_steps": 2, "accept": False})
+        pr = tc.relax_last_profile()
+        ms_p = pr["pass_ms"] / max(pr["n_pass"], 1)
+        c3_pass[prec_name] = {"ms_per_pass": ms_p, "pairs_per_s": pr["pass_pairs"] / (ms_p / 1e3)}
+    c3_pass["mixed"] = {"ms_per_pass": prof["pass_ms"] / max(prof["n_pass"], 1),
+                        "pairs_per_s": prof["pass_pairs"] / (prof["pass_ms"] / max(prof["n_pass"], 1) / 1e3)}
     ms_mixed = time_allpairs("mixed", 5)
     ms_f64 = time_allpairs("fp64", 3)
     ms_f64x = time_allpairs("fp64x", 3)
@@ -624,6 +657,7 @@ def main():
         "allpairs_n1e5": {"mixed_pairs_per_s": N * (N - 1) / (ms_mixed / 1e3), "mixed_ms": ms_mixed,
                           "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64,
                           "fp64x_pairs_per_s": N * (N - 1) / (ms_f64x / 1e3), "fp64x_ms": ms_f64x},
+        "c3_relax_pass_by_precision": c3_pass,
         "instances_c5": c5,
         "adaptive_cycle": cyc,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
