@@ -42,7 +42,7 @@ LOCAL_PREC = "fp64"  # the total energy needs 12+ digits: float64
 # DRAM bytes of one relaxation-pass launch of this workload, from an ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/relax_pass_traffic_n1e5.md); it must be
 # retaken (or set to None) whenever k_pass_mixed changes.
-RELAX_PASS_DRAM_BYTES = None
+RELAX_PASS_DRAM_BYTES = 16.3e6
 METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
 UNIT = "pair-interactions/s"
 WORKLOAD = ("adaptive-cycle step at N=1e5: fp64 local energies of all charges + 256 subdomains "

@@ -140,19 +140,7 @@ struct Prob {
     int32_t n_rb;       // row blocks
     int32_t n_t_snap;   // snapshot tiles
     int32_t n_t_priv;   // own-row tiles
-    // With a source list (listed = 1) the snapshot sources are the list_len
-    // charges gather[list_off ..] (the world range without the own charges, in
-    // order) instead of the masked range [snap_b, snap_e): no source slot is
-    // spent on a masked-out charge.
-    int32_t listed;
-    int64_t list_off;
-    int64_t list_len;
 };
-
-__host__ __device__ __forceinline__ int64_t snap_count(const Prob& p)
-{
-    return p.listed ? p.list_len : p.snap_e - p.snap_b;
-}
 
 __device__ __forceinline__ int find_prob(const Prob* __restrict__ P, int S, int64_t u)
 {
@@ -269,7 +257,6 @@ struct PassArgs {
                         // f8 old split + move (difference form)
     const void* snap;   // snapshot: float4 split (mixed, difference form), double2 (f64, delta)
     const uint32_t* mask;
-    const int32_t* gather;  // source lists of listed problems (nullable when none is listed)
     const int* active;  // nullable; problems with active[s] == 0 are skipped
     double* part_e;     // [slots x M] row partial energies (or energy changes)
     double2* part_g;    // [slots x M] row partial gradients (nullable)

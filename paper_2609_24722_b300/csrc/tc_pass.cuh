@@ -309,11 +309,8 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
     using src_t = typename SrcT<KIND>::type;
     if (t < p.n_t_snap) {
         int64_t j = (int64_t)t * T + tid;
-        bool ok = j < snap_count(p);
-        if (p.listed) {
-            // the listed charge's index, relative to snap_b as below
-            if (ok) j = (int64_t)a.gather[p.list_off + j] - p.snap_b;
-        } else if (ok && p.mask_off >= 0) {
+        bool ok = j < p.snap_e - p.snap_b;
+        if (ok && p.mask_off >= 0) {
             uint32_t w = a.mask[p.mask_off + (j >> 5)];
             ok = ((w >> (j & 31)) & 1u) == 0u;
         }

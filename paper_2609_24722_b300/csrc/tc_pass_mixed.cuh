@@ -211,16 +211,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
 
     MixedRows<R> rs;
     unsigned valid = 0;  // bit c: this thread's c-th staged source is a real charge
-    // source-list entries of the next tile to fetch, loaded one tile ahead so the
-    // copies never wait for them
-    int32_t nxt[S];
-    auto load_idx = [&](int t) {
-#pragma unroll
-        for (int c = 0; c < S; ++c) {
-            const int64_t j = (int64_t)t * T + tid + c * THREADS;
-            nxt[c] = (sprob.listed && t < sprob.n_t_snap && j < sprob.list_len) ? a.gather[sprob.list_off + j] : 0;
-        }
-    };
     // start the copies of tile t's sources (positions tid + c * THREADS) into sraw
     auto fetch = [&](int t) {
         valid = 0;
@@ -230,13 +220,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
             const float4* src;
             bool ok;
             if (t < sprob.n_t_snap) {
-                int64_t j = (int64_t)t * T + jt;
-                ok = j < snap_count(sprob);
-                if (sprob.listed) {
-                    if (ok) j = (int64_t)nxt[c] - sprob.snap_b;
-                } else if (ok && sprob.mask_off >= 0) {
-                    ok = ((a.mask[sprob.mask_off + (j >> 5)] >> (j & 31)) & 1u) == 0u;
-                }
+                const int64_t j = (int64_t)t * T + jt;
+                ok = j < sprob.snap_e - sprob.snap_b;
+                if (ok && sprob.mask_off >= 0) ok = ((a.mask[sprob.mask_off + (j >> 5)] >> (j & 31)) & 1u) == 0u;
                 src = static_cast<const float4*>(a.snap) + sprob.snap_b + j;
             } else {
                 const int64_t j = (int64_t)(t - sprob.n_t_snap) * T + jt;
@@ -286,15 +272,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
             float4 rbox = warp_box(rs.load(static_cast<const float4*>(a.rows), sprob.row_base, rl0, THREADS, sprob.m,
                                            slo2, sacc, tid));
             if (lane == 0) srbox[warp] = rbox;
-            load_idx(t0);
             fetch(t0);
-            if (t0 + 1 < t1) load_idx(t0 + 1);
             stage(0);
             __syncthreads();
             for (int t = t0; t < t1; ++t) {
                 const int buf = (t - t0) & 1;
                 if (t + 1 < t1) fetch(t + 1);
-                if (t + 2 < t1) load_idx(t + 2);
                 float4 tbox = swbox[buf][0], rb4 = srbox[0];
 #pragma unroll
                 for (int w = 1; w < NW; ++w) {

@@ -32,7 +32,7 @@ inline void plan_units(Plan& P)
     int64_t u = 0;
     for (auto& p : P.prob) {
         p.n_rb = (int32_t)((p.m + kRB - 1) / kRB);
-        p.n_t_snap = (int32_t)((snap_count(p) + kT - 1) / kT);
+        p.n_t_snap = (int32_t)((p.snap_e - p.snap_b + kT - 1) / kT);
         p.n_t_priv = (int32_t)((p.m + kT - 1) / kT);
         p.unit_off = u;
         u += (int64_t)p.n_rb * (p.n_t_snap + p.n_t_priv);

@@ -229,37 +229,6 @@ __global__ void k_split3_pos(const double2* __restrict__ pos, int64_t n, fx3* __
         out[i] = split3(pos[i].x, pos[i].y);
 }
 
-// Source list of subdomain problem s: the charges of its world range that it
-// does not move, in order (ordered compaction of the unmasked positions).
-constexpr int kListThreads = 512;
-__global__ void __launch_bounds__(kListThreads) k_build_lists(RelaxDev d, int32_t* __restrict__ gather)
-{
-    __shared__ int warp_tot[kListThreads / 32];
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const Prob p = d.prob[s];
-    if (!p.listed) return;
-    const int64_t len = p.snap_e - p.snap_b;
-    int64_t base = 0;
-    for (int64_t c0 = 0; c0 < len; c0 += kListThreads) {
-        const int64_t j = c0 + tid;
-        const bool keep = j < len && ((d.mask[p.mask_off + (j >> 5)] >> (j & 31)) & 1u) == 0u;
-        const unsigned b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) warp_tot[w] = __popc(b);
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int k = 0; k < kListThreads / 32; ++k) {
-            before += k < w ? warp_tot[k] : 0;
-            tot += warp_tot[k];
-        }
-        const int64_t r = base + before + __popc(b & ((1u << lane) - 1u));
-        // an invalid index set (repeated charges) leaves more unmasked charges than
-        // list_len; the call reports it before any pass, and nothing is written past the list
-        if (keep && r < p.list_len) gather[p.list_off + r] = (int32_t)(p.snap_b + j);
-        base += tot;
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------ updates ---
 
 struct StepParams {
@@ -1285,7 +1254,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     Plan P;
     P.prob.resize(n_sub);
     std::vector<int64_t> wbeg(n_sub);
-    int64_t rows = 0, mask_words = 0, max_m = 0, list_total = 0;
+    int64_t rows = 0, mask_words = 0, max_m = 0;
     for (int32_t k = 0; k < n_sub; ++k) {
         int64_t wb = world ? h.world[2 * k] : 0, we = world ? h.world[2 * k + 1] : n;
         if (wb < 0 || we > n || wb > we) return TC_ERR_INVALID_ARG;
@@ -1305,10 +1274,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
             p.snap_e = we;
             p.mask_off = mask_words;
             mask_words += (we - wb + 31) / 32;
-            p.listed = 1;
-            p.list_off = list_total;
-            p.list_len = (we - wb) - m;
-            list_total += p.list_len;
         }
         if (m > INT32_MAX / 2) return TC_ERR_INVALID_ARG;
         p.m = (int32_t)m;
@@ -1354,7 +1319,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
 
     Carver c;
     fx3* snap3 = nullptr;
-    int32_t* gather = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
         probd = cv.take<Prob>(n_sub);
@@ -1378,7 +1342,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         d.ls_gd = ls_on ? cv.take<double>(n_sub) : nullptr;
         d.ls_active = ls_on ? cv.take<int>(n_sub) : nullptr;
         d.mask = cv.take<uint32_t>(mask_words);
-        gather = cv.take<int32_t>(list_total);
         d.taken = cv.take<uint32_t>(taken_words);
         d.active = cv.take<int>(n_sub);
         d.ok = cv.take<int>(n_sub);
@@ -1440,8 +1403,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         ++launches;
         if (!inst) {
             k_mask_build<<<eb, 256, 0, s>>>(d);
-            k_build_lists<<<n_sub, kListThreads, 0, s>>>(d, gather);
-            launches += 2;
+            ++launches;
         }
     }
     if (!inst && n > 0) {
@@ -1474,7 +1436,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     a.W = P.W;
     a.M = M;
     a.mask = inst ? nullptr : d.mask;
-    a.gather = inst ? nullptr : gather;
     a.active = d.active;
     a.part_e = part_e;
     a.part_g = part_g;
