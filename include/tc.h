@@ -152,7 +152,9 @@ tc_status tc_project_disk(double* pos, int64_t n, double radius, const uint8_t* 
 typedef enum {
     TC_OPT_GD = 0,    /* projected gradient descent x <- P(x - step0 g) */
     TC_OPT_BB = 1,    /* projected descent with Barzilai-Borwein (s^T y / y^T y) steps */
-    TC_OPT_LBFGS = 2  /* L-BFGS on the smooth wall map x = radius sin|z| z/|z| (no projection) */
+    TC_OPT_LBFGS = 2, /* L-BFGS on the smooth wall map x = radius sin|z| z/|z| (no projection) */
+    TC_OPT_LBFGS_TU = 3 /* L-BFGS on the paper's (t, u) (Sec. II D): x = radius sin^2 t (cos u, sin u),
+                           pinned (cos u, sin u); gradients by the paper's chain rule */
 } tc_optimizer;
 
 typedef struct {

@@ -61,7 +61,7 @@ def lib(openmp: bool = False) -> C.CDLL:
             "tco_subdomain_bb": [vp, i64, vp, i64, d, d, d, i64, d, vp, vp],
             "tco_accept_sequential": [vp, i64, vp, vp, i64, vp, vp, vp],
             "tco_lbfgs": [vp, i64, i64, i64, d, d, d, d, vp, vp, vp],
-            "tco_lbfgs_ls": [vp, i64, i64, i64, d, d, d, d, vp, i64, vp, vp],
+            "tco_lbfgs_ls": [vp, i64, i64, i64, d, d, d, d, vp, i64, i64, vp, vp],
             "tco_threads": [],
             "tco_zone_select": [vp, i64, vp, vp, d, d, d, d, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp],
             "tco_cycle": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, vp, d, d, d, i64, vp, vp, vp],
@@ -217,15 +217,17 @@ def accept_sequential(pos, idx, offsets, new_act):
 
 
 def lbfgs(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: float = 1e-4,
-          maxstep: float = 1e-2, radius: float = 1.0, flags=None, line_search: int = 0):
-    """L-BFGS on the wall map with a max-displacement cap and, for line_search > 0, an Armijo
-    backtracking line search of at most that many halvings; returns (x, iterations, final RMS)."""
+          maxstep: float = 1e-2, radius: float = 1.0, flags=None, line_search: int = 0, tu: bool = False):
+    """L-BFGS on the wall map (tu=True: on the paper's (t, u) variables) with a max-displacement cap
+    and, for line_search > 0, an Armijo backtracking line search of at most that many halvings;
+    returns (x, iterations, final RMS of dE/d(variables))."""
     p = _pos(pos).copy()
     f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
     it = np.zeros(1, dtype=np.int64)
     rms = np.zeros(1)
     _check(lib().tco_lbfgs_ls(_p(p), p.shape[0], int(memory), int(max_iter), float(gtol), float(step0),
-                              float(maxstep), float(radius), _p(f), int(line_search), _p(it), _p(rms)), "lbfgs")
+                              float(maxstep), float(radius), _p(f), int(line_search), int(bool(tu)), _p(it),
+                              _p(rms)), "lbfgs")
     return p, int(it[0]), float(rms[0])
 
 

@@ -525,6 +525,63 @@ static void grad_z(const double* z, const double* g, int64_t n, double sigma, co
     }
 }
 
+/* The paper's parameterisation (Sec. II D): an interior charge is (t, u) with
+ * r = sigma sin^2 t and x = r (cos u, sin u); a boundary (pinned) charge is
+ * x = (cos u, sin u), stored as (u, 0).  Its gradients are the printed chain
+ * rule: dE/dt = (E_x cos u + E_y sin u) sigma sin 2t,
+ * dE/du = -E_x r sin u + E_y r cos u, and for a boundary charge
+ * dE/du = -E_x sin u + E_y cos u. */
+static void tu_to_x(const double* z, int64_t n, double sigma, const unsigned char* flags, double* x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double t = z[2 * i], u = z[2 * i + 1];
+        if (flags && flags[i]) {
+            x[2 * i] = cos(t);
+            x[2 * i + 1] = sin(t);
+        } else {
+            double st = sin(t), r = sigma * st * st;
+            x[2 * i] = r * cos(u);
+            x[2 * i + 1] = r * sin(u);
+        }
+    }
+}
+
+static void x_to_tu(const double* x, int64_t n, double sigma, const unsigned char* flags, double* z)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double px = x[2 * i], py = x[2 * i + 1];
+        double r = sqrt(px * px + py * py);
+        double u = r > 0.0 ? atan2(py, px) : 0.0;
+        if (flags && flags[i]) {
+            z[2 * i] = u;
+            z[2 * i + 1] = 0.0;
+        } else {
+            double q = r / sigma;
+            if (q > 1.0) q = 1.0;
+            z[2 * i] = asin(sqrt(q));
+            z[2 * i + 1] = u;
+        }
+    }
+}
+
+static void grad_tu(const double* z, const double* g, int64_t n, double sigma, const unsigned char* flags,
+                    double* gz)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double gx = g[2 * i], gy = g[2 * i + 1];
+        if (flags && flags[i]) {
+            double u = z[2 * i];
+            gz[2 * i] = -gx * sin(u) + gy * cos(u);
+            gz[2 * i + 1] = 0.0;
+        } else {
+            double t = z[2 * i], u = z[2 * i + 1];
+            double st = sin(t), r = sigma * st * st;
+            gz[2 * i] = (gx * cos(u) + gy * sin(u)) * sigma * sin(2.0 * t);
+            gz[2 * i + 1] = -gx * r * sin(u) + gy * r * cos(u);
+        }
+    }
+}
+
 /* Limited-memory BFGS on the smooth wall parameterisation, with a maximum
  * displacement cap and no line search, over all n charges of one configuration.
  *
@@ -541,7 +598,7 @@ static void grad_z(const double* z, const double* g, int64_t n, double sigma, co
  * pos (in/out, 2n): x of the final z.  Reports iterations and final RMS |gz|. */
 int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
                  double step0, double maxstep, double sigma, const unsigned char* flags,
-                 int64_t max_halvings, int64_t* iters_out, double* rms_out);
+                 int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out);
 
 /* Energy change E(xn) - E(x) of moving every charge from x to xn, summed as
  * pair differences (compensated), not as a difference of totals. */
@@ -559,7 +616,7 @@ int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double g
               double step0, double maxstep, double sigma, const unsigned char* flags,
               int64_t* iters_out, double* rms_out)
 {
-    return tco_lbfgs_ls(pos, n, memory, max_iter, gtol, step0, maxstep, sigma, flags, 0, iters_out, rms_out);
+    return tco_lbfgs_ls(pos, n, memory, max_iter, gtol, step0, maxstep, sigma, flags, 0, 0, iters_out, rms_out);
 }
 
 /* tco_lbfgs with an Armijo backtracking line search (max_halvings > 0): the
@@ -567,10 +624,11 @@ int tco_lbfgs(double* pos, int64_t n, int64_t memory, int64_t max_iter, double g
  *     E(x(z + alpha d)) - E(x(z)) <= 1e-4 alpha (dE/dz . d),
  * the energy change summed as pair differences; otherwise alpha is halved, at
  * most max_halvings times, and the last trial is taken.  max_halvings = 0 is
- * the plain iteration. */
+ * the plain iteration.  tu != 0 runs the iteration on the paper's (t, u)
+ * variables instead of the smooth map. */
 int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
                  double step0, double maxstep, double sigma, const unsigned char* flags,
-                 int64_t max_halvings, int64_t* iters_out, double* rms_out)
+                 int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out)
 {
     if (n < 0 || memory < 1 || max_iter < 0 || max_halvings < 0 || (n > 0 && !pos) || !(sigma > 0.0))
         return TCO_ERR_INVALID_ARG;
@@ -595,11 +653,11 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
     int64_t hist = 0, head = 0; /* ring buffer: newest pair at (head - 1) mod M */
     int64_t it = 0;
     double rms = 0.0;
-    x_to_z(pos, n, sigma, flags, z);
-    z_to_x(z, n, sigma, flags, pos);
+    if (tu) x_to_tu(pos, n, sigma, flags, z); else x_to_z(pos, n, sigma, flags, z);
+    if (tu) tu_to_x(z, n, sigma, flags, pos); else z_to_x(z, n, sigma, flags, pos);
     int st = tco_grad(pos, n, g);
     if (!st) {
-        grad_z(z, g, n, sigma, flags, gz);
+        if (tu) grad_tu(z, g, n, sigma, flags, gz); else grad_z(z, g, n, sigma, flags, gz);
         rms = n > 0 ? sqrt(dot(gz, gz, L) / (double)n) : 0.0;
     }
     for (; !st && it < max_iter; ++it) {
@@ -638,17 +696,17 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
             memcpy(xk, pos, sz);
             const double gd = dot(gz, d, L);
             for (int64_t h = 0;; ++h) {
-                z_to_x(zn, n, sigma, flags, pos);
+                if (tu) tu_to_x(zn, n, sigma, flags, pos); else z_to_x(zn, n, sigma, flags, pos);
                 if (instance_delta(xk, pos, n) <= 1e-4 * alpha * gd || h == max_halvings) break;
                 alpha *= 0.5;
                 for (int64_t i = 0; i < L; ++i) zn[i] = z[i] + alpha * d[i];
             }
         } else {
-            z_to_x(zn, n, sigma, flags, pos);
+            if (tu) tu_to_x(zn, n, sigma, flags, pos); else z_to_x(zn, n, sigma, flags, pos);
         }
         st = tco_grad(pos, n, g);
         if (st) break;
-        grad_z(zn, g, n, sigma, flags, gzn);
+        if (tu) grad_tu(zn, g, n, sigma, flags, gzn); else grad_z(zn, g, n, sigma, flags, gzn);
         rms = n > 0 ? sqrt(dot(gzn, gzn, L) / (double)n) : 0.0;
         /* the candidate pair is tested first and stored only if kept, so a
          * rejected pair never overwrites the oldest stored one */

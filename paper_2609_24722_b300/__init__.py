@@ -32,7 +32,7 @@ __all__ = [
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED, "fp64x": L.TC_F64X}
-_OPT = {"gd": L.TC_OPT_GD, "bb": L.TC_OPT_BB, "lbfgs": L.TC_OPT_LBFGS}
+_OPT = {"gd": L.TC_OPT_GD, "bb": L.TC_OPT_BB, "lbfgs": L.TC_OPT_LBFGS, "lbfgs_tu": L.TC_OPT_LBFGS_TU}
 
 
 def library_path() -> str:

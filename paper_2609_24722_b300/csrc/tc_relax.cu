@@ -60,6 +60,7 @@ struct RelaxDev {
     double* energy;        // per problem
     int* status;           // per problem
     int* st;               // device status word
+    int tu;                // L-BFGS variables: 0 the smooth wall map, 1 the paper's (t, u)
 };
 
 __device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, int64_t row)
@@ -127,8 +128,18 @@ __device__ double block_max(double v, double* sh)
 // x = z/|z|.  The wall is a smooth maximum of |x|, as for the paper's
 // r = sigma sin^2 t of Sec. II D, so L-BFGS needs no projection.
 
-__device__ __forceinline__ double2 z_to_x(double2 z, double radius, bool pinned)
+// Two L-BFGS variables for the wall.  The smooth map (tu = false): a free charge
+// is z in R^2 with x = radius sin|z| z/|z|, a pinned one x = z/|z|.  The
+// paper's parameterisation (tu = true, Sec. II D): a free charge is (t, u) with
+// x = radius sin^2 t (cos u, sin u), a pinned one (u, 0) with x = (cos u, sin u).
+// Both make the wall a smooth maximum of |x|, so neither needs a projection.
+__device__ __forceinline__ double2 z_to_x(double2 z, double radius, bool pinned, bool tu)
 {
+    if (tu) {
+        if (pinned) return make_double2(cos(z.x), sin(z.x));
+        const double st = sin(z.x), r = radius * st * st;
+        return make_double2(r * cos(z.y), r * sin(z.y));
+    }
     double rho = sqrt(z.x * z.x + z.y * z.y);
     if (pinned) return make_double2(z.x / rho, z.y / rho);
     if (rho > 0.0) {
@@ -138,9 +149,14 @@ __device__ __forceinline__ double2 z_to_x(double2 z, double radius, bool pinned)
     return make_double2(0.0, 0.0);
 }
 
-__device__ __forceinline__ double2 x_to_z(double2 x, double radius, bool pinned)
+__device__ __forceinline__ double2 x_to_z(double2 x, double radius, bool pinned, bool tu)
 {
     double r = sqrt(x.x * x.x + x.y * x.y);
+    if (tu) {
+        const double u = r > 0.0 ? atan2(x.y, x.x) : 0.0;
+        if (pinned) return make_double2(u, 0.0);
+        return make_double2(asin(sqrt(fmin(r / radius, 1.0))), u);
+    }
     if (pinned) return r > 0.0 ? make_double2(x.x / r, x.y / r) : make_double2(1.0, 0.0);
     if (r > 0.0) {
         double q = fmin(r / radius, 1.0);
@@ -150,9 +166,17 @@ __device__ __forceinline__ double2 x_to_z(double2 x, double radius, bool pinned)
     return make_double2(0.0, 0.0);
 }
 
-// dE/dz from dE/dx (chain rule of the map above; cf. the paper's dE/dt, dE/du).
-__device__ __forceinline__ double2 grad_z(double2 z, double2 g, double radius, bool pinned)
+// dE/dz from dE/dx by the chain rule of the map above; for (t, u) these are
+// the paper's dE/dt = (E_x cos u + E_y sin u) radius sin 2t,
+// dE/du = -E_x r sin u + E_y r cos u (pinned: r = 1, and 0 for the unused second variable).
+__device__ __forceinline__ double2 grad_z(double2 z, double2 g, double radius, bool pinned, bool tu)
 {
+    if (tu) {
+        if (pinned) return make_double2(-g.x * sin(z.x) + g.y * cos(z.x), 0.0);
+        const double c = cos(z.y), sn = sin(z.y), st = sin(z.x);
+        const double r = radius * st * st;
+        return make_double2((g.x * c + g.y * sn) * radius * sin(2.0 * z.x), (-g.x * sn + g.y * c) * r);
+    }
     double rho = sqrt(z.x * z.x + z.y * z.y);
     if (rho == 0.0) return pinned ? make_double2(0.0, 0.0) : make_double2(radius * g.x, radius * g.y);
     double ux = z.x / rho, uy = z.y / rho;
@@ -189,8 +213,8 @@ __global__ void k_rows_init(RelaxDev d, int64_t n, double radius, int lbfgs)
         else if (!inside(x.x, x.y)) set_status(d.st, ST_OUTSIDE);
         if (lbfgs) {
             const bool pinned = d.flags && d.flags[j];
-            double2 z = x_to_z(x, radius, pinned);
-            x = z_to_x(z, radius, pinned);
+            double2 z = x_to_z(x, radius, pinned, d.tu);
+            x = z_to_x(z, radius, pinned, d.tu);
             d.z[rr] = z;
         }
         if (d.x) d.x[rr] = x;
@@ -328,7 +352,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
         if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
         const double2 z = d.z[row];
-        double2 gz = grad_z(z, g, sp.radius, pinned);
+        double2 gz = grad_z(z, g, sp.radius, pinned, d.tu);
         d.q[row] = gz;
         acc[0] += gz.x * gz.x + gz.y * gz.y;
         if (k > 0) {
@@ -470,7 +494,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
         if (d.xold) d.xold[row] = d.x[row];
         double2 zn = make_double2(z.x + alpha * dv.x, z.y + alpha * dv.y);
         d.z[row] = zn;
-        double2 xn = z_to_x(zn, sp.radius, pinned);
+        double2 xn = z_to_x(zn, sp.radius, pinned, d.tu);
         d.x[row] = xn;
         d.xs[row] = split4(xn.x, xn.y);
         if (d.x3) d.x3[row] = split3(xn.x, xn.y);
@@ -540,7 +564,7 @@ __global__ void __launch_bounds__(kUpd) k_lb_grad(RelaxDev d, LbArgs la, const d
         if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
         const double2 z = d.z[row];
-        const double2 gz = grad_z(z, g, sp.radius, pinned);
+        const double2 gz = grad_z(z, g, sp.radius, pinned, d.tu);
         d.q[row] = gz;
         acc[0] += gz.x * gz.x + gz.y * gz.y;
         if (k > 0) {
@@ -775,7 +799,7 @@ __global__ void __launch_bounds__(kUpd) k_lb_step(RelaxDev d, LbArgs la, StepPar
         }
         const double2 zn = make_double2(z.x + c.alpha * dv.x, z.y + c.alpha * dv.y);
         d.z[row] = zn;
-        const double2 xn = z_to_x(zn, sp.radius, pinned);
+        const double2 xn = z_to_x(zn, sp.radius, pinned, d.tu);
         d.x[row] = xn;
         d.xs[row] = split4(xn.x, xn.y);
         if (d.x3) d.x3[row] = split3(xn.x, xn.y);
@@ -907,7 +931,7 @@ __global__ void k_ls_move(RelaxDev d, double radius)
         const double2 zk = d.xp[rr], dv = d.q[rr];
         const double2 zn = make_double2(zk.x + alpha * dv.x, zk.y + alpha * dv.y);
         d.z[rr] = zn;
-        const double2 xn = z_to_x(zn, radius, pinned);
+        const double2 xn = z_to_x(zn, radius, pinned, d.tu);
         d.x[rr] = xn;
         d.xs[rr] = split4(xn.x, xn.y);
         if (d.x3) d.x3[rr] = split3(xn.x, xn.y);
@@ -1039,13 +1063,14 @@ static tc_status check_params(const tc_relax_params* prm)
     if (prm->precision != TC_FP64 && prm->precision != TC_MIXED && prm->precision != TC_F64X) return TC_ERR_INVALID_ARG;
     if (prm->polish_precision != TC_FP64 && prm->polish_precision != TC_F64X) return TC_ERR_INVALID_ARG;
     if (prm->line_search < 0 || prm->line_search > 30) return TC_ERR_INVALID_ARG;
-    if (prm->optimizer < TC_OPT_GD || prm->optimizer > TC_OPT_LBFGS) return TC_ERR_INVALID_ARG;
+    if (prm->optimizer < TC_OPT_GD || prm->optimizer > TC_OPT_LBFGS_TU) return TC_ERR_INVALID_ARG;
+    const bool lbfgs = prm->optimizer == TC_OPT_LBFGS || prm->optimizer == TC_OPT_LBFGS_TU;
     if (prm->n_steps < 0 || prm->polish_steps < 0) return TC_ERR_INVALID_ARG;
-    if (prm->optimizer == TC_OPT_LBFGS && (prm->memory < 1 || prm->memory > kMaxMem)) return TC_ERR_INVALID_ARG;
+    if (lbfgs && (prm->memory < 1 || prm->memory > kMaxMem)) return TC_ERR_INVALID_ARG;
     if (!(prm->radius > 0.0) || !(prm->step0 > 0.0)) return TC_ERR_INVALID_ARG;
     if (prm->optimizer == TC_OPT_BB && !(prm->alpha_max >= prm->alpha_min && prm->alpha_min >= 0.0))
         return TC_ERR_INVALID_ARG;
-    if (prm->optimizer == TC_OPT_LBFGS && !(prm->maxstep > 0.0)) return TC_ERR_INVALID_ARG;
+    if (lbfgs && !(prm->maxstep > 0.0)) return TC_ERR_INVALID_ARG;
     if (!(prm->gtol >= 0.0) || !(prm->polish_gtol >= 0.0)) return TC_ERR_INVALID_ARG;
     return TC_OK;
 }
@@ -1151,7 +1176,7 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
         e = launch_pass<KIND, false, true>(a, G, 0, 0, cap);
         if (e != cudaSuccess) break;
         if (prof) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 1), cap);
-        if (sp.opt == TC_OPT_LBFGS) {
+        if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
             k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
             for (size_t q = 0; q < large.ids.size(); ++q) {
                 LbArgs la{large.ids[q], large.part, large.sc + q};
@@ -1171,7 +1196,7 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
     if (e == cudaSuccess) {
         StepParams sm = sp;
         sm.measure = 1;
-        if (sp.opt == TC_OPT_LBFGS) {
+        if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
             k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sm);
             for (size_t q = 0; q < large.ids.size(); ++q) {
                 LbArgs la{large.ids[q], large.part, large.sc + q};
@@ -1285,7 +1310,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     P.M = rows;
     plan_units(P);
     const int prec = prm->precision;
-    const bool lbfgs = prm->optimizer == TC_OPT_LBFGS;
+    const bool lbfgs = prm->optimizer == TC_OPT_LBFGS || prm->optimizer == TC_OPT_LBFGS_TU;
     const int mem = lbfgs ? prm->memory : 0;
     const int64_t G_bulk = prec == TC_MIXED  ? pass_grid<PASS_MIXED, false, true>(P.W)
                            : prec == TC_F64X ? pass_grid<PASS_F64X, false, true>(P.W)
@@ -1380,6 +1405,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     d.flags = flags;
     d.pos = reinterpret_cast<double2*>(pos);
     d.st = st;
+    d.tu = prm->optimizer == TC_OPT_LBFGS_TU ? 1 : 0;
 
     cudaError_t e = cudaSuccess;
     if (prof) cudaEventRecord(ev_a, s);

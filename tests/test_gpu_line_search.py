@@ -89,3 +89,69 @@ def test_line_search_mixed_subdomains_lower_energy():
     d = r.delta_e.cpu().numpy()
     assert np.all(d[st != 2] < 0)
     assert (st == 1).sum() >= 1
+
+
+# ------------------------------------------ L-BFGS on the paper's (t, u) variables ---
+
+@pytest.mark.parametrize("line_search", [0, 8])
+def test_lbfgs_tu_instances_match_oracle(line_search):
+    """L-BFGS on (t, u) (Sec. II D) follows the oracle's iteration; CUDA's and the host's sin, cos,
+    asin and atan2 may differ in the last place, which the 1e-9 trajectory tolerance absorbs."""
+    sizes = [60, 150, 333]
+    pos = np.concatenate([synth.arcsine_disk(m, 50 + m) for m in sizes])
+    world = np.array([[0, 60], [60, 210], [210, 543]], dtype=np.int64)
+    p = T(pos.copy())
+    iters = 25
+    r = tc.relax_subdomains(p, world=T(world), precision="fp64", optimizer="lbfgs_tu", n_steps=iters, memory=8,
+                            step0=1e-4, maxstep=0.02, accept=False, want_energy=True, line_search=line_search)
+    tc.sync_status()
+    x = p.cpu().numpy()
+    for k, (b, e) in enumerate(world):
+        xo, it, rms = oracle.lbfgs(pos[b:e], memory=8, max_iter=iters, gtol=0.0, step0=1e-4, maxstep=0.02,
+                                   line_search=line_search, tu=True)
+        assert np.abs(x[b:e] - xo).max() <= 1e-9
+        eg = oracle.energy(x[b:e])
+        assert abs(r.energy[k].item() - eg) <= 1e-12 * eg
+        assert abs(r.rms[k].item() - rms) <= 1e-6 * rms
+
+
+def test_lbfgs_tu_pinned_boundary_matches_oracle():
+    """Pinned charges on (cos u, sin u), the others on r = sigma sin^2 t: float64 trajectory parity."""
+    n = 300
+    pos = synth.arcsine_disk(n, 17)
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), 0.97)
+    p = T(p0.copy())
+    world = T(np.array([[0, n]], dtype=np.int64))
+    iters = 40
+    r = tc.relax_subdomains(p, world=world, flags=T(f), precision="fp64", optimizer="lbfgs_tu", n_steps=iters,
+                            memory=8, step0=1e-4, maxstep=0.02, radius=0.97, accept=False)
+    tc.sync_status()
+    x = p.cpu().numpy()
+    xo, _, rms = oracle.lbfgs(p0, memory=8, max_iter=iters, step0=1e-4, maxstep=0.02, radius=0.97, flags=f, tu=True)
+    assert np.abs(x - xo).max() <= 1e-9
+    assert abs(r.rms[0].item() - rms) <= 1e-6 * rms
+    rr = np.hypot(x[:, 0], x[:, 1])
+    assert np.all(np.abs(rr[f == 1] - 1.0) <= 4.5e-16)
+    assert np.all(rr[f == 0] <= 0.97 * (1 + 1e-15))
+
+
+def test_lbfgs_tu_mixed_with_polish_keeps_constraints():
+    """A mixed (t, u) run polished in float64 keeps the constraints and lowers the energy.  (t, u)
+    converges slowly here (the oracle needs about 3000 iterations for an RMS of 4e-4), so no
+    stationarity is asserted."""
+    n = 300
+    pos = synth.arcsine_disk(n, 17)
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), 0.97)
+    p = T(p0.copy())
+    world = T(np.array([[0, n]], dtype=np.int64))
+    r = tc.relax_subdomains(p, world=world, flags=T(f), precision="mixed", optimizer="lbfgs_tu", n_steps=200,
+                            memory=8, step0=1e-4, maxstep=0.02, radius=0.97, gtol=1e-3, polish_steps=200,
+                            polish_gtol=1e-9, accept=False, want_energy=True)
+    tc.sync_status()
+    x = p.cpu().numpy()
+    rr = np.hypot(x[:, 0], x[:, 1])
+    assert np.all(np.abs(rr[f == 1] - 1.0) <= 4.5e-16)
+    assert np.all(rr[f == 0] <= 0.97 * (1 + 1e-15))
+    eg = oracle.energy(x)
+    assert eg < oracle.energy(p0)
+    assert abs(r.energy[0].item() - eg) <= 1e-12 * eg

@@ -660,3 +660,29 @@ def test_lbfgs_line_search_is_monotone_and_converges():
     assert rms < 1e-10
     _, rms_c, _ = oracle.projected_grad(x, oracle.grad(x))
     assert rms_c < 1e-9
+
+
+@pytest.mark.parametrize("n,expect", [(3, math.sqrt(3)), (4, 1 + 2 * math.sqrt(2)), (5, 6.881909602355867)])
+def test_lbfgs_tu_reaches_ring_minima(n, expect):
+    """L-BFGS on the paper's (t, u) variables (Sec. II D) relaxes small N to the regular polygon on the
+    circle, the same minimum the smooth-map iteration finds, and ends float64-stationary."""
+    pos = synth.arcsine_disk(n, 3)
+    x, it, rms = oracle.lbfgs(pos, max_iter=3000, gtol=1e-10, step0=1e-3, maxstep=0.05, tu=True)
+    assert rms < 1e-10
+    assert abs(oracle.energy(x) - expect) <= 1e-12 * expect
+    _, rms_c, _ = oracle.projected_grad(x, oracle.grad(x))
+    assert rms_c < 1e-8
+    x2, _, _ = oracle.lbfgs(pos, max_iter=3000, gtol=1e-10, step0=1e-3, maxstep=0.05)
+    assert abs(oracle.energy(x2) - oracle.energy(x)) <= 1e-12 * expect
+
+
+def test_lbfgs_tu_with_pinned_boundary():
+    """Pinned charges move along the unit circle as (cos u, sin u); the others stay inside sigma."""
+    n = 80
+    pos = synth.arcsine_disk(n, 9)
+    p0, f = oracle.border_split(pos, 12, 0.95)
+    x, it, rms = oracle.lbfgs(p0, max_iter=300, step0=1e-3, maxstep=0.05, radius=0.95, flags=f, tu=True)
+    r = np.hypot(x[:, 0], x[:, 1])
+    assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
+    assert np.all(r[f == 0] <= 0.95 * (1 + 1e-15))
+    assert oracle.energy(x) < oracle.energy(p0)
