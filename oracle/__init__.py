@@ -62,6 +62,10 @@ def lib(openmp: bool = False) -> C.CDLL:
             "tco_accept_sequential": [vp, i64, vp, vp, i64, vp, vp, vp],
             "tco_lbfgs": [vp, i64, i64, i64, d, d, d, d, vp, vp, vp],
             "tco_lbfgs_ls": [vp, i64, i64, i64, d, d, d, d, vp, i64, i64, vp, vp],
+            "tco_lbfgsb": [vp, i64, i64, i64, d, d, d, d, vp, i64, vp, vp, vp],
+            "tco_lbfgsb_middle": [i64, vp, vp, i64, d, vp],
+            "tco_lbfgsb_cauchy": [i64, vp, vp, vp, vp, i64, vp, vp, d, vp, vp, vp, vp],
+            "tco_lbfgsb_subspace": [i64, vp, vp, vp, vp, i64, vp, vp, d, vp, vp, vp, vp],
             "tco_threads": [],
             "tco_zone_select": [vp, i64, vp, vp, d, d, d, d, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp],
             "tco_cycle": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, vp, d, d, d, i64, vp, vp, vp],
@@ -229,6 +233,57 @@ def lbfgs(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: 
                               float(maxstep), float(radius), _p(f), int(line_search), int(bool(tu)), _p(it),
                               _p(rms)), "lbfgs")
     return p, int(it[0]), float(rms[0])
+
+
+def lbfgsb(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: float = 1e-4,
+           maxstep: float = 1e-2, radius: float = 1.0, flags=None, line_search: int = 0):
+    """L-BFGS-B on the (t, u) variables with the box t in [0, pi/2]; returns (x, iterations, final
+    projected-gradient RMS, breakpoints passed by the Cauchy searches)."""
+    p = _pos(pos).copy()
+    f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+    it = np.zeros(1, dtype=np.int64)
+    nb = np.zeros(1, dtype=np.int64)
+    rms = np.zeros(1)
+    _check(lib().tco_lbfgsb(_p(p), p.shape[0], int(memory), int(max_iter), float(gtol), float(step0),
+                            float(maxstep), float(radius), _p(f), int(line_search), _p(it), _p(rms), _p(nb)),
+           "lbfgsb")
+    return p, int(it[0]), float(rms[0]), int(nb[0])
+
+
+def _vecs(*arrs):
+    return [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in arrs]
+
+
+def lbfgsb_middle(S, Y, theta: float):
+    """M = K^{-1} of the compact representation B = theta I - W M W^T (rows of S, Y: pairs, oldest first)."""
+    S, Y = _vecs(S, Y)
+    h, nv = S.shape
+    M = np.zeros((2 * h, 2 * h))
+    _check(lib().tco_lbfgsb_middle(h, _p(S), _p(Y), nv, float(theta), _p(M)), "lbfgsb_middle")
+    return M
+
+
+def lbfgsb_cauchy(x, g, lo, hi, S, Y, theta: float, M):
+    """Generalized Cauchy point: returns (xc, c = W^T (xc - x), breakpoints passed)."""
+    x, g, lo, hi, S, Y, M = _vecs(x, g, lo, hi, S, Y, M)
+    h = S.shape[0] if S.ndim == 2 else 0
+    xc = np.zeros_like(x)
+    c = np.zeros(max(2 * h, 1))
+    nb = np.zeros(1, dtype=np.int64)
+    _check(lib().tco_lbfgsb_cauchy(x.size, _p(x), _p(g), _p(lo), _p(hi), h, _p(S), _p(Y), float(theta), _p(M),
+                                   _p(xc), _p(c), _p(nb)), "lbfgsb_cauchy")
+    return xc, c[:2 * h], int(nb[0])
+
+
+def lbfgsb_subspace(x, g, lo, hi, S, Y, theta: float, M, xc, c):
+    """Subspace minimisation from the Cauchy point xc: returns xbar."""
+    x, g, lo, hi, S, Y, M, xc = _vecs(x, g, lo, hi, S, Y, M, xc)
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+    h = S.shape[0] if S.ndim == 2 else 0
+    xbar = np.zeros_like(x)
+    _check(lib().tco_lbfgsb_subspace(x.size, _p(x), _p(g), _p(lo), _p(hi), h, _p(S), _p(Y), float(theta), _p(M),
+                                     _p(xc), _p(c if c.size else np.zeros(1)), _p(xbar)), "lbfgsb_subspace")
+    return xbar
 
 
 def zone_size(q: int, m_min: int, m_max: int, period: int, n: int) -> int:

@@ -735,6 +735,441 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
     return st;
 }
 
+/* ------------------------------------------------------------ L-BFGS-B --- */
+
+/* Sec. II C step 4 optimises each subdomain with L-BFGS-B (Byrd, Lu, Nocedal &
+ * Zhu 1995) on the variables of Sec. II D.  The pieces below follow that
+ * method; the variables are nv = 2n numbers, the box is lo <= v <= hi
+ * (+-INFINITY for an unbounded side), and h stored pairs (s_a, y_a), a = 0 the
+ * oldest, are rows of S and Y (h x nv).
+ *
+ * Compact representation (Byrd, Nocedal & Schnabel 1994, Thm 2.3) of the BFGS
+ * matrix built from theta I by the h updates:
+ *     B = theta I - W M W^T,  W = [Y^T, theta S^T] (nv x 2h),
+ *     M = K^{-1},  K = [[-D, L^T], [L, theta S S^T]],
+ * D = diag(s_a . y_a), L_ab = s_a . y_b for a > b (else 0). */
+
+static double tco_wrow(int64_t h, const double* S, const double* Y, int64_t nv, double theta, int64_t i, int64_t a)
+{
+    /* element (i, a) of W */
+    return a < h ? Y[a * nv + i] : theta * S[(a - h) * nv + i];
+}
+
+/* M = K^{-1} by Gauss-Jordan elimination with partial pivoting on [K | I]. */
+int tco_lbfgsb_middle(int64_t h, const double* S, const double* Y, int64_t nv, double theta, double* M)
+{
+    if (h < 0 || nv < 0 || (h > 0 && (!S || !Y || !M))) return TCO_ERR_INVALID_ARG;
+    int64_t q = 2 * h;
+    if (q == 0) return TCO_OK;
+    double* A = (double*)calloc((size_t)(q * 2 * q), sizeof(double));
+    if (!A) return TCO_ERR_NO_MEMORY;
+    for (int64_t a = 0; a < h; ++a)
+        for (int64_t b = 0; b < h; ++b) {
+            double sy_ab = dot(S + a * nv, Y + b * nv, nv);
+            double ss_ab = dot(S + a * nv, S + b * nv, nv);
+            if (a == b) A[a * 2 * q + b] = -sy_ab;            /* -D */
+            if (a > b) A[(h + a) * 2 * q + b] = sy_ab;         /* L */
+            if (a > b) A[b * 2 * q + (h + a)] = sy_ab;         /* L^T */
+            A[(h + a) * 2 * q + (h + b)] = theta * ss_ab;      /* theta S S^T */
+        }
+    for (int64_t a = 0; a < q; ++a) A[a * 2 * q + q + a] = 1.0;
+    int st = TCO_OK;
+    for (int64_t col = 0; col < q && st == TCO_OK; ++col) {
+        int64_t piv = col;
+        for (int64_t r = col + 1; r < q; ++r)
+            if (fabs(A[r * 2 * q + col]) > fabs(A[piv * 2 * q + col])) piv = r;
+        if (!(fabs(A[piv * 2 * q + col]) > 0.0)) { st = TCO_ERR_NONFINITE; break; }
+        if (piv != col)
+            for (int64_t k = 0; k < 2 * q; ++k) {
+                double t = A[col * 2 * q + k];
+                A[col * 2 * q + k] = A[piv * 2 * q + k];
+                A[piv * 2 * q + k] = t;
+            }
+        double pv = A[col * 2 * q + col];
+        for (int64_t k = 0; k < 2 * q; ++k) A[col * 2 * q + k] /= pv;
+        for (int64_t r = 0; r < q; ++r) {
+            if (r == col) continue;
+            double f = A[r * 2 * q + col];
+            if (f != 0.0)
+                for (int64_t k = 0; k < 2 * q; ++k) A[r * 2 * q + k] -= f * A[col * 2 * q + k];
+        }
+    }
+    if (st == TCO_OK)
+        for (int64_t a = 0; a < q; ++a)
+            for (int64_t b = 0; b < q; ++b) M[a * q + b] = A[a * 2 * q + q + b];
+    free(A);
+    return st;
+}
+
+/* y = M x for the 2h x 2h matrix M. */
+static void tco_matvec(int64_t q, const double* M, const double* x, double* y)
+{
+    for (int64_t a = 0; a < q; ++a) {
+        double s = 0.0;
+        for (int64_t b = 0; b < q; ++b) s += M[a * q + b] * x[b];
+        y[a] = s;
+    }
+}
+
+typedef struct {
+    double t;
+    int64_t i;
+} brk_t;
+
+static int brk_cmp(const void* a, const void* b)
+{
+    const brk_t* p = (const brk_t*)a;
+    const brk_t* r = (const brk_t*)b;
+    if (p->t < r->t) return -1;
+    if (p->t > r->t) return 1;
+    return (p->i > r->i) - (p->i < r->i);
+}
+
+/* Generalized Cauchy point (Byrd et al. 1995, Sec. 4): the first local
+ * minimiser of the quadratic model m(v) = g.(v - x) + (v - x).B(v - x)/2 along
+ * the projected steepest-descent path v(t) = P(x - t g), t >= 0.
+ *   Breakpoint of variable i: t_i = (x_i - hi_i)/g_i (g_i < 0), (x_i - lo_i)/g_i
+ *   (g_i > 0), infinity otherwise; direction d_i = -g_i, or 0 where t_i = 0.
+ *   On the segment starting at t_old the model is f' dt + f'' dt^2 / 2 + const,
+ *   with f' = g.d + ... kept in closed form through p = W^T d and
+ *   c = W^T (v(t_old) - x):  initially p = W^T d, c = 0, f' = -d.d,
+ *   f'' = theta d.d - p.M p.  The breakpoints are visited in increasing
+ *   (t_i, i); while the segment minimiser dt* = -f'/f'' lies beyond the next
+ *   breakpoint b, variable b is fixed at its bound (z_b = bound - x_b) and
+ *       c += dt p,
+ *       f' += dt f'' + g_b^2 + theta g_b z_b - g_b w_b.M c,
+ *       f'' += -theta g_b^2 - 2 g_b w_b.M p - g_b^2 w_b.M w_b,
+ *       p += g_b w_b,  d_b = 0
+ *   (w_b = row b of W).  f'' is kept at least 2^-52 times its first value, as a
+ *   guard against rounding (B is positive definite, so f'' > 0 in exact
+ *   arithmetic while d != 0).  At the end dt* = max(dt*, 0), every variable not
+ *   fixed moves to x + (t_old + dt*) d, and c += dt* p.
+ * Writes xc (nv), c (2h) and the number of breakpoints passed (nullable). */
+int tco_lbfgsb_cauchy(int64_t nv, const double* x, const double* g, const double* lo, const double* hi, int64_t h,
+                      const double* S, const double* Y, double theta, const double* M, double* xc, double* c,
+                      int64_t* n_break)
+{
+    if (nv < 0 || h < 0 || !(theta > 0.0) || (nv > 0 && (!x || !g || !lo || !hi || !xc)) ||
+        (h > 0 && (!S || !Y || !M || !c)))
+        return TCO_ERR_INVALID_ARG;
+    int64_t q = 2 * h;
+    double* d = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
+    double* tb = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
+    unsigned char* fixed = (unsigned char*)calloc((size_t)(nv > 0 ? nv : 1), 1);
+    brk_t* br = (brk_t*)malloc(sizeof(brk_t) * (size_t)(nv > 0 ? nv : 1));
+    double p[64], wb[64], mv[64];
+    if (!d || !tb || !fixed || !br || q > 64) {
+        free(d); free(tb); free(fixed); free(br);
+        return q > 64 ? TCO_ERR_INVALID_ARG : TCO_ERR_NO_MEMORY;
+    }
+    int64_t nb = 0, passed = 0;
+    acc_t dd = {0.0, 0.0};
+    for (int64_t i = 0; i < nv; ++i) {
+        double t = INFINITY;
+        if (g[i] < 0.0 && hi[i] < INFINITY) t = (x[i] - hi[i]) / g[i];
+        else if (g[i] > 0.0 && lo[i] > -INFINITY) t = (x[i] - lo[i]) / g[i];
+        tb[i] = t;
+        d[i] = t == 0.0 ? 0.0 : -g[i];
+        acc_add(&dd, d[i] * d[i]);
+        if (t > 0.0 && t < INFINITY) { br[nb].t = t; br[nb].i = i; ++nb; }
+    }
+    for (int64_t a = 0; a < q; ++a) {
+        acc_t s = {0.0, 0.0};
+        for (int64_t i = 0; i < nv; ++i) acc_add(&s, tco_wrow(h, S, Y, nv, theta, i, a) * d[i]);
+        p[a] = acc_get(&s);
+        c[a] = 0.0;
+    }
+    double fp = -acc_get(&dd);
+    tco_matvec(q, M, p, mv);
+    double pmp = 0.0;
+    for (int64_t a = 0; a < q; ++a) pmp += p[a] * mv[a];
+    double fpp = -theta * fp - pmp;
+    const double fpp0 = fpp;
+    double told = 0.0, dtm = 0.0;
+    if (fpp0 > 0.0) {
+        dtm = -fp / fpp;
+        qsort(br, (size_t)nb, sizeof(brk_t), brk_cmp);
+        for (int64_t k = 0; k < nb; ++k) {
+            int64_t b = br[k].i;
+            double t = br[k].t, dt = t - told;
+            if (dtm < dt) break;
+            double xb = d[b] > 0.0 ? hi[b] : lo[b];
+            double zb = xb - x[b], gb = g[b];
+            for (int64_t a = 0; a < q; ++a) { c[a] += dt * p[a]; wb[a] = tco_wrow(h, S, Y, nv, theta, b, a); }
+            double wMc = 0.0, wMp = 0.0, wMw = 0.0;
+            tco_matvec(q, M, c, mv);
+            for (int64_t a = 0; a < q; ++a) wMc += wb[a] * mv[a];
+            tco_matvec(q, M, p, mv);
+            for (int64_t a = 0; a < q; ++a) wMp += wb[a] * mv[a];
+            tco_matvec(q, M, wb, mv);
+            for (int64_t a = 0; a < q; ++a) wMw += wb[a] * mv[a];
+            fp = fp + dt * fpp + gb * gb + theta * gb * zb - gb * wMc;
+            fpp = fpp - theta * gb * gb - 2.0 * gb * wMp - gb * gb * wMw;
+            if (fpp < 0x1p-52 * fpp0) fpp = 0x1p-52 * fpp0;
+            for (int64_t a = 0; a < q; ++a) p[a] += gb * wb[a];
+            d[b] = 0.0;
+            fixed[b] = 1;
+            xc[b] = xb;
+            dtm = -fp / fpp;
+            told = t;
+            ++passed;
+        }
+        if (dtm < 0.0) dtm = 0.0;
+        told += dtm;
+        for (int64_t a = 0; a < q; ++a) c[a] += dtm * p[a];
+    }
+    for (int64_t i = 0; i < nv; ++i)
+        if (!fixed[i]) xc[i] = fpp0 > 0.0 ? x[i] + told * d[i] : x[i];
+    if (n_break) *n_break = passed;
+    free(d); free(tb); free(fixed); free(br);
+    return TCO_OK;
+}
+
+/* Subspace minimisation, direct primal method (Byrd et al. 1995, Sec. 5.1).
+ * Free variables F = { i : lo_i < xc_i < hi_i }; with Z selecting them:
+ *     r = Z^T (g + theta (xc - x) - W M c)          (reduced model gradient at xc)
+ *     v = M (W_F^T r),   N = I - M (W_F^T W_F) / theta,   v <- N^{-1} v
+ *     du = -r / theta - W_F v / theta^2              (= -(Z^T B Z)^{-1} r)
+ *     a* = max { a <= 1 : lo_i <= xc_i + a du_i <= hi_i, i in F }
+ *     xbar = xc + a* du on F, xc elsewhere.
+ * N^{-1} v is a Gauss elimination with partial pivoting. */
+int tco_lbfgsb_subspace(int64_t nv, const double* x, const double* g, const double* lo, const double* hi, int64_t h,
+                        const double* S, const double* Y, double theta, const double* M, const double* xc,
+                        const double* c, double* xbar)
+{
+    if (nv < 0 || h < 0 || !(theta > 0.0) || (nv > 0 && (!x || !g || !lo || !hi || !xc || !xbar)) ||
+        (h > 0 && (!S || !Y || !M || !c)) || h > 32)
+        return TCO_ERR_INVALID_ARG;
+    int64_t q = 2 * h;
+    double Mc[64], v[64], wi[64], A[64 * 64], N[64 * 65];
+    double* r = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
+    if (!r) return TCO_ERR_NO_MEMORY;
+    tco_matvec(q, M, c, Mc);
+    acc_t va[64], Aa[64 * 64];
+    for (int64_t a = 0; a < q; ++a) { va[a].s = va[a].c = 0.0; for (int64_t b = 0; b < q; ++b) Aa[a * q + b].s = Aa[a * q + b].c = 0.0; }
+    for (int64_t i = 0; i < nv; ++i) {
+        r[i] = 0.0;
+        if (!(lo[i] < xc[i] && xc[i] < hi[i])) continue;
+        double wMc = 0.0;
+        for (int64_t a = 0; a < q; ++a) { wi[a] = tco_wrow(h, S, Y, nv, theta, i, a); wMc += wi[a] * Mc[a]; }
+        r[i] = g[i] + theta * (xc[i] - x[i]) - wMc;
+        for (int64_t a = 0; a < q; ++a) {
+            acc_add(&va[a], wi[a] * r[i]);
+            for (int64_t b = 0; b < q; ++b) acc_add(&Aa[a * q + b], wi[a] * wi[b]);
+        }
+    }
+    double wv[64];
+    for (int64_t a = 0; a < q; ++a) {
+        wv[a] = acc_get(&va[a]);
+        for (int64_t b = 0; b < q; ++b) A[a * q + b] = acc_get(&Aa[a * q + b]);
+    }
+    tco_matvec(q, M, wv, v);
+    /* N = I - M A / theta, augmented with v */
+    for (int64_t a = 0; a < q; ++a) {
+        for (int64_t b = 0; b < q; ++b) {
+            double s = 0.0;
+            for (int64_t k = 0; k < q; ++k) s += M[a * q + k] * A[k * q + b];
+            N[a * (q + 1) + b] = (a == b ? 1.0 : 0.0) - s / theta;
+        }
+        N[a * (q + 1) + q] = v[a];
+    }
+    int st = TCO_OK;
+    for (int64_t col = 0; col < q; ++col) {
+        int64_t piv = col;
+        for (int64_t rr = col + 1; rr < q; ++rr)
+            if (fabs(N[rr * (q + 1) + col]) > fabs(N[piv * (q + 1) + col])) piv = rr;
+        if (!(fabs(N[piv * (q + 1) + col]) > 0.0)) { st = TCO_ERR_NONFINITE; break; }
+        if (piv != col)
+            for (int64_t k = 0; k <= q; ++k) {
+                double t = N[col * (q + 1) + k];
+                N[col * (q + 1) + k] = N[piv * (q + 1) + k];
+                N[piv * (q + 1) + k] = t;
+            }
+        for (int64_t rr = col + 1; rr < q; ++rr) {
+            double f = N[rr * (q + 1) + col] / N[col * (q + 1) + col];
+            for (int64_t k = col; k <= q; ++k) N[rr * (q + 1) + k] -= f * N[col * (q + 1) + k];
+        }
+    }
+    if (st == TCO_OK) {
+        for (int64_t a = q - 1; a >= 0; --a) {
+            double s = N[a * (q + 1) + q];
+            for (int64_t k = a + 1; k < q; ++k) s -= N[a * (q + 1) + k] * v[k];
+            v[a] = s / N[a * (q + 1) + a];
+        }
+        double astar = 1.0;
+        for (int64_t i = 0; i < nv; ++i) {
+            if (!(lo[i] < xc[i] && xc[i] < hi[i])) continue;
+            double wv2 = 0.0;
+            for (int64_t a = 0; a < q; ++a) wv2 += tco_wrow(h, S, Y, nv, theta, i, a) * v[a];
+            double du = -r[i] / theta - wv2 / (theta * theta);
+            r[i] = du;
+            if (du > 0.0 && hi[i] < INFINITY && (hi[i] - xc[i]) / du < astar) astar = (hi[i] - xc[i]) / du;
+            if (du < 0.0 && lo[i] > -INFINITY && (lo[i] - xc[i]) / du < astar) astar = (lo[i] - xc[i]) / du;
+        }
+        for (int64_t i = 0; i < nv; ++i)
+            xbar[i] = (lo[i] < xc[i] && xc[i] < hi[i]) ? xc[i] + astar * r[i] : xc[i];
+    }
+    free(r);
+    return st;
+}
+
+/* Box of the (t, u) variables: a free charge (t, u) has t in [0, pi/2] (the
+ * range of Sec. II D, on which r = sigma sin^2 t covers [0, sigma] once) and u
+ * unbounded; a pinned charge (u, 0) has u unbounded and its unused second
+ * variable fixed at 0. */
+static const double TCO_HALF_PI = 1.5707963267948966;
+
+static void tu_box(int64_t n, const unsigned char* flags, double* lo, double* hi)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (flags && flags[i]) {
+            lo[2 * i] = -INFINITY; hi[2 * i] = INFINITY;
+            lo[2 * i + 1] = 0.0; hi[2 * i + 1] = 0.0;
+        } else {
+            lo[2 * i] = 0.0; hi[2 * i] = TCO_HALF_PI;
+            lo[2 * i + 1] = -INFINITY; hi[2 * i + 1] = INFINITY;
+        }
+    }
+}
+
+static void box_clamp(double* v, const double* lo, const double* hi, int64_t nv)
+{
+    for (int64_t i = 0; i < nv; ++i) v[i] = v[i] < lo[i] ? lo[i] : (v[i] > hi[i] ? hi[i] : v[i]);
+}
+
+/* RMS over charges of the projected gradient P(v - g) - v. */
+static double proj_rms(const double* v, const double* g, const double* lo, const double* hi, int64_t n)
+{
+    acc_t s = {0.0, 0.0};
+    for (int64_t i = 0; i < 2 * n; ++i) {
+        double w = v[i] - g[i];
+        w = w < lo[i] ? lo[i] : (w > hi[i] ? hi[i] : w);
+        acc_add(&s, (w - v[i]) * (w - v[i]));
+    }
+    return n > 0 ? sqrt(acc_get(&s) / (double)n) : 0.0;
+}
+
+/* L-BFGS-B on the (t, u) variables of Sec. II D over all n charges of one
+ * configuration (Sec. II C step 4 applies it to a subdomain).  Iteration with
+ * at most `memory` pairs:
+ *   stop when the projected-gradient RMS < gtol;
+ *   theta = y.y / s.y of the newest pair (1 / step0 without pairs);
+ *   xc = generalized Cauchy point, xbar = subspace minimiser (above);
+ *   d = xbar - v; if g.d >= 0 the pairs are dropped and d = P(v - step0 g) - v;
+ *   alpha = min(1, maxstep / max_i |d_i|) (|d_i| of charge i's two variables);
+ *   v+ = P(v + alpha d), with the Armijo halving of tco_lbfgs_ls when
+ *   max_halvings > 0 (energy change as pair differences);
+ *   the pair (v+ - v, g+ - g) is kept iff s.y > 1e-12 |s||y|.
+ * pos (in/out): x of the final variables.  Reports iterations, the final
+ * projected-gradient RMS and the number of breakpoints the Cauchy searches
+ * passed (each nullable). */
+int tco_lbfgsb(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol, double step0, double maxstep,
+               double sigma, const unsigned char* flags, int64_t max_halvings, int64_t* iters_out, double* rms_out,
+               int64_t* breaks_out)
+{
+    if (n < 0 || memory < 1 || memory > 32 || max_iter < 0 || max_halvings < 0 || (n > 0 && !pos) ||
+        !(sigma > 0.0) || !(step0 > 0.0) || !(maxstep > 0.0))
+        return TCO_ERR_INVALID_ARG;
+    int64_t L = 2 * n;
+    size_t sz = sizeof(double) * (size_t)(L > 0 ? L : 1);
+    double *xk = malloc(sz), *v = malloc(sz), *vn = malloc(sz), *g = malloc(sz), *gv = malloc(sz),
+           *gvn = malloc(sz), *d = malloc(sz), *lo = malloc(sz), *hi = malloc(sz), *xc = malloc(sz),
+           *xbar = malloc(sz);
+    double* S = malloc(sz * (size_t)memory);
+    double* Y = malloc(sz * (size_t)memory);
+    double* So = malloc(sz * (size_t)memory);
+    double* Yo = malloc(sz * (size_t)memory);
+    double M[64 * 64], c[64];
+    int st = TCO_OK;
+    if (!xk || !v || !vn || !g || !gv || !gvn || !d || !lo || !hi || !xc || !xbar || !S || !Y || !So || !Yo)
+        st = TCO_ERR_NO_MEMORY;
+    int64_t hist = 0, head = 0, it = 0, breaks = 0;
+    double rms = 0.0, theta = 1.0 / step0;
+    if (!st) {
+        tu_box(n, flags, lo, hi);
+        x_to_tu(pos, n, sigma, flags, v);
+        box_clamp(v, lo, hi, L);
+        tu_to_x(v, n, sigma, flags, pos);
+        st = tco_grad(pos, n, g);
+    }
+    if (!st) {
+        grad_tu(v, g, n, sigma, flags, gv);
+        rms = proj_rms(v, gv, lo, hi, n);
+    }
+    for (; !st && it < max_iter; ++it) {
+        if (rms < gtol) break;
+        for (int64_t a = 0; a < hist; ++a) { /* oldest first */
+            int64_t j = ((head - hist + a) % memory + memory) % memory;
+            memcpy(So + a * L, S + j * L, sz);
+            memcpy(Yo + a * L, Y + j * L, sz);
+        }
+        int64_t nbk = 0;
+        st = tco_lbfgsb_middle(hist, So, Yo, L, theta, M);
+        if (!st) st = tco_lbfgsb_cauchy(L, v, gv, lo, hi, hist, So, Yo, theta, M, xc, c, &nbk);
+        if (!st) st = tco_lbfgsb_subspace(L, v, gv, lo, hi, hist, So, Yo, theta, M, xc, c, xbar);
+        if (st) break;
+        breaks += nbk;
+        for (int64_t i = 0; i < L; ++i) d[i] = xbar[i] - v[i];
+        if (dot(gv, d, L) >= 0.0) {
+            hist = 0;
+            head = 0;
+            theta = 1.0 / step0;
+            for (int64_t i = 0; i < L; ++i) {
+                double w = v[i] - step0 * gv[i];
+                w = w < lo[i] ? lo[i] : (w > hi[i] ? hi[i] : w);
+                d[i] = w - v[i];
+            }
+        }
+        double dmax = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double a = sqrt(d[2 * i] * d[2 * i] + d[2 * i + 1] * d[2 * i + 1]);
+            if (a > dmax) dmax = a;
+        }
+        double alpha = (dmax > maxstep) ? maxstep / dmax : 1.0;
+        for (int64_t i = 0; i < L; ++i) vn[i] = v[i] + alpha * d[i];
+        box_clamp(vn, lo, hi, L);
+        if (max_halvings > 0) {
+            memcpy(xk, pos, sz);
+            const double gd = dot(gv, d, L);
+            for (int64_t hh = 0;; ++hh) {
+                tu_to_x(vn, n, sigma, flags, pos);
+                if (instance_delta(xk, pos, n) <= 1e-4 * alpha * gd || hh == max_halvings) break;
+                alpha *= 0.5;
+                for (int64_t i = 0; i < L; ++i) vn[i] = v[i] + alpha * d[i];
+                box_clamp(vn, lo, hi, L);
+            }
+        } else {
+            tu_to_x(vn, n, sigma, flags, pos);
+        }
+        st = tco_grad(pos, n, g);
+        if (st) break;
+        grad_tu(vn, g, n, sigma, flags, gvn);
+        rms = proj_rms(vn, gvn, lo, hi, n);
+        acc_t sy_a = {0.0, 0.0}, ss_a = {0.0, 0.0}, yy_a = {0.0, 0.0};
+        for (int64_t i = 0; i < L; ++i) {
+            double si = vn[i] - v[i], yi = gvn[i] - gv[i];
+            acc_add(&sy_a, si * yi);
+            acc_add(&ss_a, si * si);
+            acc_add(&yy_a, yi * yi);
+        }
+        double sy = acc_get(&sy_a);
+        if (sy > 1e-12 * sqrt(acc_get(&ss_a)) * sqrt(acc_get(&yy_a))) {
+            for (int64_t i = 0; i < L; ++i) { S[head * L + i] = vn[i] - v[i]; Y[head * L + i] = gvn[i] - gv[i]; }
+            theta = acc_get(&yy_a) / sy;
+            head = (head + 1) % memory;
+            if (hist < memory) ++hist;
+        }
+        memcpy(v, vn, sz);
+        memcpy(gv, gvn, sz);
+    }
+    if (iters_out) *iters_out = it;
+    if (rms_out) *rms_out = rms;
+    if (breaks_out) *breaks_out = breaks;
+    free(xk); free(v); free(vn); free(g); free(gv); free(gvn); free(d); free(lo); free(hi); free(xc); free(xbar);
+    free(S); free(Y); free(So); free(Yo);
+    return st;
+}
+
 /* ------------------------------------------------ adaptive subdomains --- */
 
 /* Active-set size at schedule position q.  Sec. II C lets the zone radius

@@ -686,3 +686,163 @@ def test_lbfgs_tu_with_pinned_boundary():
     assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
     assert np.all(r[f == 0] <= 0.95 * (1 + 1e-15))
     assert oracle.energy(x) < oracle.energy(p0)
+
+
+# ------------------------------------------------------------------ L-BFGS-B ---
+# The pieces of L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995; Sec. II C step 4) are pinned against dense
+# linear algebra: the BFGS matrix by its rank-two recursion, the Cauchy point by scanning the
+# projected path, the subspace step by a dense reduced Newton solve.
+
+def _bfgs_pairs(nv, h, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((nv, nv))
+    hess = a @ a.T + nv * np.eye(nv)
+    s = rng.standard_normal((h, nv))
+    return s, s @ hess.T  # y = H s: every pair has s.y > 0
+
+
+def _bfgs_dense(s_rows, y_rows, theta):
+    b = theta * np.eye(s_rows.shape[1] if s_rows.ndim == 2 else 0)
+    for s, y in zip(s_rows, y_rows):
+        bs = b @ s
+        b = b - np.outer(bs, bs) / (s @ bs) + np.outer(y, y) / (y @ s)
+    return b
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 5])
+def test_lbfgsb_compact_form_is_the_bfgs_recursion(h):
+    """theta I - W M W^T equals h rank-two BFGS updates of theta I applied oldest first."""
+    s, y = _bfgs_pairs(9, h, 10 + h)
+    theta = 3.7
+    m = oracle.lbfgsb_middle(s, y, theta)
+    w = np.hstack([y.T, theta * s.T])
+    b = theta * np.eye(9) - w @ m @ w.T
+    ref = _bfgs_dense(s, y, theta)
+    assert np.abs(b - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def _box_case(seed, theta=0.05):
+    """Variables 0-5 boxed in [0, 1], 6-9 free, 10 fixed; two stored pairs."""
+    rng = np.random.default_rng(seed)
+    nv = 11
+    lo = np.r_[np.zeros(6), np.full(4, -np.inf), 0.3]
+    hi = np.r_[np.ones(6), np.full(4, np.inf), 0.3]
+    x = np.r_[rng.uniform(0.05, 0.95, 6), rng.standard_normal(4), 0.3]
+    g = rng.standard_normal(nv)
+    g[:6] *= 12.0  # steep enough that the projected path meets several bounds
+    g[10] = 0.7  # a fixed variable's gradient must not move it
+    s, y = _bfgs_pairs(nv, 2, seed)
+    return x, g, lo, hi, s, y, theta
+
+
+def _model(x, g, b, v):
+    dv = v - x
+    return g @ dv + 0.5 * dv @ b @ dv
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_lbfgsb_cauchy_point_is_first_minimum_along_projected_path(seed):
+    """The generalized Cauchy point is the first local minimiser of the quadratic model along
+    P(x - t g), found here by scanning t on a fine grid and refining with a bounded Brent search."""
+    from scipy.optimize import minimize_scalar
+
+    x, g, lo, hi, s, y, theta = _box_case(seed)
+    m = oracle.lbfgsb_middle(s, y, theta)
+    xc, c, nb = oracle.lbfgsb_cauchy(x, g, lo, hi, s, y, theta, m)
+    b = _bfgs_dense(s, y, theta)
+    path = lambda t: np.clip(x - t * g, lo, hi)
+    f = lambda t: _model(x, g, b, path(t))
+    ts = np.linspace(0.0, 40.0, 400001)
+    vals = np.array([f(t) for t in ts])
+    k = next(k for k in range(1, len(ts) - 1) if vals[k] <= vals[k - 1] and vals[k] <= vals[k + 1])
+    r = minimize_scalar(f, bounds=(ts[k - 1], ts[k + 1]), method="bounded", options={"xatol": 1e-12})
+    np.testing.assert_allclose(xc, path(r.x), rtol=0, atol=1e-7)
+    assert xc[10] == 0.3 and np.all(xc >= lo) and np.all(xc <= hi)
+    w = np.hstack([y.T, theta * s.T])
+    np.testing.assert_allclose(c, w.T @ (xc - x), rtol=0, atol=1e-10 * np.abs(w).max())
+    assert nb >= 3  # each case passes several breakpoints
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_lbfgsb_subspace_step_is_reduced_newton_then_backtracked(seed):
+    """From the Cauchy point, the free variables take the Newton step of the model restricted to
+    them (dense solve with the BFGS matrix), shortened so that every variable stays in its box."""
+    x, g, lo, hi, s, y, theta = _box_case(seed, theta=0.8)
+    m = oracle.lbfgsb_middle(s, y, theta)
+    xc, c, _ = oracle.lbfgsb_cauchy(x, g, lo, hi, s, y, theta, m)
+    xbar = oracle.lbfgsb_subspace(x, g, lo, hi, s, y, theta, m, xc, c)
+    b = _bfgs_dense(s, y, theta)
+    free = (lo < xc) & (xc < hi)
+    rc = g + b @ (xc - x)
+    du = -np.linalg.solve(b[np.ix_(free, free)], rc[free])
+    a = 1.0
+    for v, l_, h_, dv in zip(xc[free], lo[free], hi[free], du):
+        if dv > 0 and np.isfinite(h_):
+            a = min(a, (h_ - v) / dv)
+        if dv < 0 and np.isfinite(l_):
+            a = min(a, (l_ - v) / dv)
+    ref = xc.copy()
+    ref[free] = xc[free] + a * du
+    np.testing.assert_allclose(xbar, ref, rtol=0, atol=1e-10)
+    assert np.all(xbar >= lo) and np.all(xbar <= hi)
+
+
+def test_lbfgsb_subspace_cases_include_a_shortened_step():
+    shortened = 0
+    for seed in range(1, 6):
+        x, g, lo, hi, s, y, theta = _box_case(seed, theta=0.8)
+        m = oracle.lbfgsb_middle(s, y, theta)
+        xc, c, _ = oracle.lbfgsb_cauchy(x, g, lo, hi, s, y, theta, m)
+        xbar = oracle.lbfgsb_subspace(x, g, lo, hi, s, y, theta, m, xc, c)
+        b = _bfgs_dense(s, y, theta)
+        free = (lo < xc) & (xc < hi)
+        du = -np.linalg.solve(b[np.ix_(free, free)], (g + b @ (xc - x))[free])
+        shortened += not np.allclose(xbar[free], xc[free] + du, rtol=0, atol=1e-12)
+    assert shortened >= 1
+
+
+@pytest.mark.parametrize("h", [0, 1, 4])
+def test_lbfgsb_without_bounds_is_the_quasi_newton_step(h):
+    """With no finite bound, Cauchy point plus subspace step is x - B^{-1} g."""
+    nv = 10
+    rng = np.random.default_rng(50 + h)
+    x, g = rng.standard_normal(nv), rng.standard_normal(nv)
+    lo, hi = np.full(nv, -np.inf), np.full(nv, np.inf)
+    s, y = _bfgs_pairs(nv, max(h, 1), 60 + h)
+    s, y = s[:h], y[:h]
+    theta = 1.3
+    m = oracle.lbfgsb_middle(s, y, theta) if h else np.zeros((0, 0))
+    xc, c, nb = oracle.lbfgsb_cauchy(x, g, lo, hi, s, y, theta, m)
+    xbar = oracle.lbfgsb_subspace(x, g, lo, hi, s, y, theta, m, xc, c)
+    b = _bfgs_dense(s, y, theta) if h else theta * np.eye(nv)
+    assert nb == 0
+    np.testing.assert_allclose(xbar, x - np.linalg.solve(b, g), rtol=0, atol=1e-12 * max(1.0, np.abs(g).max()))
+
+
+@pytest.mark.parametrize("n,expect", [(3, math.sqrt(3)), (4, 1 + 2 * math.sqrt(2)), (5, 6.881909602355867)])
+def test_lbfgsb_reaches_ring_minima(n, expect):
+    """L-BFGS-B on (t, u) relaxes small N to the regular polygon on the circle (the closed-form
+    ring energies) and ends with a vanishing projected gradient."""
+    pos = synth.arcsine_disk(n, 3)
+    x, it, rms, _ = oracle.lbfgsb(pos, max_iter=3000, gtol=1e-10, step0=1e-3, maxstep=0.05)
+    assert rms < 1e-10
+    assert abs(oracle.energy(x) - expect) <= 1e-12 * expect
+    _, rms_c, _ = oracle.projected_grad(x, oracle.grad(x))
+    assert rms_c < 1e-8
+
+
+def test_lbfgsb_pinned_boundary_and_armijo_descent():
+    """Pinned charges stay on the unit circle, the others inside sigma; with the line search every
+    accepted step lowers the energy, so a run of k + 1 iterations ends below a run of k."""
+    n = 80
+    pos = synth.arcsine_disk(n, 9)
+    p0, f = oracle.border_split(pos, 12, 0.95)
+    energies = []
+    for k in [0, 5, 10, 20, 40]:
+        x, it, rms, _ = oracle.lbfgsb(p0, max_iter=k, step0=1e-3, maxstep=0.05, radius=0.95, flags=f,
+                                      line_search=20)
+        r = np.hypot(x[:, 0], x[:, 1])
+        assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
+        assert np.all(r[f == 0] <= 0.95 * (1 + 1e-15))
+        energies.append(oracle.energy(x))
+    assert all(b < a for a, b in zip(energies, energies[1:]))
