@@ -153,8 +153,14 @@ typedef enum {
     TC_OPT_GD = 0,    /* projected gradient descent x <- P(x - step0 g) */
     TC_OPT_BB = 1,    /* projected descent with Barzilai-Borwein (s^T y / y^T y) steps */
     TC_OPT_LBFGS = 2, /* L-BFGS on the smooth wall map x = radius sin|z| z/|z| (no projection) */
-    TC_OPT_LBFGS_TU = 3 /* L-BFGS on the paper's (t, u) (Sec. II D): x = radius sin^2 t (cos u, sin u),
+    TC_OPT_LBFGS_TU = 3, /* L-BFGS on the paper's (t, u) (Sec. II D): x = radius sin^2 t (cos u, sin u),
                            pinned (cos u, sin u); gradients by the paper's chain rule */
+    TC_OPT_LBFGSB_TU = 4 /* L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995), the optimiser Sec. II C step 4
+                            names, on the same (t, u) with the box t in [0, pi/2]: generalized
+                            Cauchy point, direct-primal subspace minimisation, then the capped
+                            step (and line search) below.  memory 1..8; every problem at most
+                            16384 charges (else TC_ERR_INVALID_ARG); rms is the RMS of the
+                            projected gradient P(v - g) - v */
 } tc_optimizer;
 
 typedef struct {

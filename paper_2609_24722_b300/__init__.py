@@ -32,7 +32,8 @@ __all__ = [
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED, "fp64x": L.TC_F64X}
-_OPT = {"gd": L.TC_OPT_GD, "bb": L.TC_OPT_BB, "lbfgs": L.TC_OPT_LBFGS, "lbfgs_tu": L.TC_OPT_LBFGS_TU}
+_OPT = {"gd": L.TC_OPT_GD, "bb": L.TC_OPT_BB, "lbfgs": L.TC_OPT_LBFGS, "lbfgs_tu": L.TC_OPT_LBFGS_TU,
+        "lbfgsb_tu": L.TC_OPT_LBFGSB_TU}
 
 
 def library_path() -> str:

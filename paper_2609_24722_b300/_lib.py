@@ -18,7 +18,7 @@ TC_OK = 0
 TC_FP64 = 0
 TC_MIXED = 1
 TC_F64X = 2
-TC_OPT_GD, TC_OPT_BB, TC_OPT_LBFGS, TC_OPT_LBFGS_TU = 0, 1, 2, 3
+TC_OPT_GD, TC_OPT_BB, TC_OPT_LBFGS, TC_OPT_LBFGS_TU, TC_OPT_LBFGSB_TU = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_CUDA", 3: "TC_ERR_NONFINITE",
                 4: "TC_ERR_OUTSIDE_DISK", 5: "TC_ERR_TIMEOUT", 6: "TC_ERR_NOT_CONVERGED", 7: "TC_ERR_NO_MEMORY"}
 

@@ -51,25 +51,21 @@ def test_line_search_instances_match_oracle(prec):
 
 
 def test_line_search_large_instance_matches_oracle():
-    """An instance above 16384 charges (grid-wide L-BFGS update) with the line search."""
+    """An instance above 16384 charges (grid-wide L-BFGS update) with the line search.  From the
+    lattice start a capped first step of 0.05 raises E by about 2e4 (the oracle's figure), so the
+    halvings always run."""
     n = 17000
-    pos = synth.arcsine_disk(n, 78)
-    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    pos = synth.lattice_disk(n, 78)
+    x1 = np.ascontiguousarray(pos[synth.zorder(pos)])
     world = T(np.array([[0, n]], dtype=np.int64))
-    # start near equilibrium, where a 0.05 step overshoots and the halvings run
-    q = T(pos.copy())
-    tc.relax_subdomains(q, world=world, precision="fp64", optimizer="lbfgs", n_steps=20, memory=8, step0=1e-3,
-                        maxstep=0.01, accept=False)
-    tc.sync_status()
-    x1 = q.cpu().numpy()
     p = T(x1.copy())
     iters = 2
     r = tc.relax_subdomains(p, world=world, precision="fp64", optimizer="lbfgs", n_steps=iters, memory=8,
-                            step0=1e-3, maxstep=0.05, accept=False, line_search=6)
+                            step0=1.0, maxstep=0.05, accept=False, line_search=6)
     tc.sync_status()
-    xo, it, rms = oracle.lbfgs(x1, memory=8, max_iter=iters, gtol=0.0, step0=1e-3, maxstep=0.05, line_search=6)
-    xn, _, _ = oracle.lbfgs(x1, memory=8, max_iter=iters, gtol=0.0, step0=1e-3, maxstep=0.05)
-    assert np.abs(xo - xn).max() > 1e-6
+    xo, it, rms = oracle.lbfgs(x1, memory=8, max_iter=iters, gtol=0.0, step0=1.0, maxstep=0.05, line_search=6)
+    xn, _, _ = oracle.lbfgs(x1, memory=8, max_iter=iters, gtol=0.0, step0=1.0, maxstep=0.05)
+    assert np.abs(xo - xn).max() > 1e-3
     assert int(r.steps[0]) == iters
     assert np.abs(p.cpu().numpy() - xo).max() <= 1e-9
 
