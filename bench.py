@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle"], default=None)
     ap.add_argument("--batch", type=int, default=64, help="cycle case: subdomains per batch")
     ap.add_argument("--zone-steps", type=int, default=100, help="cycle case: relaxation steps per zone")
+    ap.add_argument("--cycle-opt", choices=["bb", "lbfgsb_tu"], default="bb", help="cycle case: zone optimiser")
     ap.add_argument("--prec", choices=["mixed", "fp64", "fp64x"], default="mixed")
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--nsub", type=int, default=16)
@@ -87,7 +88,8 @@ def run_case(args):
     if args.case == "cycle":
         # cycle time against N at a fixed number of subdomain optimisations (Sec. II E)
         for n in [args.n // 8, args.n // 4, args.n // 2, args.n]:
-            print(json.dumps(run_cycle(dev, n=n, n_sub=args.nsub, batch=args.batch, steps=args.zone_steps)))
+            print(json.dumps(run_cycle(dev, n=n, n_sub=args.nsub, batch=args.batch, steps=args.zone_steps,
+                                       optimizer=args.cycle_opt)))
         return
     if args.config is not None:
         from paper_2609_24722_b300 import _lib
@@ -388,12 +390,14 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
 
 
 def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 100, m_min: int = 200,
-              m_max: int = 4000, period: int = 64, seed: int = 0, local_precision: str = "mixed") -> dict:
+              m_max: int = 4000, period: int = 64, seed: int = 0, local_precision: str = "mixed",
+              optimizer: str = "bb") -> dict:
     """The adaptive optimisation cycle (Sec. II C) on the GPU, after the border-interior split of
     Sec. II B (N_b pinned boundary charges, interior radius ramped from Eq. sigma to 1 over the
     batches): per batch of `batch` subdomains, local energies of all N charges, defect threshold e_i > mu - sigma_e, centres (80 % at defects, 20 %
     uniform in the disk), zones of the m nearest charges (m a triangle wave between m_min and m_max),
-    `steps` mixed projected BB steps per zone against all N, sequential float64 accept."""
+    `steps` mixed steps per zone against all N (projected BB, or the paper's L-BFGS-B on (t, u) with
+    optimizer="lbfgsb_tu"), sequential float64 accept."""
     import numpy as np
     import torch
 
@@ -409,8 +413,12 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     u = torch.tensor(np.random.default_rng(seed + 7).random((n_sub, 3)), device=dev)
     eta = 1e-4 / n
     kw = dict(batch=batch, m_min=m_min, m_max=m_max, period=period, local_precision=local_precision,
-              precision="mixed", optimizer="bb", n_steps=steps, step0=eta, alpha_min=0.0, alpha_max=10 * eta,
+              precision="mixed", optimizer=optimizer, n_steps=steps, step0=eta, alpha_min=0.0, alpha_max=10 * eta,
               sigma0=sigma0, sigma1=1.0)
+    if optimizer != "bb":
+        # quasi-Newton: the first step is eta-scaled, later ones scale themselves; each charge moves
+        # at most 1e-3 in (t, u) per step (a sixth of the local spacing at N = 1e5)
+        kw.update(memory=8, maxstep=1e-3)
     sizes = np.diff(tc.zone_offsets(n, n_sub, m_min=m_min, m_max=m_max, period=period))
     # warm-up on a copy (graph capture, workspace growth)
     tc.cycle(p.clone(), u[: min(batch, n_sub)], flags, **kw)
@@ -439,7 +447,8 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     return {"workload": f"N={n} lattice background split into N_b={tc.boundary_count(n)} pinned boundary charges "
                         f"and an interior disk whose radius ramps {sigma0:.5f} -> 1 over the batches; {n_sub} "
                         f"subdomains in batches of {batch}, zones of {m_min}..{m_max} nearest charges (triangle "
-                        f"wave, period {period}), {steps} mixed BB steps each, {local_precision} local energies "
+                        f"wave, period {period}), {steps} mixed {'BB' if optimizer == 'bb' else optimizer} steps each, "
+                        f"{local_precision} local energies "
                         f"per batch, fp64 sequential accept",
             "cycle_time_s": ms / 1e3, "ms_per_subdomain": ms / n_sub, "pairs_per_s": pairs / (ms / 1e3),
             "accepted": int((st == 1).sum()), "skipped_overlap": int((st == 2).sum()),
@@ -618,6 +627,10 @@ def main():
         c5["fp64x_polish_variant"] = {k: c5x[k] for k in ("workload", "relax_time_s", "pairs_per_s_mixed_with_polish",
                                                             "best_energy_sum", "fp64_energy_vs_oracle_max_rel")}
     cyc = run_cycle(dev) if not args.no_instances else None
+    if cyc is not None:
+        cb = run_cycle(dev, optimizer="lbfgsb_tu")
+        cyc["lbfgsb_tu_variant"] = {k: cb[k] for k in ("workload", "cycle_time_s", "ms_per_subdomain", "accepted",
+                                                        "energy_start", "energy_end", "energy_drop")}
     pipes = tc.probe_pipes()
     tc.sync_status()
 

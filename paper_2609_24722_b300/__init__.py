@@ -233,7 +233,7 @@ def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, peri
           kappa: float = -1.0, p_defect: float = 0.8, wall_tol: float = 1e-9, sigma0: float = 1.0, sigma1: float = 1.0,
           local_precision="mixed", precision="mixed", optimizer="bb", n_steps=200, memory=8, step0=1e-9,
           alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0, polish_steps=0, polish_gtol=0.0,
-          want_energy=False, profile=False):
+          want_energy=False, profile=False, line_search=0):
     """One optimisation cycle (Sec. II C) of uniforms.shape[0] subdomains in batches, in place on pos.
 
     flags (uint8, nullable): pinned boundary charges; sigma0 -> sigma1: interior radius ramp.
@@ -246,7 +246,7 @@ def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, peri
     prm = L.CycleParams()
     prm.zone = zone_params(m_min, m_max, period, phase, kappa, p_defect, 1.0, wall_tol)
     prm.relax = _relax_params(precision, optimizer, n_steps, memory, step0, alpha_min, alpha_max, maxstep, gtol,
-                              1.0, polish_steps, polish_gtol, True, want_energy, profile)
+                              1.0, polish_steps, polish_gtol, True, want_energy, profile, line_search=line_search)
     prm.batch = int(batch)
     prm.local_precision = _prec(local_precision)
     prm.sigma0 = float(sigma0)
