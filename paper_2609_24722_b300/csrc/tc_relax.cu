@@ -141,9 +141,14 @@ __device__ double block_max(double v, double* sh)
 __device__ __forceinline__ double2 z_to_x(double2 z, double radius, bool pinned, bool tu)
 {
     if (tu) {
-        if (pinned) return make_double2(cos(z.x), sin(z.x));
+        double s_, c_;
+        if (pinned) {
+            sincos(z.x, &s_, &c_);
+            return make_double2(c_, s_);
+        }
         const double st = sin(z.x), r = radius * st * st;
-        return make_double2(r * cos(z.y), r * sin(z.y));
+        sincos(z.y, &s_, &c_);
+        return make_double2(r * c_, r * s_);
     }
     double rho = sqrt(z.x * z.x + z.y * z.y);
     if (pinned) return make_double2(z.x / rho, z.y / rho);
@@ -177,10 +182,13 @@ __device__ __forceinline__ double2 x_to_z(double2 x, double radius, bool pinned,
 __device__ __forceinline__ double2 grad_z(double2 z, double2 g, double radius, bool pinned, bool tu)
 {
     if (tu) {
-        if (pinned) return make_double2(-g.x * sin(z.x) + g.y * cos(z.x), 0.0);
-        const double c = cos(z.y), sn = sin(z.y), st = sin(z.x);
+        double sn, c;
+        sincos(z.x, &sn, &c);
+        if (pinned) return make_double2(-g.x * sn + g.y * c, 0.0);
+        const double st = sn, ct = c;  // sin 2t = 2 sin t cos t
+        sincos(z.y, &sn, &c);
         const double r = radius * st * st;
-        return make_double2((g.x * c + g.y * sn) * radius * sin(2.0 * z.x), (-g.x * sn + g.y * c) * r);
+        return make_double2((g.x * c + g.y * sn) * radius * (2.0 * st * ct), (-g.x * sn + g.y * c) * r);
     }
     double rho = sqrt(z.x * z.x + z.y * z.y);
     if (rho == 0.0) return pinned ? make_double2(0.0, 0.0) : make_double2(radius * g.x, radius * g.y);
@@ -524,12 +532,17 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
 // coordinates of kBQ entries: entry a < kBMem is y of the a-th oldest stored
 // pair, entry kBMem + a is theta s of it.  Entries of pairs not stored are 0 in
 // W and the identity in K, so every sum over entries adds the non-zero terms
-// in the compact order.  The products s_a.y_b and s_a.s_b are kept per ring
-// slot and computed once, when the newer of the two pairs is stored.
+// in the compact order.  The products s_a.y_b, s_a.s_b and y_a.y_b are kept per
+// ring slot and computed once, when the newer of the two pairs is stored.
+//
+// The float64 pipe is the limit (one problem runs on one SM), so the per-row
+// work is kept small: rows of W are read unscaled, W' = [Y, S], and theta is
+// applied to the short vectors (W = W' D, D = diag(1, theta)); W_F^T W_F is
+// W^T W, known from the kept products, less the rows whose t is at a bound.
 
 constexpr int kBMem = 8;                            // largest L-BFGS-B memory
 constexpr int kBQ = 2 * kBMem;                      // padded order of K and M
-constexpr int kBSmall = 2 * kBMem * kBMem + 1;      // per problem: s.y and s.s by slot, theta
+constexpr int kBSmall = 3 * kBMem * kBMem + 1;      // per problem: s.y, s.s, y.y by slot, theta
 constexpr int kRed = 40;                            // widest multi-value block reduction
 constexpr double kHalfPi = 1.5707963267948966;      // upper bound of t
 
@@ -635,8 +648,8 @@ __device__ bool warp_gauss_jordan(double* aug)
     return true;
 }
 
-// Row rl's two W rows (variables x and y) in the padded coordinates.
-__device__ __forceinline__ void w_rows(const RelaxDev& d, int64_t row, const int* slot, int hb, double theta,
+// Row rl's two rows of W' = [Y, S] (variables x and y) in the padded coordinates.
+__device__ __forceinline__ void w_rows(const RelaxDev& d, int64_t row, const int* slot, int hb,
                                        double (&wx)[kBQ], double (&wy)[kBQ])
 {
 #pragma unroll
@@ -646,8 +659,8 @@ __device__ __forceinline__ void w_rows(const RelaxDev& d, int64_t row, const int
             const double2 yj = d.Yh[(int64_t)j * d.M + row], sj = d.Sh[(int64_t)j * d.M + row];
             wx[a] = yj.x;
             wy[a] = yj.y;
-            wx[kBMem + a] = theta * sj.x;
-            wy[kBMem + a] = theta * sj.y;
+            wx[kBMem + a] = sj.x;
+            wy[kBMem + a] = sj.y;
         } else {
             wx[a] = wy[a] = wx[kBMem + a] = wy[kBMem + a] = 0.0;
         }
@@ -670,6 +683,22 @@ __device__ __forceinline__ void matvec16(const double* M, const double* x, doubl
         for (int b = 0; b < kBQ; ++b) s += M[a * kBQ + b] * x[b];
         y[a] = s;
     }
+}
+
+// Row a of M x (sums in entry order); one lane per row.
+__device__ __forceinline__ double row_dot16(const double* M, const double* x, int a)
+{
+    double s = 0.0;
+    for (int b = 0; b < kBQ; ++b) s += M[a * kBQ + b] * x[b];
+    return s;
+}
+
+// Sum of v over lanes 0 .. kBQ - 1 of a warp (fixed tree), valid in lane 0.
+__device__ __forceinline__ double lanes_sum16(double v)
+{
+#pragma unroll
+    for (int o = kBQ / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // Entries [C0, C0 + NC) of the upper triangle (row-major) of w w^T.
@@ -695,10 +724,11 @@ template <int C0, int NC> __device__ __forceinline__ void gram_store(const doubl
         }
 }
 
-// One chunk of W_F^T W_F over the free variables (xc strictly inside its box).
+// One chunk of W'^T W' over the variables at a bound in xc whose W' row is not
+// zero: the t of a free charge at 0 or pi/2 (a pinned charge's fixed second
+// variable has y = s = 0).
 template <int C0, int NC>
-__device__ void gram_chunk(const RelaxDev& d, const Prob& p, const int* slot, int hb, double theta, double* A,
-                           double (*red)[kRed])
+__device__ void gram_chunk(const RelaxDev& d, const Prob& p, const int* slot, int hb, double* A, double (*red)[kRed])
 {
     double acc[NC];
 #pragma unroll
@@ -710,16 +740,16 @@ __device__ void gram_chunk(const RelaxDev& d, const Prob& p, const int* slot, in
         double2 lo, hi;
         tu_bounds(pinned, lo, hi);
         const double2 xc = d.xc[row];
+        if (pinned || (lo.x < xc.x && xc.x < hi.x)) continue;
         double wx[kBQ], wy[kBQ];
-        w_rows(d, row, slot, hb, theta, wx, wy);
-        if (lo.x < xc.x && xc.x < hi.x) gram_add<C0, NC>(wx, acc);
-        if (lo.y < xc.y && xc.y < hi.y) gram_add<C0, NC>(wy, acc);
+        w_rows(d, row, slot, hb, wx, wy);
+        gram_add<C0, NC>(wx, acc);
     }
     block_sums_w<NC>(acc, red);
     if (threadIdx.x == 0) gram_store<C0, NC>(acc, A);
 }
 
-__global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
+__global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
                                                          StepParams sp)
 {
     __shared__ double sh[kUpd];
@@ -729,7 +759,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
     __shared__ double Mm[kBQ * kBQ];
     __shared__ double A[kBQ * kBQ];         // W_F^T W_F
     __shared__ double Nv[kBQ * (kBQ + 1)];  // [N | v]
-    __shared__ double pv[kBQ], cv[kBQ], mc[kBQ], vv[kBQ];
+    __shared__ double pv[kBQ], cv[kBQ], mc[kBQ], vv[kBQ], wbs[kBQ], wrs[kBQ];
     __shared__ int slot[kBMem], oth[kBMem];
     __shared__ double bc[4];                // told, dtm, fp, fpp of the Cauchy search
     __shared__ int bflag[2];
@@ -741,7 +771,8 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
     const int64_t M = d.M;
     double* sy_t = d.bsmall + (int64_t)s * kBSmall;  // [slot a][slot b] = s_a . y_b
     double* ss_t = sy_t + kBMem * kBMem;              // s_a . s_b
-    double* theta_t = ss_t + kBMem * kBMem;           // y.y / s.y of the newest pair
+    double* yy_t = ss_t + kBMem * kBMem;              // y_a . y_b
+    double* theta_t = yy_t + kBMem * kBMem;           // y.y / s.y of the newest pair
 
     // 1. dE/d(t, u) of the new point into q, pair statistics, projected-gradient RMS
     double acc[4] = {0.0, 0.0, 0.0, 0.0};  // |P(z - g) - z|^2, s.y, s.s, y.y
@@ -788,9 +819,9 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
             for (int a = no; a < kBMem; ++a) oth[a] = -1;
         }
         __syncthreads();
-        double dots[3 * (kBMem - 1)];
+        double dots[4 * (kBMem - 1)];
 #pragma unroll
-        for (int i = 0; i < 3 * (kBMem - 1); ++i) dots[i] = 0.0;
+        for (int i = 0; i < 4 * (kBMem - 1); ++i) dots[i] = 0.0;
         TC_ROWS(p)
         {
             const int64_t row = p.row_base + rl;
@@ -801,25 +832,28 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
                 const int j = oth[o];
                 if (j < 0) continue;
                 const double2 sj = d.Sh[(int64_t)j * M + row], yj = d.Yh[(int64_t)j * M + row];
-                dots[3 * o] += sn.x * yj.x + sn.y * yj.y;
-                dots[3 * o + 1] += sj.x * yn.x + sj.y * yn.y;
-                dots[3 * o + 2] += sn.x * sj.x + sn.y * sj.y;
+                dots[4 * o] += sn.x * yj.x + sn.y * yj.y;
+                dots[4 * o + 1] += sj.x * yn.x + sj.y * yn.y;
+                dots[4 * o + 2] += sn.x * sj.x + sn.y * sj.y;
+                dots[4 * o + 3] += yn.x * yj.x + yn.y * yj.y;
             }
             d.Sh[(int64_t)head * M + row] = sn;
             d.Yh[(int64_t)head * M + row] = yn;
             d.gp[row] = gz;
         }
-        block_sums_w<3 * (kBMem - 1)>(dots, red);
+        block_sums_w<4 * (kBMem - 1)>(dots, red);
         if (threadIdx.x == 0) {
             for (int o = 0; o < kBMem - 1; ++o) {
                 const int j = oth[o];
                 if (j < 0) continue;
-                sy_t[head * kBMem + j] = dots[3 * o];
-                sy_t[j * kBMem + head] = dots[3 * o + 1];
-                ss_t[head * kBMem + j] = ss_t[j * kBMem + head] = dots[3 * o + 2];
+                sy_t[head * kBMem + j] = dots[4 * o];
+                sy_t[j * kBMem + head] = dots[4 * o + 1];
+                ss_t[head * kBMem + j] = ss_t[j * kBMem + head] = dots[4 * o + 2];
+                yy_t[head * kBMem + j] = yy_t[j * kBMem + head] = dots[4 * o + 3];
             }
             sy_t[head * kBMem + head] = acc[1];
             ss_t[head * kBMem + head] = acc[2];
+            yy_t[head * kBMem + head] = acc[3];
             *theta_t = acc[3] / acc[1];
         }
         head = (head + 1) % mem;
@@ -894,28 +928,33 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
         d.q[row] = dv;
         d.bp[row] = tx > 0.0 && tx < INFINITY ? tx : INFINITY;  // only a t variable has a finite one
         double wx[kBQ], wy[kBQ];
-        w_rows(d, row, slot, hb, theta, wx, wy);
+        w_rows(d, row, slot, hb, wx, wy);
 #pragma unroll
         for (int a = 0; a < kBQ; ++a) pd[a] += wx[a] * dv.x + wy[a] * dv.y;
         pd[kBQ] += dv.x * dv.x + dv.y * dv.y;
     }
     block_sums_w<kBQ + 1>(pd, red);
-    if (threadIdx.x == 0) {
-        double mp[kBQ];
-        for (int a = 0; a < kBQ; ++a) {
-            pv[a] = pd[a];
-            cv[a] = 0.0;
+    // The small dense algebra runs on warp 0, one lane per entry: a float64
+    // instruction of one thread takes the SM's float64 pipe as long as a warp's.
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        if (lane == 0)
+            for (int a = 0; a < kBQ; ++a) {
+                pv[a] = a < kBMem ? pd[a] : theta * pd[a];  // p = D W'^T d
+                cv[a] = 0.0;
+            }
+        __syncwarp();
+        const double mp = lane < kBQ ? row_dot16(Mm, pv, lane) : 0.0;
+        const double pmp = lanes_sum16(lane < kBQ ? pv[lane] * mp : 0.0);
+        if (lane == 0) {
+            const double fp = -pd[kBQ];
+            const double fpp = -theta * fp - pmp;
+            bc[0] = 0.0;
+            bc[1] = fpp > 0.0 ? -fp / fpp : 0.0;
+            bc[2] = fp;
+            bc[3] = fpp;
+            bflag[1] = fpp > 0.0 ? 1 : 0;
         }
-        matvec16(Mm, pv, mp);
-        double pmp = 0.0;
-        for (int a = 0; a < kBQ; ++a) pmp += pv[a] * mp[a];
-        const double fp = -pd[kBQ];
-        const double fpp = -theta * fp - pmp;
-        bc[0] = 0.0;
-        bc[1] = fpp > 0.0 ? -fp / fpp : 0.0;
-        bc[2] = fp;
-        bc[3] = fpp;
-        bflag[1] = fpp > 0.0 ? 1 : 0;
     }
     __syncthreads();
     const double fpp0 = bc[3];
@@ -933,28 +972,40 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
             }
         }
         block_argmin(tmin, rmin, sh, shi);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             const double told = bc[0], dtm = bc[1];
             const double dt = tmin - told;
             if (rmin == INT_MAX || dtm < dt) {
-                bflag[1] = 0;
+                if (lane == 0) bflag[1] = 0;
             } else {
                 const int64_t b = p.row_base + rmin;
+                const double gb = d.gp[b].x;
+                double wa = 0.0;  // entry `lane` of w_b (row b of W, variable t)
+                if (lane < kBQ) {
+                    const int ia = lane < kBMem ? lane : lane - kBMem;
+                    if (ia < hb) {
+                        const int64_t o = (int64_t)slot[ia] * M + b;
+                        wa = lane < kBMem ? d.Yh[o].x : theta * d.Sh[o].x;
+                    }
+                    wbs[lane] = wa;
+                    cv[lane] += dt * pv[lane];
+                }
+                __syncwarp();
+                double mcl = 0.0, mpl = 0.0, mwl = 0.0;
+                if (lane < kBQ) {
+                    mcl = row_dot16(Mm, cv, lane);
+                    mpl = row_dot16(Mm, pv, lane);
+                    mwl = row_dot16(Mm, wbs, lane);
+                }
+                const double wMc = lanes_sum16(wa * mcl), wMp = lanes_sum16(wa * mpl), wMw = lanes_sum16(wa * mwl);
+                __syncwarp();
+                if (lane < kBQ) pv[lane] += gb * wa;
+                if (lane == 0) {
                 const bool pinned = d.flags && d.flags[d.gidx[b]];
                 double2 lo, hi;
                 tu_bounds(pinned, lo, hi);
                 const double xb = d.q[b].x > 0.0 ? hi.x : lo.x;
-                const double zb = xb - d.z[b].x, gb = d.gp[b].x;
-                double wb[kBQ], wdummy[kBQ], mv[kBQ];
-                w_rows(d, b, slot, hb, theta, wb, wdummy);
-                for (int a = 0; a < kBQ; ++a) cv[a] += dt * pv[a];
-                double wMc = 0.0, wMp = 0.0, wMw = 0.0;
-                matvec16(Mm, cv, mv);
-                for (int a = 0; a < kBQ; ++a) wMc += wb[a] * mv[a];
-                matvec16(Mm, pv, mv);
-                for (int a = 0; a < kBQ; ++a) wMp += wb[a] * mv[a];
-                matvec16(Mm, wb, mv);
-                for (int a = 0; a < kBQ; ++a) wMw += wb[a] * mv[a];
+                const double zb = xb - d.z[b].x;
                 double fp = bc[2], fpp = bc[3];
                 fp = __dsub_rn(__dadd_rn(__dadd_rn(__dadd_rn(fp, __dmul_rn(dt, fpp)), __dmul_rn(gb, gb)),
                                          __dmul_rn(__dmul_rn(theta, gb), zb)),
@@ -963,7 +1014,6 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
                                           __dmul_rn(__dmul_rn(2.0, gb), wMp)),
                                 __dmul_rn(__dmul_rn(gb, gb), wMw));
                 if (fpp < 0x1p-52 * fpp0) fpp = 0x1p-52 * fpp0;
-                for (int a = 0; a < kBQ; ++a) pv[a] += gb * wb[a];
                 d.q[b] = make_double2(0.0, d.q[b].y);
                 d.bp[b] = -1.0;  // fixed at its bound
                 reinterpret_cast<double*>(d.xc + b)[0] = xb;
@@ -971,15 +1021,16 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
                 bc[1] = -fp / fpp;
                 bc[2] = fp;
                 bc[3] = fpp;
+                }
             }
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && moves) {
-        double dtm = bc[1];
-        if (dtm < 0.0) dtm = 0.0;
-        bc[0] += dtm;
-        for (int a = 0; a < kBQ; ++a) cv[a] += dtm * pv[a];
+    if (threadIdx.x < 32 && moves) {
+        const double dtm = fmax(bc[1], 0.0);
+        if (lane < kBQ) cv[lane] += dtm * pv[lane];
+        __syncwarp();
+        if (lane == 0) bc[0] += dtm;
     }
     __syncthreads();
     {
@@ -994,11 +1045,15 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
     }
 
     // 5. subspace minimisation over the free variables (direct primal method)
-    if (threadIdx.x == 0) matvec16(Mm, cv, mc);
+    if (threadIdx.x < kBQ) {
+        const double t = row_dot16(Mm, cv, threadIdx.x);
+        mc[threadIdx.x] = threadIdx.x < kBMem ? t : theta * t;  // D M c: a row of W' dotted with it is w . M c
+    }
     __syncthreads();
     double wr[kBQ];
 #pragma unroll
     for (int a = 0; a < kBQ; ++a) wr[a] = 0.0;
+    int bound_rows = 0;
     TC_ROWS(p)
     {
         const int64_t row = p.row_base + rl;
@@ -1007,8 +1062,9 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
         tu_bounds(pinned, lo, hi);
         const double2 z = d.z[row], gz = d.gp[row], xc = d.xc[row];
         double wx[kBQ], wy[kBQ];
-        w_rows(d, row, slot, hb, theta, wx, wy);
+        w_rows(d, row, slot, hb, wx, wy);
         const bool fx = lo.x < xc.x && xc.x < hi.x, fy = lo.y < xc.y && xc.y < hi.y;
+        if (!pinned && !fx) bound_rows = 1;
         const double rx = fx ? gz.x + theta * (xc.x - z.x) - dot16(wx, mc) : 0.0;
         const double ry = fy ? gz.y + theta * (xc.y - z.y) - dot16(wy, mc) : 0.0;
         d.q[row] = make_double2(rx, ry);
@@ -1016,24 +1072,64 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
         for (int a = 0; a < kBQ; ++a) wr[a] += wx[a] * rx + wy[a] * ry;
     }
     block_sums_w<kBQ>(wr, red);
-    gram_chunk<0, 34>(d, p, slot, hb, theta, A, red);
-    gram_chunk<34, 34>(d, p, slot, hb, theta, A, red);
-    gram_chunk<68, 34>(d, p, slot, hb, theta, A, red);
-    gram_chunk<102, 34>(d, p, slot, hb, theta, A, red);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        constexpr int ld = kBQ + 1;
-        matvec16(Mm, wr, vv);
-        for (int a = 0; a < kBQ; ++a) {
-            for (int b = 0; b < kBQ; ++b) {
-                double t = 0.0;
-                for (int q = 0; q < kBQ; ++q) t += Mm[a * kBQ + q] * A[q * kBQ + b];
-                Nv[a * ld + b] = __dsub_rn(a == b ? 1.0 : 0.0, __ddiv_rn(t, theta));
-            }
-            Nv[a * ld + kBQ] = vv[a];
+    // W'^T W' over every variable, from the kept products (into aug, free after the inversion)
+    for (int e = threadIdx.x; e < kBQ * kBQ; e += kUpd) {
+        const int a = e / kBQ, b = e % kBQ;
+        const bool ya = a < kBMem, yb = b < kBMem;
+        const int ia = ya ? a : a - kBMem, ib = yb ? b : b - kBMem;
+        double val = 0.0;
+        if (ia < hb && ib < hb) {
+            const int ja = slot[ia], jb = slot[ib];
+            if (ya && yb)
+                val = yy_t[ja * kBMem + jb];
+            else if (ya)
+                val = sy_t[jb * kBMem + ja];  // y_ia . s_ib
+            else if (yb)
+                val = sy_t[ja * kBMem + jb];  // s_ia . y_ib
+            else
+                val = ss_t[ja * kBMem + jb];
         }
+        aug[e] = val;
+    }
+    // less the rows at a bound
+    if (__syncthreads_or(bound_rows)) {
+        gram_chunk<0, 34>(d, p, slot, hb, A, red);
+        gram_chunk<34, 34>(d, p, slot, hb, A, red);
+        gram_chunk<68, 34>(d, p, slot, hb, A, red);
+        gram_chunk<102, 34>(d, p, slot, hb, A, red);
+    } else if (threadIdx.x == 0) {
+        for (int e = 0; e < kBQ * kBQ; ++e) A[e] = 0.0;
+    }
+    __syncthreads();
+    static_assert(kBQ * kBQ == kUpd, "one entry of the small matrices per thread");
+    constexpr int ld = kBQ + 1;
+    {
+        // W_F^T W_F = D (W'^T W' - bound rows) D and W_F^T r = D W'^T r
+        const int e = threadIdx.x;
+        const double sa = e / kBQ < kBMem ? 1.0 : theta, sb = e % kBQ < kBMem ? 1.0 : theta;
+        A[e] = (aug[e] - A[e]) * sa * sb;
+        if (e < kBQ) {
+            double w = 0.0;
+#pragma unroll
+            for (int i = 0; i < kBQ; ++i)
+                if (i == e) w = wr[i];
+            wrs[e] = e < kBMem ? w : theta * w;
+        }
+    }
+    __syncthreads();
+    {
+        // N = I - M A / theta (one entry per thread) and its right-hand side M D W'^T r
+        const int e = threadIdx.x, ea = e / kBQ, eb = e % kBQ;
+        double t = 0.0;
+        for (int q = 0; q < kBQ; ++q) t += Mm[ea * kBQ + q] * A[q * kBQ + eb];
+        Nv[ea * ld + eb] = __dsub_rn(ea == eb ? 1.0 : 0.0, __ddiv_rn(t, theta));
+        if (e < kBQ) Nv[e * ld + kBQ] = row_dot16(Mm, wrs, e);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // Gauss elimination with partial pivoting on [N | v], one of the kBQ + 1 columns per lane
         bool ok = true;
-        for (int col = 0; col < kBQ && ok; ++col) {
+        for (int col = 0; col < kBQ; ++col) {
             int piv = col;
             for (int r = col + 1; r < kBQ; ++r)
                 if (fabs(Nv[r * ld + col]) > fabs(Nv[piv * ld + col])) piv = r;
@@ -1041,24 +1137,30 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
                 ok = false;
                 break;
             }
-            if (piv != col)
-                for (int q = 0; q <= kBQ; ++q) {
-                    const double t = Nv[col * ld + q];
-                    Nv[col * ld + q] = Nv[piv * ld + q];
-                    Nv[piv * ld + q] = t;
-                }
+            __syncwarp();
+            if (piv != col && lane <= kBQ) {
+                const double t = Nv[col * ld + lane];
+                Nv[col * ld + lane] = Nv[piv * ld + lane];
+                Nv[piv * ld + lane] = t;
+            }
+            __syncwarp();
             for (int r = col + 1; r < kBQ; ++r) {
                 const double f = __ddiv_rn(Nv[r * ld + col], Nv[col * ld + col]);
-                for (int q = col; q <= kBQ; ++q) Nv[r * ld + q] = __dsub_rn(Nv[r * ld + q], __dmul_rn(f, Nv[col * ld + q]));
+                __syncwarp();
+                if (lane >= col && lane <= kBQ)
+                    Nv[r * ld + lane] = __dsub_rn(Nv[r * ld + lane], __dmul_rn(f, Nv[col * ld + lane]));
+                __syncwarp();
             }
         }
         if (ok)
             for (int a = kBQ - 1; a >= 0; --a) {
-                double t = Nv[a * ld + kBQ];
-                for (int q = a + 1; q < kBQ; ++q) t = __dsub_rn(t, __dmul_rn(Nv[a * ld + q], vv[q]));
-                vv[a] = __ddiv_rn(t, Nv[a * ld + a]);
+                // v_a = (rhs_a - sum_{q > a} N_aq v_q) / N_aa, the products on lanes a+1 .. kBQ-1
+                const double t = lanes_sum16(lane > a && lane < kBQ ? __dmul_rn(Nv[a * ld + lane], vv[lane]) : 0.0);
+                if (lane == 0) vv[a] = __ddiv_rn(__dsub_rn(Nv[a * ld + kBQ], t), Nv[a * ld + a]);
+                __syncwarp();
             }
-        bflag[0] = ok ? 1 : 0;
+        if (lane >= kBMem && lane < kBQ) vv[lane] *= theta;  // D v: a row of W' dotted with it is w . v
+        if (lane == 0) bflag[0] = ok ? 1 : 0;
     }
     __syncthreads();
     if (!bflag[0]) {
@@ -1067,6 +1169,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
         return;
     }
     double amin = 1.0;
+    const double ith = 1.0 / theta, ith2 = ith * ith;
     TC_ROWS(p)
     {
         const int64_t row = p.row_base + rl;
@@ -1075,10 +1178,10 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgsb(RelaxDev d, const double
         tu_bounds(pinned, lo, hi);
         const double2 r = d.q[row], xc = d.xc[row];
         double wx[kBQ], wy[kBQ];
-        w_rows(d, row, slot, hb, theta, wx, wy);
+        w_rows(d, row, slot, hb, wx, wy);
         const bool fx = lo.x < xc.x && xc.x < hi.x, fy = lo.y < xc.y && xc.y < hi.y;
-        const double dux = fx ? -r.x / theta - dot16(wx, vv) / (theta * theta) : 0.0;
-        const double duy = fy ? -r.y / theta - dot16(wy, vv) / (theta * theta) : 0.0;
+        const double dux = fx ? -r.x * ith - dot16(wx, vv) * ith2 : 0.0;
+        const double duy = fy ? -r.y * ith - dot16(wy, vv) * ith2 : 0.0;
         if (fx && dux > 0.0 && hi.x < INFINITY) amin = fmin(amin, (hi.x - xc.x) / dux);
         if (fx && dux < 0.0 && lo.x > -INFINITY) amin = fmin(amin, (lo.x - xc.x) / dux);
         if (fy && duy > 0.0 && hi.y < INFINITY) amin = fmin(amin, (hi.y - xc.y) / duy);
