@@ -69,6 +69,9 @@ def lib(openmp: bool = False) -> C.CDLL:
             "tco_threads": [],
             "tco_zone_select": [vp, i64, vp, vp, d, d, d, d, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp],
             "tco_cycle": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, vp, d, d, d, i64, vp, vp, vp],
+            "tco_cycle_opt": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, vp, i64, d, d, d, i64, d, i64, i64,
+                              vp, vp, vp],
+            "tco_subdomain_lbfgsb": [vp, i64, vp, i64, i64, i64, d, d, d, vp, i64, vp],
             "tco_border_split": [vp, i64, i64, d, vp],
         }
         for name, args in sig.items():
@@ -254,6 +257,19 @@ def _vecs(*arrs):
     return [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in arrs]
 
 
+def subdomain_lbfgsb(snap, idx, memory: int = 8, steps: int = 100, step0: float = 1e-4, maxstep: float = 1e-2,
+                     radius: float = 1.0, flags=None, line_search: int = 0):
+    """L-BFGS-B on (t, u) of the charges idx against the others held at snap; returns their positions."""
+    s = _pos(snap)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    f = _flags(flags)
+    act = np.zeros((ix.size, 2))
+    _check(lib().tco_subdomain_lbfgsb(_p(s), s.shape[0], _p(ix), ix.size, int(memory), int(steps), float(step0),
+                                      float(maxstep), float(radius), _p(f), int(line_search), _p(act)),
+           "subdomain_lbfgsb")
+    return act
+
+
 def lbfgsb_middle(S, Y, theta: float):
     """M = K^{-1} of the compact representation B = theta I - W M W^T (rows of S, Y: pairs, oldest first)."""
     S, Y = _vecs(S, Y)
@@ -317,10 +333,12 @@ def zone_select(pos, local_e, uniforms, m_min: int, m_max: int, period: int, pha
 
 def cycle(pos, uniforms, m_min: int, m_max: int, period: int, batch: int, step0: float, alpha_min: float,
           alpha_max: float, steps: int, kappa: float = -1.0, p_defect: float = 0.8, sigma0: float = 1.0,
-          sigma1: float = 1.0, wall_tol: float = 1e-9, flags=None):
+          sigma1: float = 1.0, wall_tol: float = 1e-9, flags=None, optimizer: str = "bb", memory: int = 8,
+          maxstep: float = 1e-3, line_search: int = 0):
     """One optimisation cycle (Sec. II C) in batches; returns (pos, trace, delta, accepted).
 
-    sigma0 -> sigma1: interior radius ramp over the batches; flags: pinned boundary charges."""
+    sigma0 -> sigma1: interior radius ramp over the batches; flags: pinned boundary charges;
+    optimizer "bb" (projected BB) or "lbfgsb_tu" (L-BFGS-B on (t, u) per zone)."""
     p = _pos(pos).copy()
     f = _flags(flags)
     u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1, 3))
@@ -329,10 +347,11 @@ def cycle(pos, uniforms, m_min: int, m_max: int, period: int, batch: int, step0:
     trace = np.zeros(nb + 1)
     d = np.zeros(max(ns, 1))
     acc = np.zeros(max(ns, 1), dtype=np.uint8)
-    _check(lib().tco_cycle(_p(p), p.shape[0], _p(f), float(kappa), float(p_defect), float(sigma0), float(sigma1),
-                           float(wall_tol),
-                           int(m_min), int(m_max), int(period), ns, int(batch), _p(u), float(step0),
-                           float(alpha_min), float(alpha_max), int(steps), _p(trace), _p(d), _p(acc)), "cycle")
+    opt = {"bb": 0, "lbfgsb_tu": 1}[optimizer]
+    _check(lib().tco_cycle_opt(_p(p), p.shape[0], _p(f), float(kappa), float(p_defect), float(sigma0),
+                               float(sigma1), float(wall_tol), int(m_min), int(m_max), int(period), ns, int(batch),
+                               _p(u), opt, float(step0), float(alpha_min), float(alpha_max), int(memory),
+                               float(maxstep), int(line_search), int(steps), _p(trace), _p(d), _p(acc)), "cycle")
     return p, trace, d[:ns], acc[:ns]
 
 

@@ -1049,8 +1049,44 @@ static double proj_rms(const double* v, const double* g, const double* lo, const
     return n > 0 ? sqrt(acc_get(&s) / (double)n) : 0.0;
 }
 
+/* What one L-BFGS-B run minimises: a whole configuration (snap NULL: E of
+ * Eq. hamiltonian over the moving charges alone), or the subdomain objective
+ * E_sub of Sec. II D, whose moving charges are A = idx[0 .. m) and whose other
+ * charges stay at snap (n charges). */
+typedef struct {
+    const double* snap;
+    int64_t n;
+    const int32_t* idx;
+    double* cur; /* subdomain: scratch copy of snap (2n) */
+} tco_obj_t;
+
+static int obj_grad(const tco_obj_t* o, const double* x, int64_t m, double* g)
+{
+    if (!o->snap) return tco_grad(x, m, g);
+    return tco_subdomain_grad(o->snap, o->n, o->idx, m, x, g, NULL, NULL);
+}
+
+/* Energy change of moving the charges from xold to xnew, as pair differences. */
+static int obj_delta(const tco_obj_t* o, const double* xold, const double* xnew, int64_t m, double* de)
+{
+    if (!o->snap) {
+        *de = instance_delta(xold, xnew, m);
+        return TCO_OK;
+    }
+    memcpy(o->cur, o->snap, sizeof(double) * 2 * (size_t)o->n);
+    for (int64_t k = 0; k < m; ++k) {
+        o->cur[2 * (int64_t)o->idx[k]] = xold[2 * k];
+        o->cur[2 * (int64_t)o->idx[k] + 1] = xold[2 * k + 1];
+    }
+    return tco_delta_energy(o->cur, o->n, o->idx, m, xnew, de);
+}
+
+static int lbfgsb_run(const tco_obj_t* o, double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                      double step0, double maxstep, double sigma, const unsigned char* flags, int64_t max_halvings,
+                      int64_t* iters_out, double* rms_out, int64_t* breaks_out);
+
 /* L-BFGS-B on the (t, u) variables of Sec. II D over all n charges of one
- * configuration (Sec. II C step 4 applies it to a subdomain).  Iteration with
+ * configuration (tco_subdomain_lbfgsb: over a subdomain, as Sec. II C step 4).  Iteration with
  * at most `memory` pairs:
  *   stop when the projected-gradient RMS < gtol;
  *   theta = y.y / s.y of the newest pair (1 / step0 without pairs);
@@ -1066,6 +1102,44 @@ static double proj_rms(const double* v, const double* g, const double* lo, const
 int tco_lbfgsb(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol, double step0, double maxstep,
                double sigma, const unsigned char* flags, int64_t max_halvings, int64_t* iters_out, double* rms_out,
                int64_t* breaks_out)
+{
+    tco_obj_t o = {NULL, n, NULL, NULL};
+    return lbfgsb_run(&o, pos, n, memory, max_iter, gtol, step0, maxstep, sigma, flags, max_halvings, iters_out,
+                      rms_out, breaks_out);
+}
+
+/* L-BFGS-B on one subdomain (Sec. II C step 4): the charges of A = idx[0 .. m)
+ * start at snap[idx] and move, on the (t, u) variables with interior radius
+ * sigma (charges with flags[idx[k]] != 0 pinned to the unit circle; flags over
+ * all n, nullable); every other charge stays at snap.  The objective is E_sub
+ * of Sec. II D (tco_subdomain_grad), the line search's energy change
+ * tco_delta_energy against snap.  Iteration as tco_lbfgsb with gtol = 0.
+ * act_out (2m): the positions after `steps` iterations. */
+int tco_subdomain_lbfgsb(const double* snap, int64_t n, const int32_t* idx, int64_t m, int64_t memory,
+                         int64_t steps, double step0, double maxstep, double sigma, const unsigned char* flags,
+                         int64_t max_halvings, double* act_out)
+{
+    if (n < 1 || m < 0 || !snap || (m > 0 && (!idx || !act_out))) return TCO_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < m; ++k)
+        if (idx[k] < 0 || idx[k] >= n) return TCO_ERR_INVALID_ARG;
+    double* cur = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    unsigned char* fa = flags ? (unsigned char*)malloc((size_t)(m > 0 ? m : 1)) : NULL;
+    if (!cur || (flags && !fa)) { free(cur); free(fa); return TCO_ERR_NO_MEMORY; }
+    for (int64_t k = 0; k < m; ++k) {
+        act_out[2 * k] = snap[2 * (int64_t)idx[k]];
+        act_out[2 * k + 1] = snap[2 * (int64_t)idx[k] + 1];
+        if (fa) fa[k] = flags[idx[k]];
+    }
+    tco_obj_t o = {snap, n, idx, cur};
+    int st = lbfgsb_run(&o, act_out, m, memory, steps, 0.0, step0, maxstep, sigma, fa, max_halvings, NULL, NULL, NULL);
+    free(cur);
+    free(fa);
+    return st;
+}
+
+static int lbfgsb_run(const tco_obj_t* o, double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                      double step0, double maxstep, double sigma, const unsigned char* flags, int64_t max_halvings,
+                      int64_t* iters_out, double* rms_out, int64_t* breaks_out)
 {
     if (n < 0 || memory < 1 || memory > 32 || max_iter < 0 || max_halvings < 0 || (n > 0 && !pos) ||
         !(sigma > 0.0) || !(step0 > 0.0) || !(maxstep > 0.0))
@@ -1090,7 +1164,7 @@ int tco_lbfgsb(double* pos, int64_t n, int64_t memory, int64_t max_iter, double 
         x_to_tu(pos, n, sigma, flags, v);
         box_clamp(v, lo, hi, L);
         tu_to_x(v, n, sigma, flags, pos);
-        st = tco_grad(pos, n, g);
+        st = obj_grad(o, pos, n, g);
     }
     if (!st) {
         grad_tu(v, g, n, sigma, flags, gv);
@@ -1133,7 +1207,9 @@ int tco_lbfgsb(double* pos, int64_t n, int64_t memory, int64_t max_iter, double 
             const double gd = dot(gv, d, L);
             for (int64_t hh = 0;; ++hh) {
                 tu_to_x(vn, n, sigma, flags, pos);
-                if (instance_delta(xk, pos, n) <= 1e-4 * alpha * gd || hh == max_halvings) break;
+                double de = 0.0;
+                st = obj_delta(o, xk, pos, n, &de);
+                if (st || de <= 1e-4 * alpha * gd || hh == max_halvings) break;
                 alpha *= 0.5;
                 for (int64_t i = 0; i < L; ++i) vn[i] = v[i] + alpha * d[i];
                 box_clamp(vn, lo, hi, L);
@@ -1141,7 +1217,7 @@ int tco_lbfgsb(double* pos, int64_t n, int64_t memory, int64_t max_iter, double 
         } else {
             tu_to_x(vn, n, sigma, flags, pos);
         }
-        st = tco_grad(pos, n, g);
+        if (!st) st = obj_grad(o, pos, n, g);
         if (st) break;
         grad_tu(vn, g, n, sigma, flags, gvn);
         rms = proj_rms(vn, gvn, lo, hi, n);
@@ -1338,15 +1414,37 @@ int tco_border_split(double* pos, int64_t n, int64_t n_b, double sigma, unsigned
  *                              phase = b batch)      (steps 2-3)
  *   each zone relaxes against the batch-start snapshot with tco_subdomain_bb
  *   (step 4, projected gradient descent with BB steps, `steps` steps, free
- *   charges confined to sigma_b, pinned ones to the unit circle)
+ *   charges confined to sigma_b, pinned ones to the unit circle), or, in
+ *   tco_cycle_opt with optimizer 1, with tco_subdomain_lbfgsb (the paper's
+ *   L-BFGS-B on (t, u), interior radius sigma_b)
  *   tco_accept_sequential applies the relaxed zones in order (dE < 0, no clash).
  * trace (nullable, n_batches + 1): E before each batch and after the last.
  * delta, accepted (n_sub): per subdomain, as tco_accept_sequential. */
+int tco_cycle_opt(double* pos, int64_t n, const unsigned char* flags, double kappa, double p_defect, double sigma0,
+                  double sigma1, double wall_tol, int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub,
+                  int64_t batch, const double* uniforms, int64_t optimizer, double step0, double alpha_min,
+                  double alpha_max, int64_t memory, double maxstep, int64_t max_halvings, int64_t steps,
+                  double* trace, double* delta, unsigned char* accepted);
+
 int tco_cycle(double* pos, int64_t n, const unsigned char* flags, double kappa, double p_defect, double sigma0,
               double sigma1, double wall_tol, int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub,
               int64_t batch, const double* uniforms, double step0, double alpha_min, double alpha_max,
               int64_t steps, double* trace, double* delta, unsigned char* accepted)
 {
+    return tco_cycle_opt(pos, n, flags, kappa, p_defect, sigma0, sigma1, wall_tol, m_min, m_max, period, n_sub, batch,
+                         uniforms, 0, step0, alpha_min, alpha_max, 1, 1.0, 0, steps, trace, delta, accepted);
+}
+
+/* tco_cycle with the zone optimiser chosen: 0 = projected BB (step0,
+ * alpha_min, alpha_max), 1 = L-BFGS-B on (t, u) (memory, step0, maxstep,
+ * at most max_halvings Armijo halvings per step). */
+int tco_cycle_opt(double* pos, int64_t n, const unsigned char* flags, double kappa, double p_defect, double sigma0,
+                  double sigma1, double wall_tol, int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub,
+                  int64_t batch, const double* uniforms, int64_t optimizer, double step0, double alpha_min,
+                  double alpha_max, int64_t memory, double maxstep, int64_t max_halvings, int64_t steps,
+                  double* trace, double* delta, unsigned char* accepted)
+{
+    if (optimizer < 0 || optimizer > 1) return TCO_ERR_INVALID_ARG;
     if (n < 1 || n_sub < 0 || batch < 1 || !pos || (n_sub > 0 && (!uniforms || !delta || !accepted)))
         return TCO_ERR_INVALID_ARG;
     int64_t n_batches = (n_sub + batch - 1) / batch;
@@ -1368,8 +1466,10 @@ int tco_cycle(double* pos, int64_t n, const unsigned char* flags, double kappa, 
         st = tco_zone_select(pos, n, e, flags, kappa, p_defect, radius, wall_tol, m_min, m_max, period, b0, k,
                              uniforms + 3 * b0, idx, off, NULL, NULL);
         for (int64_t s = 0; s < k && !st; ++s)
-            st = tco_subdomain_bb(pos, n, idx + off[s], off[s + 1] - off[s], step0, alpha_min, alpha_max,
-                                  steps, radius, flags, act + 2 * off[s]);
+            st = optimizer == 0 ? tco_subdomain_bb(pos, n, idx + off[s], off[s + 1] - off[s], step0, alpha_min,
+                                                   alpha_max, steps, radius, flags, act + 2 * off[s])
+                                : tco_subdomain_lbfgsb(pos, n, idx + off[s], off[s + 1] - off[s], memory, steps,
+                                                       step0, maxstep, radius, flags, max_halvings, act + 2 * off[s]);
         if (!st) st = tco_accept_sequential(pos, n, idx, off, k, act, delta + b0, accepted + b0);
     }
     if (!st && trace) st = tco_energy(pos, n, &trace[nb], NULL);

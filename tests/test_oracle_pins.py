@@ -846,3 +846,58 @@ def test_lbfgsb_pinned_boundary_and_armijo_descent():
         assert np.all(r[f == 0] <= 0.95 * (1 + 1e-15))
         energies.append(oracle.energy(x))
     assert all(b < a for a, b in zip(energies, energies[1:]))
+
+
+def test_subdomain_lbfgsb_of_every_charge_is_the_instance():
+    """A subdomain holding every charge (E_sub gradient, pairwise energy change against the
+    snapshot) runs the same iteration as the whole-configuration L-BFGS-B."""
+    pos = synth.arcsine_disk(90, 4)
+    a = oracle.subdomain_lbfgsb(pos, np.arange(90), memory=6, steps=40, step0=1e-3, maxstep=0.05, line_search=5)
+    b, _, _, _ = oracle.lbfgsb(pos, memory=6, max_iter=40, step0=1e-3, maxstep=0.05, line_search=5)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", ["ring_two", "ring_three", "wall"])
+def test_subdomain_lbfgsb_single_charge_reaches_the_constrained_minimum(case):
+    """One moving charge against fixed ones: L-BFGS-B on (t, u) ends at the minimiser of its own
+    energy sum_j 1/|x - s_j| over |x| <= sigma that scipy's SLSQP finds in Cartesian coordinates from
+    the same start (interior minima, and one on the wall |x| = sigma, where t = pi/2 is active)."""
+    from scipy.optimize import minimize
+
+    ang = 2 * np.pi * np.arange(12) / 12
+    ring = np.stack([np.cos(ang), np.sin(ang)], 1)
+    bg, start = {
+        "ring_two": (np.vstack([ring, [[0.0, 0.45], [0.0, -0.45]]]), [0.5, 0.12]),
+        "ring_three": (np.vstack([ring, [[0.0, 0.45], [0.0, -0.45], [-0.5, 0.0]]]), [0.45, 0.1]),
+        "wall": (np.array([[0.1, 0.05], [0.05, -0.1], [-0.1, 0.02], [0.3, 0.25]]), [0.5, 0.3]),
+    }[case]
+    snap = np.vstack([bg, [start]])
+    k = snap.shape[0] - 1
+    act = oracle.subdomain_lbfgsb(snap, [k], memory=5, steps=300, step0=1e-3, maxstep=0.05, radius=0.9)[0]
+    energy = lambda x: sum(1.0 / math.hypot(x[0] - s[0], x[1] - s[1]) for s in bg)
+    ref = minimize(energy, np.array(start), method="SLSQP", constraints=[{"type": "ineq", "fun": lambda x: 0.81 - x @ x}],
+                   options={"ftol": 1e-16, "maxiter": 1000}).x
+    np.testing.assert_allclose(act, ref, rtol=0, atol=1e-7)
+    if case == "wall":
+        assert abs(math.hypot(*act) - 0.9) <= 1e-15
+
+
+def test_cycle_with_lbfgsb_zones_keeps_its_bookkeeping():
+    """The cycle with L-BFGS-B per zone: E_{b+1} - E_b is the sum of batch b's accepted energy changes,
+    the energy never rises, pinned charges stay on the circle and free ones inside the final sigma."""
+    n = 1200
+    pos = synth.arcsine_disk(n, 21)
+    s0 = 1 - 1 / (2 * math.sqrt(n))
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
+    u = np.random.default_rng(22).random((9, 3))
+    p, trace, d, acc = oracle.cycle(p0, u, m_min=20, m_max=150, period=4, batch=3, step0=1e-4, alpha_min=0.0,
+                                    alpha_max=0.0, steps=12, sigma0=s0, sigma1=1.0, flags=f, optimizer="lbfgsb_tu",
+                                    memory=6, maxstep=0.02, line_search=4)
+    assert np.all(np.diff(trace) <= 0)
+    for b in range(3):
+        sl = slice(3 * b, 3 * b + 3)
+        assert abs((trace[b + 1] - trace[b]) - d[sl][acc[sl] == 1].sum()) <= 1e-12 * trace[b]
+    r = np.hypot(p[:, 0], p[:, 1])
+    assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
+    assert np.all(r[f == 0] <= 1.0 + 1e-15)
+    assert (acc == 1).sum() >= 3
