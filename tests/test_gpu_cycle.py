@@ -226,3 +226,33 @@ def test_cycle_pinned_sigma_ramp_fp64_matches_oracle(batch):
     x = p.cpu().numpy()
     rr = np.hypot(x[:, 0], x[:, 1])
     assert np.all(np.abs(rr[f == 1] - 1.0) <= 4.5e-16)
+
+
+@pytest.mark.parametrize("batch,line_search", [(3, 0), (4, 4)])
+def test_cycle_lbfgsb_zones_fp64_matches_oracle(batch, line_search):
+    """The paper's cycle with its optimiser: L-BFGS-B on (t, u) per zone (Sec. II C step 4, Sec. II D)
+    after the border-interior split, float64 throughout; accept decisions equal, charges to 1e-9."""
+    n = 1500
+    pos = synth.arcsine_disk(n, 13)
+    s0 = 1 - 1 / (2 * np.sqrt(n))
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
+    u = np.random.default_rng(15).random((12, 3))
+    kw = dict(m_min=20, m_max=150, period=4)
+    po, trace_o, do, ao = oracle.cycle(p0, u, batch=batch, step0=1e-4, alpha_min=0.0, alpha_max=0.0, steps=12,
+                                       sigma0=s0, sigma1=1.0, flags=f, optimizer="lbfgsb_tu", memory=6,
+                                       maxstep=0.02, line_search=line_search, **kw)
+    p = T(p0.copy())
+    r, trace = tc.cycle(p, T(u), T(f), batch=batch, local_precision="fp64", precision="fp64",
+                        optimizer="lbfgsb_tu", n_steps=12, memory=6, step0=1e-4, maxstep=0.02,
+                        line_search=line_search, sigma0=s0, sigma1=1.0, **kw)
+    tc.sync_status()
+    np.testing.assert_array_equal(r.status.cpu().numpy(), ao)
+    assert (ao == 1).sum() >= 3
+    np.testing.assert_allclose(p.cpu().numpy(), po, rtol=0, atol=1e-9)
+    # charges within 1e-9 move E by at most sum_i |g_i| 1e-9, a few 1e-10 of E here; the last
+    # trace entry is E of the GPU's own final configuration, to float64 summation accuracy
+    np.testing.assert_allclose(trace.cpu().numpy(), trace_o, rtol=1e-9)
+    eg = oracle.energy(p.cpu().numpy())
+    assert abs(trace[-1].item() - eg) <= 1e-13 * eg
+    d = r.delta_e.cpu().numpy()
+    np.testing.assert_allclose(d[ao == 1], do[ao == 1], rtol=1e-6, atol=1e-9)

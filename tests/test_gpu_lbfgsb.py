@@ -122,3 +122,30 @@ def test_lbfgsb_rejects_unsupported_sizes():
     with pytest.raises(tc.TCError):
         tc.relax_subdomains(big, world=T(np.array([[0, 16385]], dtype=np.int64)), precision="fp64",
                             optimizer="lbfgsb_tu", n_steps=1, memory=4, step0=1e-4, maxstep=0.02, accept=False)
+
+
+def test_lbfgsb_degenerate_instances_match_oracle():
+    """Instances of 1, 2 and 5 charges, and one whose charges are all pinned to the circle."""
+    sizes = [1, 2, 5, 9]
+    pos = np.concatenate([synth.arcsine_disk(m, 70 + m) for m in sizes])
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    world = np.stack([off[:-1], off[1:]], 1).astype(np.int64)
+    flags = np.zeros(len(pos), dtype=np.uint8)
+    flags[off[3]:off[4]] = 1
+    p0 = pos.copy()
+    r0 = np.hypot(p0[:, 0], p0[:, 1])
+    p0[flags == 1] /= r0[flags == 1, None]
+    p = T(p0.copy())
+    iters = 20
+    tc.relax_subdomains(p, world=T(world), flags=T(flags), precision="fp64", optimizer="lbfgsb_tu", n_steps=iters,
+                        memory=4, step0=1e-3, maxstep=0.05, accept=False)
+    tc.sync_status()
+    x = p.cpu().numpy()
+    for k in range(len(sizes)):
+        b, e = off[k], off[k + 1]
+        xo, _, _, _ = oracle.lbfgsb(p0[b:e], memory=4, max_iter=iters, step0=1e-3, maxstep=0.05, flags=flags[b:e])
+        assert np.abs(x[b:e] - xo).max() <= 1e-9
+    rr = np.hypot(x[:, 0], x[:, 1])
+    assert np.all(np.abs(rr[flags == 1] - 1.0) <= 4.5e-16)
+    # a lone charge feels no force: it moves only by the rounding of x -> (t, u) -> x
+    np.testing.assert_allclose(x[0], p0[0], rtol=0, atol=4e-16)
