@@ -59,6 +59,29 @@ def test_argument_errors_are_synchronous_without_touching_a_device(lib):
     cp = L.CycleParams(zone=z, batch=1, sigma0=0.5, sigma1=0.4)  # sigma must not fall
     assert lib.tc_cycle(None, 10, None, C.byref(cp), 1, None, None, None, None) == 1
     assert lib.tc_border_split(None, 10, 11, 0.9, None, None) == 1  # n_b > n
+    # L-BFGS-B keeps at most 8 pairs; an optimizer past the last is rejected
+    ok = dict(precision=0, n_steps=1, memory=8, step0=1e-3, maxstep=0.01, radius=1.0)
+    prm = L.RelaxParams(optimizer=L.TC_OPT_LBFGSB_TU, **{**ok, "memory": 9})
+    assert lib.tc_relax_subdomains(None, 10, None, None, 1, None, None, C.byref(prm), None, None) == 1
+    prm = L.RelaxParams(optimizer=L.TC_OPT_LBFGSB_TU + 1, **ok)
+    assert lib.tc_relax_subdomains(None, 10, None, None, 1, None, None, C.byref(prm), None, None) == 1
+
+
+def test_enum_values_match_header():
+    """Every enumerator that the binding names has the header's value."""
+    import os
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(L.__file__), "..", "include", "tc.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    values = {}
+    for body in re.findall(r"typedef enum\s*\{(.*?)\}", hdr, flags=re.S):
+        for name, val in re.findall(r"(TC_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+            values[name] = int(val)
+    named = {k: getattr(L, k) for k in dir(L) if k.startswith("TC_") and isinstance(getattr(L, k), int)}
+    assert {"TC_OPT_LBFGSB_TU", "TC_F64X", "TC_MIXED"} <= set(named)
+    for k, v in named.items():
+        assert k in values and values[k] == v, k
 
 
 def test_boundary_count_host_only_matches_oracle(lib):
