@@ -158,9 +158,9 @@ typedef enum {
     TC_OPT_LBFGSB_TU = 4 /* L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995), the optimiser Sec. II C step 4
                             names, on the same (t, u) with the box t in [0, pi/2]: generalized
                             Cauchy point, direct-primal subspace minimisation, then the capped
-                            step (and line search) below.  memory 1..8; every problem at most
-                            16384 charges (else TC_ERR_INVALID_ARG); rms is the RMS of the
-                            projected gradient P(v - g) - v */
+                            step (and line search) below.  memory 1..8; one CTA steps each
+                            problem, so a problem of many thousand charges steps slowly;
+                            rms is the RMS of the projected gradient P(v - g) - v */
 } tc_optimizer;
 
 typedef struct {

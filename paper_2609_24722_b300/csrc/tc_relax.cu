@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
 // ------------------------------------------------------------ L-BFGS-B ---
 // L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995), the optimiser of Sec. II C step 4,
 // on the (t, u) variables of Sec. II D with the box t in [0, pi/2], one CTA per
-// problem of at most kLargeRows rows.  A pinned charge's variables are (u, 0):
+// problem of any size (its time grows with the problem's rows).  A pinned charge's variables are (u, 0):
 // u unbounded, the second fixed at 0.
 //
 // Compact representation B = theta I - W M W^T, M = K^{-1},
@@ -592,25 +592,37 @@ template <int N> __device__ void block_sums_w(double (&v)[N], double (*red)[kRed
     __syncthreads();
 }
 
+// Smallest (t, row) over a warp, ties to the lower row; every lane gets it (a
+// minimum with a fixed tie rule does not depend on the order of comparisons).
+__device__ __forceinline__ void warp_argmin(double& t, int& r)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t2 = __shfl_xor_sync(0xffffffffu, t, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+        if (t2 < t || (t2 == t && r2 < r)) {
+            t = t2;
+            r = r2;
+        }
+    }
+}
+
 // Smallest (t, row) over the block, ties to the lower row.
 __device__ void block_argmin(double& t, int& r, double* sht, int* shr)
 {
-    sht[threadIdx.x] = t;
-    shr[threadIdx.x] = r;
-    __syncthreads();
-    for (int w = kUpd / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            const double t2 = sht[threadIdx.x + w];
-            const int r2 = shr[threadIdx.x + w];
-            if (t2 < sht[threadIdx.x] || (t2 == sht[threadIdx.x] && r2 < shr[threadIdx.x])) {
-                sht[threadIdx.x] = t2;
-                shr[threadIdx.x] = r2;
-            }
-        }
-        __syncthreads();
+    warp_argmin(t, r);
+    if ((threadIdx.x & 31) == 0) {
+        sht[threadIdx.x >> 5] = t;
+        shr[threadIdx.x >> 5] = r;
     }
+    __syncthreads();
     t = sht[0];
     r = shr[0];
+    for (int w = 1; w < kUpd / 32; ++w)
+        if (sht[w] < t || (sht[w] == t && shr[w] < r)) {
+            t = sht[w];
+            r = shr[w];
+        }
     __syncthreads();
 }
 
@@ -959,18 +971,22 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     __syncthreads();
     const double fpp0 = bc[3];
     const bool moves = fpp0 > 0.0;
-    // visit the breakpoints in increasing (t, row) while the segment minimiser lies beyond them
-    while (bflag[1]) {
-        double tmin = INFINITY;
-        int rmin = INT_MAX;
-        TC_ROWS(p)
-        {
-            const double t = d.bp[p.row_base + rl];
-            if (t > 0.0 && t < tmin) {
-                tmin = t;
-                rmin = (int)rl;
-            }
+    // visit the breakpoints in increasing (t, row) while the segment minimiser lies beyond them;
+    // each thread keeps the smallest (t, row) of its own rows and rescans them only when the
+    // breakpoint just fixed was one of them
+    double own_t = INFINITY;
+    int own_r = INT_MAX;
+    TC_ROWS(p)
+    {
+        const double t = d.bp[p.row_base + rl];
+        if (t > 0.0 && t < own_t) {
+            own_t = t;
+            own_r = (int)rl;
         }
+    }
+    while (bflag[1]) {
+        double tmin = own_t;
+        int rmin = own_r;
         block_argmin(tmin, rmin, sh, shi);
         if (threadIdx.x < 32) {
             const double told = bc[0], dtm = bc[1];
@@ -1025,6 +1041,26 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
             }
         }
         __syncthreads();
+        if (bflag[1] && rmin != INT_MAX) {
+            // the owner's warp rescans the owner's rows, 32 at a time
+            const int owner = rmin % kUpd;
+            if ((int)(threadIdx.x >> 5) == (owner >> 5)) {
+                double tb = INFINITY;
+                int rb_ = INT_MAX;
+                for (int64_t rl = owner + (int64_t)lane * kUpd; rl < p.m; rl += 32LL * kUpd) {
+                    const double t = d.bp[p.row_base + rl];
+                    if (t > 0.0 && t < tb) {
+                        tb = t;
+                        rb_ = (int)rl;
+                    }
+                }
+                warp_argmin(tb, rb_);
+                if ((int)threadIdx.x == owner) {
+                    own_t = tb;
+                    own_r = rb_;
+                }
+            }
+        }
     }
     if (threadIdx.x < 32 && moves) {
         const double dtm = fmax(bc[1], 0.0);
@@ -2107,13 +2143,10 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int64_t M = P.M;
     const int64_t taken_words = (n + 31) / 32;
     LargeSet large;
-    if (lbfgs)
+    // L-BFGS-B steps every problem with one CTA, whatever its size
+    if (lbfgs && !boxed)
         for (int32_t k = 0; k < n_sub; ++k)
             if (P.prob[k].m > kLargeRows) large.ids.push_back(k);
-    if (boxed && !large.ids.empty()) {
-        set_last_error("tc_relax_subdomains: L-BFGS-B takes problems of at most 16384 charges");
-        return TC_ERR_INVALID_ARG;
-    }
 
     Carver c;
     fx3* snap3 = nullptr;

@@ -112,16 +112,29 @@ def test_lbfgsb_mixed_with_polish_keeps_the_box():
     assert abs(r.energy[0].item() - eg) <= 1e-12 * eg
 
 
-def test_lbfgsb_rejects_unsupported_sizes():
+def test_lbfgsb_rejects_more_than_eight_pairs():
     pos = T(synth.arcsine_disk(100, 1))
     world = T(np.array([[0, 100]], dtype=np.int64))
     with pytest.raises(tc.TCError):
         tc.relax_subdomains(pos, world=world, precision="fp64", optimizer="lbfgsb_tu", n_steps=2, memory=9,
                             step0=1e-4, maxstep=0.02, accept=False)
-    big = T(synth.arcsine_disk(16385, 2))
-    with pytest.raises(tc.TCError):
-        tc.relax_subdomains(big, world=T(np.array([[0, 16385]], dtype=np.int64)), precision="fp64",
-                            optimizer="lbfgsb_tu", n_steps=1, memory=4, step0=1e-4, maxstep=0.02, accept=False)
+
+
+def test_lbfgsb_large_instance_matches_oracle():
+    """An instance of 17 000 charges (more than the grid-wide L-BFGS path's threshold): one CTA
+    steps it, on the same iteration as the oracle."""
+    n = 17000
+    pos = synth.arcsine_disk(n, 81)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    p = T(pos.copy())
+    iters = 4
+    r = tc.relax_subdomains(p, world=T(np.array([[0, n]], dtype=np.int64)), precision="fp64",
+                            optimizer="lbfgsb_tu", n_steps=iters, memory=4, step0=1e-5, maxstep=0.01, accept=False)
+    tc.sync_status()
+    xo, _, rms, nb = oracle.lbfgsb(pos, memory=4, max_iter=iters, step0=1e-5, maxstep=0.01)
+    assert nb >= 1
+    assert np.abs(p.cpu().numpy() - xo).max() <= 1e-9
+    assert abs(r.rms[0].item() - rms) <= 1e-6 * rms
 
 
 def test_lbfgsb_degenerate_instances_match_oracle():
