@@ -524,8 +524,8 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
 // ------------------------------------------------------------ L-BFGS-B ---
 // L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995), the optimiser of Sec. II C step 4,
 // on the (t, u) variables of Sec. II D with the box t in [0, pi/2], one CTA per
-// problem of any size (its time grows with the problem's rows).  A pinned charge's variables are (u, 0):
-// u unbounded, the second fixed at 0.
+// problem of any size (its time grows with the problem's rows).  A pinned
+// charge's variables are (u, 0): u unbounded, the second fixed at 0.
 //
 // Compact representation B = theta I - W M W^T, M = K^{-1},
 // K = [[-D, L^T], [L, theta S S^T]] (Byrd, Nocedal & Schnabel 1994), in padded
@@ -685,16 +685,6 @@ __device__ __forceinline__ double dot16(const double (&w)[kBQ], const double* v)
 #pragma unroll
     for (int a = 0; a < kBQ; ++a) s += w[a] * v[a];
     return s;
-}
-
-// y = M x (padded), sums in entry order.
-__device__ __forceinline__ void matvec16(const double* M, const double* x, double* y)
-{
-    for (int a = 0; a < kBQ; ++a) {
-        double s = 0.0;
-        for (int b = 0; b < kBQ; ++b) s += M[a * kBQ + b] * x[b];
-        y[a] = s;
-    }
 }
 
 // Row a of M x (sums in entry order); one lane per row.
