@@ -647,6 +647,16 @@ def main():
                 "peak_source": "measured: tc_probe_pipes FFMA lane-ops/s / 8 and MUFU.RSQ/s, this run",
                 "frac_of_pairmix_ceiling": achieved / pipes["pairmix_per_s"],
                 "pipe_peaks": pipes}
+    # the plain float64 form beside it: the all-pairs E + grad at N = 1e5 against the float64 pipe.
+    # Float64-pipe operations per ordered pair: dx, dy; r^2 as a mul and an fma; 1/r from a float32
+    # seed by one series step (mul, fma, fma, mul, fma); r^-3 as two muls; two gradient fmas; one
+    # energy add: 14.
+    fp64_achieved = N * (N - 1) / (ms_f64 / 1e3)
+    fp64_peak = pipes["dfma_per_s"] / 14.0
+    roofline_fp64 = {"bound": "fp64", "achieved": fp64_achieved / 1e9, "peak": fp64_peak / 1e9, "unit": "Gpair/s",
+                     "frac": fp64_achieved / fp64_peak, "kernel": "k_pass<F64, E+grad> (all pairs, N=1e5)",
+                     "ops_per_pair": 14,
+                     "peak_source": "measured: tc_probe_pipes DFMA ops/s / 14, this run"}
 
     if rank != 0:
         if world > 1:
@@ -677,6 +687,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": args.steps * (prof["launches"] + 3),
         "roofline": roofline,
+        "roofline_fp64": roofline_fp64,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
