@@ -66,6 +66,7 @@ struct RelaxDev {
     double* bp;            // per row: breakpoint of the row's t in the Cauchy search (L-BFGS-B)
     double2* xc;           // per row: generalized Cauchy point (L-BFGS-B)
     double* bsmall;        // per problem: s.y and s.s of the stored pairs by slot, theta (L-BFGS-B)
+    int* any_active;       // one int: some problem still steps (early stop between graph replays)
 };
 
 __device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, int64_t row)
@@ -1937,94 +1938,161 @@ static cudaError_t line_search(RelaxDev& d, const LsArgs& ls, const Plan& P, con
     return e;
 }
 
+// Steps captured in one CUDA graph and replayed (the last chunk may be shorter).
+constexpr int kChunkSteps = 64;
+
+// OR of the problems' active flags, for the host's early stop between chunks.
+__global__ void k_any_active(const int* __restrict__ active, int S, int* __restrict__ any)
+{
+    __shared__ int sh;
+    if (threadIdx.x == 0) sh = 0;
+    __syncthreads();
+    int a = 0;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) a |= active[k] != 0;
+    if (a) sh = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) *any = sh;
+}
+
+// The launches of one step (pass, optimiser update, line search) on stream st;
+// ev_mid (nullable) is recorded between the pass and the update.
+template <int KIND>
+static cudaError_t launch_step(RelaxDev& d, const PassArgs& a, const Plan& P, int64_t G, const StepParams& sp,
+                               cudaStream_t st, int& launches, const LargeSet& large, const LsArgs* ls,
+                               cudaEvent_t ev_mid)
+{
+    const SlotView v{P.W, G, 0, P.M, 0};
+    cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
+    if (e != cudaSuccess) return e;
+    if (ev_mid && (e = cudaEventRecord(ev_mid, st)) != cudaSuccess) return e;
+    if (sp.opt == TC_OPT_LBFGSB_TU) {
+        k_update_lbfgsb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
+        if (ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, st, launches);
+    } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
+        k_update_lbfgs<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
+        for (size_t q = 0; q < large.ids.size(); ++q) {
+            LbArgs la{large.ids[q], large.part, large.sc + q};
+            if (e == cudaSuccess) e = lbfgs_large(d, la, a.part_g, v, sp, st);
+            launches += 2 * (2 * sp.memory + 1) + 6;
+        }
+        if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, st, launches);
+    } else {
+        k_update_gdbb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
+    }
+    launches += (a.W > 0 ? 1 : 0) + 1;
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// One more pass at the final rows and a measuring update: the reported RMS
+// describes the returned configuration.
+template <int KIND>
+static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P, int64_t G, const StepParams& sp,
+                                  cudaStream_t st, int& launches, const LargeSet& large)
+{
+    const SlotView v{P.W, G, 0, P.M, 0};
+    cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
+    if (e != cudaSuccess) return e;
+    StepParams sm = sp;
+    sm.measure = 1;
+    if (sp.opt == TC_OPT_LBFGSB_TU) {
+        k_update_lbfgsb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
+    } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
+        k_update_lbfgs<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
+        for (size_t q = 0; q < large.ids.size(); ++q) {
+            LbArgs la{large.ids[q], large.part, large.sc + q};
+            k_lb_grad<<<kLargeBlocks, kUpd, 0, st>>>(d, la, a.part_g, v, sm);
+            k_lb_decide<<<1, 32, 0, st>>>(d, la, sm);
+            launches += 2;
+        }
+    } else {
+        k_update_gdbb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
+    }
+    launches += (a.W > 0 ? 1 : 0) + 1;
+    return cudaGetLastError();
+}
+
+// The step loop of one phase.  Three ways to launch it:
+//  - profiled: directly on s, with an event between each pass and update;
+//  - inside a caller's stream capture: every step joins the caller's graph;
+//  - otherwise: kChunkSteps steps are captured once on a private stream and the
+//    graph is replayed on s; with a stopping tolerance the host checks between
+//    replays whether any problem is still active and stops when none is (the
+//    steps it skips would have been no-ops: every kernel returns at once for an
+//    inactive problem).  A shorter last chunk is launched directly.
 template <int KIND>
 static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, const StepParams& sp, int steps,
                            cudaStream_t s, bool prof, int& launches, const LargeSet& large,
                            const LsArgs* ls = nullptr)
 {
     if (steps <= 0) return TC_OK;
-    size_t ev0 = 0;  // events 0 .. 2 steps: [pass k] between 2k and 2k+1, [update k] between 2k+1 and 2k+2
-    SlotView v{P.W, G, 0, P.M, 0};
     cudaStreamCaptureStatus cs;
     if (cudaError_t e_ = cudaStreamIsCapturing(s, &cs); e_ != cudaSuccess) return cuda_fail(e_, "cudaStreamIsCapturing");
-    // Inside a caller's capture the launches simply join the caller's graph;
-    // otherwise the loop is captured on a private stream and replayed on s.
-    // A profiled call launches directly on s, with an event between launches.
-    const bool capture = cs == cudaStreamCaptureStatusNone && !prof;
-    cudaStream_t cap = s;
-    if (capture) {
-        tc_status err = TC_OK;
-        cap = capture_stream(&err);
-        if (!cap) return err;
-        if (cudaError_t e_ = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal); e_ != cudaSuccess) return cuda_fail(e_, "cudaStreamBeginCapture");
-    }
     cudaError_t e = cudaSuccess;
     const char* where = "step loop launch";
-    if (prof) e = cudaEventRecord(g_events.get(ev0), cap);
-    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-        e = launch_pass<KIND, false, true>(a, G, 0, 0, cap);
-        if (e != cudaSuccess) break;
-        if (prof) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 1), cap);
-        if (sp.opt == TC_OPT_LBFGSB_TU) {
-            k_update_lbfgsb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
-            if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, cap, launches);
-        } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
-            k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
-            for (size_t q = 0; q < large.ids.size(); ++q) {
-                LbArgs la{large.ids[q], large.part, large.sc + q};
-                if (e == cudaSuccess) e = lbfgs_large(d, la, a.part_g, v, sp, cap);
-                launches += 2 * (2 * sp.memory + 1) + 6;
+    if (prof) {
+        // events 0 .. 2 steps: [pass k] between 2k and 2k+1, [update k] between 2k+1 and 2k+2
+        e = cudaEventRecord(g_events.get(0), s);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            e = launch_step<KIND>(d, a, P, G, sp, s, launches, large, ls, g_events.get(2 * k + 1));
+            if (e == cudaSuccess) e = cudaEventRecord(g_events.get(2 * k + 2), s);
+        }
+        if (e == cudaSuccess) e = launch_measure<KIND>(d, a, P, G, sp, s, launches, large);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < steps; ++k) {
+                g_last_profile.pass_ms += elapsed(g_events.get(2 * k), g_events.get(2 * k + 1));
+                g_last_profile.update_ms += elapsed(g_events.get(2 * k + 1), g_events.get(2 * k + 2));
             }
-            if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, cap, launches);
-        } else {
-            k_update_gdbb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sp);
+            g_last_profile.relax_ms += elapsed(g_events.get(0), g_events.get(2 * steps));
+            g_last_profile.n_pass += a.W > 0 ? steps : 0;
         }
-        if (e == cudaSuccess) e = cudaGetLastError();
-        if (prof && e == cudaSuccess) e = cudaEventRecord(g_events.get(ev0 + 2 * k + 2), cap);
-        launches += (a.W > 0 ? 1 : 0) + 1;
+        return cuda_status(e, where);
     }
-    // one more pass at the final rows: the reported RMS describes the returned configuration
-    if (e == cudaSuccess) e = launch_pass<KIND, false, true>(a, G, 0, 0, cap);
-    if (e == cudaSuccess) {
-        StepParams sm = sp;
-        sm.measure = 1;
-        if (sp.opt == TC_OPT_LBFGSB_TU) {
-            k_update_lbfgsb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sm);
-        } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
-            k_update_lbfgs<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sm);
-            for (size_t q = 0; q < large.ids.size(); ++q) {
-                LbArgs la{large.ids[q], large.part, large.sc + q};
-                k_lb_grad<<<kLargeBlocks, kUpd, 0, cap>>>(d, la, a.part_g, v, sm);
-                k_lb_decide<<<1, 32, 0, cap>>>(d, la, sm);
-                launches += 2;
+    if (cs != cudaStreamCaptureStatusNone) {
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_step<KIND>(d, a, P, G, sp, s, launches, large, ls, nullptr);
+        if (e == cudaSuccess) e = launch_measure<KIND>(d, a, P, G, sp, s, launches, large);
+        return cuda_status(e, where);
+    }
+    const int K = std::min(steps, kChunkSteps);
+    tc_status err = TC_OK;
+    cudaStream_t cap = capture_stream(&err);
+    if (!cap) return err;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int per_chunk = 0;
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    for (int k = 0; k < K && e == cudaSuccess; ++k) e = launch_step<KIND>(d, a, P, G, sp, cap, per_chunk, large, ls, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e == cudaSuccess && (e = e2) != cudaSuccess) where = "cudaStreamEndCapture";
+    if (e == cudaSuccess && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) where = "cudaGraphInstantiate";
+    int done = 0;
+    while (e == cudaSuccess && done + K <= steps) {
+        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+            where = "cudaGraphLaunch";
+            break;
+        }
+        done += K;
+        launches += per_chunk;
+        if (done < steps && sp.gtol > 0.0) {
+            int any = 1;
+            k_any_active<<<1, 256, 0, s>>>(d.active, d.S, d.any_active);
+            ++launches;
+            if ((e = cudaMemcpyAsync(&any, d.any_active, sizeof(int), cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+                e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                where = "step loop execution";
+                break;
             }
-        } else {
-            k_update_gdbb<<<d.S, kUpd, 0, cap>>>(d, a.part_g, v, sm);
+            if (!any) done = steps;  // every problem has stopped
         }
-        e = cudaGetLastError();
-        launches += (a.W > 0 ? 1 : 0) + 1;
     }
-    if (capture) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-        if (e == cudaSuccess && (e = e2) != cudaSuccess) where = "cudaStreamEndCapture";
-        if (e == cudaSuccess && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) where = "cudaGraphInstantiate";
-        if (e == cudaSuccess && (e = cudaGraphLaunch(exec, s)) != cudaSuccess) where = "cudaGraphLaunch";
-        // the executable graph is destroyed only after its launch has finished
-        if (e == cudaSuccess && (e = cudaStreamSynchronize(s)) != cudaSuccess) where = "step loop execution";
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-    }
-    if (prof && e == cudaSuccess) {
-        if (!capture) e = cudaStreamSynchronize(s);
-        for (int k = 0; k < steps; ++k) {
-            g_last_profile.pass_ms += elapsed(g_events.get(ev0 + 2 * k), g_events.get(ev0 + 2 * k + 1));
-            g_last_profile.update_ms += elapsed(g_events.get(ev0 + 2 * k + 1), g_events.get(ev0 + 2 * k + 2));
-        }
-        g_last_profile.relax_ms += elapsed(g_events.get(ev0), g_events.get(ev0 + 2 * steps));
-        g_last_profile.n_pass += a.W > 0 ? steps : 0;
-    }
+    for (; e == cudaSuccess && done < steps; ++done) e = launch_step<KIND>(d, a, P, G, sp, s, launches, large, ls, nullptr);
+    if (e == cudaSuccess) e = launch_measure<KIND>(d, a, P, G, sp, s, launches, large);
+    // the executable graph is destroyed only after its launches have finished
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && (e = e3) != cudaSuccess) where = "step loop execution";
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
     return cuda_status(e, where);
 }
 
@@ -2159,6 +2227,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         d.bp = cv.take<double>(boxed ? M : 0);
         d.xc = cv.take<double2>(boxed ? M : 0);
         d.bsmall = cv.take<double>(boxed ? (size_t)n_sub * kBSmall : 0);
+        d.any_active = cv.take<int>(1);
         d.rows4 = cv.take<d4>(M);
         d.rows8 = ls_on ? cv.take<f8>(M) : nullptr;
         d.xold = ls_on ? cv.take<double2>(M) : nullptr;
