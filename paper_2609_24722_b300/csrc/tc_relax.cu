@@ -1366,6 +1366,7 @@ __global__ void k_lb_decide(RelaxDev d, LbArgs la, StepParams sp)
     if (threadIdx.x != 0) return;
     LbScal& c = *la.sc;
     c.done = 1;
+    c.keep = 0;  // a stopped problem stores no pair (k_lb_store runs every step)
     if (!d.active[la.s]) return;
     const Prob p = d.prob[la.s];
     const int k = d.steps[la.s];

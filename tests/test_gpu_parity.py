@@ -399,3 +399,28 @@ def test_sampled_rows_at_full_size():
     # Euler's identity for the degree -1 energy holds for the full float64 result
     gfull = tc.grad(p, "fp64").cpu().numpy()
     assert abs((pos * gfull).sum() + ed.item()) <= 1e-11 * ed.item()
+
+
+@pytest.mark.parametrize("n", [2000, 17000])
+def test_lbfgs_tolerance_stop_then_polish_equals_one_run(n):
+    """A float64 L-BFGS phase that stops on its tolerance, then a float64 polish that keeps the
+    history, takes the same steps as one uninterrupted run of as many steps (the converged point's
+    gradient is recomputed, its pair fails the curvature test, and the direction is the same).
+    n = 17000 takes the grid-wide update of large problems."""
+    pos = synth.arcsine_disk(n, 91)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    world = T(np.array([[0, n]], dtype=np.int64))
+    kw = dict(precision="fp64", optimizer="lbfgs", memory=8, step0=1e-5, maxstep=0.01, accept=False)
+    p = T(pos.copy())
+    r = tc.relax_subdomains(p, world=world, n_steps=30, **kw)
+    tc.sync_status()
+    gtol = 1.0001 * r.rms[0].item()
+    pa = T(pos.copy())
+    ra = tc.relax_subdomains(pa, world=world, n_steps=300, gtol=gtol, polish_steps=12, polish_gtol=0.0, **kw)
+    tc.sync_status()
+    k = int(ra.steps[0])
+    assert 12 < k <= 30 + 12  # the first phase stopped on its tolerance
+    pb = T(pos.copy())
+    tc.relax_subdomains(pb, world=world, n_steps=k, **kw)
+    tc.sync_status()
+    np.testing.assert_array_equal(pa.cpu().numpy(), pb.cpu().numpy())
