@@ -217,6 +217,12 @@ typedef struct {
  *   flags   [n]         nullable; nonzero = pinned to the unit circle
  *   prm                 HOST pointer to the parameters
  *   out     [n_sub]     DEVICE results
+ * Synchronises `stream`: it reads the sizes to the host first and returns
+ * when the results are written.  The step loop runs as a 64-step CUDA graph
+ * replayed on `stream`.  With gtol (or polish_gtol) > 0, the host checks
+ * between replays whether any problem still steps, and stops once none
+ * does.  Called while `stream` is being captured, every step joins the
+ * caller's graph instead.
  * Device errors: TC_ERR_INVALID_ARG (index set), TC_ERR_NONFINITE, TC_ERR_OUTSIDE_DISK. */
 tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
                               int32_t n_sub, const int64_t* world, const uint8_t* flags,

@@ -18,8 +18,9 @@ namespace tc {
 
 constexpr int kUpd = 256;   // update / reduction CTA size
 constexpr int kMaxMem = 16; // largest L-BFGS memory
-// Problems with more rows than this take the L-BFGS update as a sequence of
-// grid-wide launches instead of one CTA.
+// Problems with more rows than this take the L-BFGS update (smooth map or
+// (t, u)) as a sequence of grid-wide launches instead of one CTA; L-BFGS-B
+// always runs one CTA per problem.
 constexpr int kLargeRows = 16384;
 constexpr int kLargeBlocks = 296;  // CTAs of the grid-wide update launches
 
