@@ -22,6 +22,10 @@
  *   Sec. II C, steps 2-4: defect threshold on the local energies, centre
  *       choice (defect charge or uniform point), the zone around the centre,
  *       and the optimisation cycle built from them.
+ *   Sec. II C step 4 + Sec. II D: L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995) on
+ *       the (t, u) variables with the box t in [0, pi/2], for a whole
+ *       configuration or a subdomain against the fixed others, and the cycle
+ *       with it as the zone optimiser.
  *
  * Parity status: every function here is pinned by tests against closed forms,
  * brute force in extended precision, invariants or the paper's asymptotic
