@@ -901,3 +901,30 @@ def test_cycle_with_lbfgsb_zones_keeps_its_bookkeeping():
     assert np.all(np.abs(r[f == 1] - 1.0) <= 4.5e-16)
     assert np.all(r[f == 0] <= 1.0 + 1e-15)
     assert (acc == 1).sum() >= 3
+
+
+def test_cycle_with_lbfgsb_zones_is_its_steps_in_order():
+    """With one zone per batch, the cycle is: local energies, the zone of batch b at sigma_b, L-BFGS-B
+    on that zone against the rest, the float64 accept; rebuilt here from those oracle pieces."""
+    n = 400
+    pos = synth.arcsine_disk(n, 31)
+    s0 = 1 - 1 / (2 * math.sqrt(n))
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
+    u = np.random.default_rng(32).random((5, 3))
+    kw = dict(m_min=10, m_max=60, period=4)
+    p, trace, d, acc = oracle.cycle(p0, u, batch=1, step0=1e-4, alpha_min=0.0, alpha_max=0.0, steps=6,
+                                    sigma0=s0, sigma1=1.0, flags=f, optimizer="lbfgsb_tu", memory=5,
+                                    maxstep=0.02, line_search=3, **kw)
+    q = p0.copy()
+    for b in range(5):
+        radius = oracle.sigma_ramp(s0, 1.0, b, 5)
+        e_tot, e_loc = oracle.energy(q, local=True)
+        assert trace[b] == e_tot
+        idx, off, _, _ = oracle.zone_select(q, e_loc, u[b:b + 1], phase=b, radius=radius, flags=f, **kw)
+        act = oracle.subdomain_lbfgsb(q, idx, memory=5, steps=6, step0=1e-4, maxstep=0.02, radius=radius,
+                                      flags=f, line_search=3)
+        q, db, ab = oracle.accept_sequential(q, idx, off, act)
+        assert db[0] == d[b] and ab[0] == acc[b]
+    np.testing.assert_array_equal(p, q)
+    assert trace[5] == oracle.energy(q)
+    assert (acc == 1).sum() >= 3  # the zones really move
