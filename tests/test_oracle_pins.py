@@ -903,17 +903,21 @@ def test_cycle_with_lbfgsb_zones_keeps_its_bookkeeping():
     assert (acc == 1).sum() >= 3
 
 
-def test_cycle_with_lbfgsb_zones_is_its_steps_in_order():
-    """With one zone per batch, the cycle is: local energies, the zone of batch b at sigma_b, L-BFGS-B
-    on that zone against the rest, the float64 accept; rebuilt here from those oracle pieces."""
+@pytest.mark.parametrize("opt", ["lbfgsb_tu", "bb"])
+def test_cycle_is_its_steps_in_order(opt):
+    """With one zone per batch, the cycle is: local energies, the zone of batch b at sigma_b, the zone
+    optimiser (L-BFGS-B or projected BB) against the rest, the float64 accept; rebuilt here from
+    those oracle pieces."""
     n = 400
+    eta = 1e-4 / n
     pos = synth.arcsine_disk(n, 31)
     s0 = 1 - 1 / (2 * math.sqrt(n))
     p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
     u = np.random.default_rng(32).random((5, 3))
     kw = dict(m_min=10, m_max=60, period=4)
-    p, trace, d, acc = oracle.cycle(p0, u, batch=1, step0=1e-4, alpha_min=0.0, alpha_max=0.0, steps=6,
-                                    sigma0=s0, sigma1=1.0, flags=f, optimizer="lbfgsb_tu", memory=5,
+    step0 = 1e-4 if opt == "lbfgsb_tu" else eta
+    p, trace, d, acc = oracle.cycle(p0, u, batch=1, step0=step0, alpha_min=0.0, alpha_max=10 * eta, steps=6,
+                                    sigma0=s0, sigma1=1.0, flags=f, optimizer=opt, memory=5,
                                     maxstep=0.02, line_search=3, **kw)
     q = p0.copy()
     for b in range(5):
@@ -921,8 +925,11 @@ def test_cycle_with_lbfgsb_zones_is_its_steps_in_order():
         e_tot, e_loc = oracle.energy(q, local=True)
         assert trace[b] == e_tot
         idx, off, _, _ = oracle.zone_select(q, e_loc, u[b:b + 1], phase=b, radius=radius, flags=f, **kw)
-        act = oracle.subdomain_lbfgsb(q, idx, memory=5, steps=6, step0=1e-4, maxstep=0.02, radius=radius,
-                                      flags=f, line_search=3)
+        if opt == "lbfgsb_tu":
+            act = oracle.subdomain_lbfgsb(q, idx, memory=5, steps=6, step0=step0, maxstep=0.02, radius=radius,
+                                          flags=f, line_search=3)
+        else:
+            act = oracle.subdomain_bb(q, idx, step0, 0.0, 10 * eta, 6, radius=radius, flags=f)
         q, db, ab = oracle.accept_sequential(q, idx, off, act)
         assert db[0] == d[b] and ab[0] == acc[b]
     np.testing.assert_array_equal(p, q)
