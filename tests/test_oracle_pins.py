@@ -935,3 +935,52 @@ def test_cycle_is_its_steps_in_order(opt):
     np.testing.assert_array_equal(p, q)
     assert trace[5] == oracle.energy(q)
     assert (acc == 1).sum() >= 3  # the zones really move
+
+
+def _tu_to_x(z, sigma, f):
+    t, u = z[:, 0], z[:, 1]
+    r = np.where(f == 1, 1.0, sigma * np.sin(t) ** 2)
+    ang = np.where(f == 1, z[:, 0], u)
+    return np.stack([r * np.cos(ang), r * np.sin(ang)], 1)
+
+
+def _smooth_to_x(z, sigma, f):
+    rho = np.hypot(z[:, 0], z[:, 1])
+    scale = np.where(f == 1, 1.0 / rho, sigma * np.sin(rho) / rho)
+    return z * scale[:, None]
+
+
+@pytest.mark.parametrize("tu", [False, True])
+def test_first_lbfgs_step_follows_the_maps_gradient(tu):
+    """Without history the first L-BFGS step is z - step0 dE/dz.  dE/dz is taken here by central
+    differences of E(x(z)) over the map's own variables (Sec. II D's r = sigma sin^2 t, u; pinned
+    charges on (cos u, sin u); or the smooth map x = sigma sin|z| z/|z|), so every term of the chain
+    rule is checked, pinned charges included."""
+    n, sigma = 30, 0.9
+    pos = synth.arcsine_disk(n, 41)
+    p0, f = oracle.border_split(pos, 6, sigma)
+    r = np.hypot(p0[:, 0], p0[:, 1])
+    if tu:
+        z0 = np.stack([np.where(f == 1, np.arctan2(p0[:, 1], p0[:, 0]), np.arcsin(np.sqrt(np.minimum(r / sigma, 1)))),
+                       np.where(f == 1, 0.0, np.arctan2(p0[:, 1], p0[:, 0]))], 1)
+        to_x = _tu_to_x
+    else:
+        k = np.where(f == 1, 1.0, np.arcsin(np.minimum(r / sigma, 1)) / r)
+        z0 = p0 * k[:, None]
+        to_x = _smooth_to_x
+    h = 1e-6
+    gz = np.zeros_like(z0)
+    for i in range(n):
+        for c in range(2):
+            if tu and f[i] == 1 and c == 1:
+                continue  # the unused second variable of a pinned charge
+            zp, zm = z0.copy(), z0.copy()
+            zp[i, c] += h
+            zm[i, c] -= h
+            gz[i, c] = (oracle.energy(to_x(zp, sigma, f)) - oracle.energy(to_x(zm, sigma, f))) / (2 * h)
+    step0 = 1e-6
+    x1, _, _ = oracle.lbfgs(p0, memory=4, max_iter=1, step0=step0, maxstep=10.0, radius=sigma, flags=f, tu=tu)
+    expect = to_x(z0 - step0 * gz, sigma, f)
+    moved = np.abs(x1 - p0).max()
+    assert moved > 1e-6
+    assert np.abs(x1 - expect).max() <= 1e-5 * moved
