@@ -4,8 +4,10 @@
 // A relaxation step of every problem is one pair pass (all problems' units in
 // one persistent launch, tc_pass.cuh) followed by one update launch (one CTA
 // per problem: reduce the row partials in a fixed order, take the optimiser
-// step, re-split the moved rows).  The step loop is captured once into a CUDA
-// graph and replayed.
+// step, re-split the moved rows; L-BFGS-B in tc_lbfgsb.cuh; L-BFGS of very
+// large problems as grid-wide launches), and optionally an Armijo line search.
+// 64 steps are captured once into a CUDA graph and replayed; with a stopping
+// tolerance the host stops replaying once no problem is active.
 #include <algorithm>
 #include <climits>
 #include <cmath>
