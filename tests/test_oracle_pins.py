@@ -984,3 +984,32 @@ def test_first_lbfgs_step_follows_the_maps_gradient(tu):
     moved = np.abs(x1 - p0).max()
     assert moved > 1e-6
     assert np.abs(x1 - expect).max() <= 1e-5 * moved
+
+
+def test_lbfgsb_reports_the_projected_gradient_rms():
+    """L-BFGS-B's stop measure at the start point: RMS over charges of P(v - g) - v on the box
+    t in [0, pi/2] (pinned charges: u free, second variable fixed), g by central differences of
+    E(x(t, u)).  The gradients are large, so for most charges t - g_t falls outside the box and the
+    projection decides the measure."""
+    n, sigma = 40, 0.9
+    pos = synth.arcsine_disk(n, 43)
+    p0, f = oracle.border_split(pos, 7, sigma)
+    r = np.hypot(p0[:, 0], p0[:, 1])
+    ang = np.arctan2(p0[:, 1], p0[:, 0])
+    z0 = np.stack([np.where(f == 1, ang, np.arcsin(np.sqrt(np.minimum(r / sigma, 1)))), np.where(f == 1, 0.0, ang)], 1)
+    h = 1e-6
+    g = np.zeros_like(z0)
+    for i in range(n):
+        for c in range(2 if f[i] == 0 else 1):
+            zp, zm = z0.copy(), z0.copy()
+            zp[i, c] += h
+            zm[i, c] -= h
+            g[i, c] = (oracle.energy(_tu_to_x(zp, sigma, f)) - oracle.energy(_tu_to_x(zm, sigma, f))) / (2 * h)
+    lo = np.where(f[:, None] == 1, [-np.inf, 0.0], [0.0, -np.inf])
+    hi = np.where(f[:, None] == 1, [np.inf, 0.0], [math.pi / 2, np.inf])
+    pg = np.clip(z0 - g, lo, hi) - z0
+    expect = math.sqrt((pg ** 2).sum() / n)
+    assert (np.abs(np.clip(z0 - g, lo, hi) - (z0 - g)) > 1.0).any(1).sum() >= 10  # the box acts
+    _, it, rms, _ = oracle.lbfgsb(p0, max_iter=0, radius=sigma, flags=f)
+    assert it == 0
+    assert abs(rms - expect) <= 1e-6 * expect
