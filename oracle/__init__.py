@@ -62,6 +62,7 @@ def lib(openmp: bool = False) -> C.CDLL:
             "tco_accept_sequential": [vp, i64, vp, vp, i64, vp, vp, vp],
             "tco_lbfgs": [vp, i64, i64, i64, d, d, d, d, vp, vp, vp],
             "tco_lbfgs_ls": [vp, i64, i64, i64, d, d, d, d, vp, i64, i64, vp, vp],
+            "tco_lbfgs_trace": [vp, i64, i64, i64, d, d, d, d, vp, i64, i64, vp, vp, vp, vp, vp, vp],
             "tco_lbfgsb": [vp, i64, i64, i64, d, d, d, d, vp, i64, vp, vp, vp],
             "tco_lbfgsb_middle": [i64, vp, vp, i64, d, vp],
             "tco_lbfgsb_cauchy": [i64, vp, vp, vp, vp, i64, vp, vp, d, vp, vp, vp, vp],
@@ -236,6 +237,26 @@ def lbfgs(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: 
                               float(maxstep), float(radius), _p(f), int(line_search), int(bool(tu)), _p(it),
                               _p(rms)), "lbfgs")
     return p, int(it[0]), float(rms[0])
+
+
+def lbfgs_trace(pos, memory: int = 8, max_iter: int = 10, gtol: float = 0.0, step0: float = 1e-4,
+                maxstep: float = 1e-2, radius: float = 1.0, flags=None, line_search: int = 0, tu: bool = False):
+    """The lbfgs iteration with its path: returns (x, z (k+1, 2n), dE/dz (k+1, 2n), directions (k, 2n),
+    step scales (k,)) for the k iterations taken (the step scale is the one before any halving)."""
+    p = _pos(pos).copy()
+    f = None if flags is None else np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+    L = 2 * p.shape[0]
+    ztr = np.zeros((max_iter + 1, max(L, 1)))
+    gtr = np.zeros((max_iter + 1, max(L, 1)))
+    dtr = np.zeros((max(max_iter, 1), max(L, 1)))
+    atr = np.zeros(max(max_iter, 1))
+    it = np.zeros(1, dtype=np.int64)
+    rms = np.zeros(1)
+    _check(lib().tco_lbfgs_trace(_p(p), p.shape[0], int(memory), int(max_iter), float(gtol), float(step0),
+                                 float(maxstep), float(radius), _p(f), int(line_search), int(bool(tu)), _p(it),
+                                 _p(rms), _p(ztr), _p(gtr), _p(dtr), _p(atr)), "lbfgs_trace")
+    k = int(it[0])
+    return p, ztr[:k + 1, :L], gtr[:k + 1, :L], dtr[:k, :L], atr[:k]
 
 
 def lbfgsb(pos, memory: int = 8, max_iter: int = 1000, gtol: float = 0.0, step0: float = 1e-4,

@@ -604,6 +604,16 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
                  double step0, double maxstep, double sigma, const unsigned char* flags,
                  int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out);
 
+/* The iteration of tco_lbfgs_ls with its path recorded (nullable arrays, one
+ * row of 2n per iteration): z_tr[k] and gz_tr[k] the variables and dE/dz at
+ * iterate k (k = 0 .. iterations), d_tr[k] the search direction taken at
+ * iterate k after the descent check and alpha_tr[k] its step scale
+ * (k < iterations).  Rows are written as the iteration reaches them. */
+static int lbfgs_core(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                      double step0, double maxstep, double sigma, const unsigned char* flags,
+                      int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out,
+                      double* z_tr, double* gz_tr, double* d_tr, double* alpha_tr);
+
 /* Energy change E(xn) - E(x) of moving every charge from x to xn, summed as
  * pair differences (compensated), not as a difference of totals. */
 static double instance_delta(const double* x, const double* xn, int64_t n)
@@ -634,6 +644,24 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
                  double step0, double maxstep, double sigma, const unsigned char* flags,
                  int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out)
 {
+    return lbfgs_core(pos, n, memory, max_iter, gtol, step0, maxstep, sigma, flags, max_halvings, tu, iters_out,
+                      rms_out, NULL, NULL, NULL, NULL);
+}
+
+int tco_lbfgs_trace(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                    double step0, double maxstep, double sigma, const unsigned char* flags,
+                    int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out,
+                    double* z_tr, double* gz_tr, double* d_tr, double* alpha_tr)
+{
+    return lbfgs_core(pos, n, memory, max_iter, gtol, step0, maxstep, sigma, flags, max_halvings, tu, iters_out,
+                      rms_out, z_tr, gz_tr, d_tr, alpha_tr);
+}
+
+static int lbfgs_core(double* pos, int64_t n, int64_t memory, int64_t max_iter, double gtol,
+                      double step0, double maxstep, double sigma, const unsigned char* flags,
+                      int64_t max_halvings, int64_t tu, int64_t* iters_out, double* rms_out,
+                      double* z_tr, double* gz_tr, double* d_tr, double* alpha_tr)
+{
     if (n < 0 || memory < 1 || max_iter < 0 || max_halvings < 0 || (n > 0 && !pos) || !(sigma > 0.0))
         return TCO_ERR_INVALID_ARG;
     int64_t L = 2 * n;
@@ -663,6 +691,8 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
     if (!st) {
         if (tu) grad_tu(z, g, n, sigma, flags, gz); else grad_z(z, g, n, sigma, flags, gz);
         rms = n > 0 ? sqrt(dot(gz, gz, L) / (double)n) : 0.0;
+        if (z_tr) memcpy(z_tr, z, sz);
+        if (gz_tr) memcpy(gz_tr, gz, sz);
     }
     for (; !st && it < max_iter; ++it) {
         if (rms < gtol) break;
@@ -695,6 +725,7 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
             if (a > dmax) dmax = a;
         }
         double alpha = (dmax > maxstep) ? maxstep / dmax : 1.0;
+        if (d_tr) memcpy(d_tr + it * L, d, sz);
         for (int64_t i = 0; i < L; ++i) zn[i] = z[i] + alpha * d[i];
         if (max_halvings > 0) {
             memcpy(xk, pos, sz);
@@ -712,6 +743,9 @@ int tco_lbfgs_ls(double* pos, int64_t n, int64_t memory, int64_t max_iter, doubl
         if (st) break;
         if (tu) grad_tu(zn, g, n, sigma, flags, gzn); else grad_z(zn, g, n, sigma, flags, gzn);
         rms = n > 0 ? sqrt(dot(gzn, gzn, L) / (double)n) : 0.0;
+        if (alpha_tr) alpha_tr[it] = alpha;
+        if (z_tr) memcpy(z_tr + (it + 1) * L, zn, sz);
+        if (gz_tr) memcpy(gz_tr + (it + 1) * L, gzn, sz);
         /* the candidate pair is tested first and stored only if kept, so a
          * rejected pair never overwrites the oldest stored one */
         acc_t sy_a = {0.0, 0.0}, ss_a = {0.0, 0.0}, yy_a = {0.0, 0.0};

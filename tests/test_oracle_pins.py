@@ -1013,3 +1013,71 @@ def test_lbfgsb_reports_the_projected_gradient_rms():
     _, it, rms, _ = oracle.lbfgsb(p0, max_iter=0, radius=sigma, flags=f)
     assert it == 0
     assert abs(rms - expect) <= 1e-6 * expect
+
+
+def _dense_inverse_bfgs(pairs, gamma, L):
+    """H (L x L) after the BFGS inverse updates H <- V^T H V + rho s s^T (V = I - rho y s^T) of
+    gamma I, oldest pair first (Nocedal & Wright, Eq. 6.17 and Sec. 7.2)."""
+    H = gamma * np.eye(L)
+    for s_, y_ in pairs:
+        rho = 1.0 / (s_ @ y_)
+        V = np.eye(L) - rho * np.outer(y_, s_)
+        H = V.T @ H @ V + rho * np.outer(s_, s_)
+    return H
+
+
+LBFGS_PATHS = [
+    # (n, seed, memory, iterations, step0, maxstep, tu, pinned, radius): 25-30 iterations with memory
+    # 3-4 wrap the pair ring many times; the first and last cases skip pairs (s.y <= 1e-12 |s||y|)
+    (10, 0, 3, 25, 1e-3, 0.3, False, 0, 1.0),
+    (10, 5, 3, 25, 1e-3, 0.3, True, 0, 1.0),
+    (10, 3, 3, 25, 1e-3, 0.3, False, 0, 1.0),
+    (14, 8, 4, 30, 1e-3, 0.2, False, 4, 0.95),
+    (14, 8, 4, 30, 1e-3, 0.2, True, 4, 0.95),
+]
+
+
+@pytest.mark.parametrize("n,seed,memory,iters,step0,maxstep,tu,pinned,radius", LBFGS_PATHS)
+def test_lbfgs_direction_is_the_dense_inverse_bfgs_product(n, seed, memory, iters, step0, maxstep, tu, pinned,
+                                                          radius):
+    """The L-BFGS iteration (two-loop recursion with a ring of `memory` pairs) against the matrix it
+    stands for: at every iterate the direction equals -H g, H built densely from gamma I by the
+    BFGS inverse updates of the last `memory` kept pairs (gamma = s.y / y.y of the newest pair,
+    step0 without pairs); the step scale is min(1, maxstep / max_i |d_i|); z moves by alpha d; a
+    pair enters the ring iff s.y > 1e-12 |s||y|.  The pairs and gradients come from the recorded
+    path, the chain rule of dE/dz being pinned on its own by the central-difference tests above.
+    Gamma from the oldest pair, the loops walked in the wrong order or rho of the wrong slot each
+    change the direction by O(1) on these paths."""
+    x0 = synth.arcsine_disk(n, seed)
+    flags = None
+    if pinned:
+        flags = np.zeros(n, np.uint8)
+        flags[np.argsort(-np.linalg.norm(x0, axis=1))[:pinned]] = 1
+        x0 = oracle.project(x0, radius, flags)
+    xt, Z, Gz, D, A = oracle.lbfgs_trace(x0, memory=memory, max_iter=iters, step0=step0, maxstep=maxstep, tu=tu,
+                                         flags=flags, radius=radius)
+    assert len(A) == iters
+    # recording the path changes nothing: the untraced iteration ends at the same positions
+    xl, _, _ = oracle.lbfgs(x0, memory=memory, max_iter=iters, step0=step0, maxstep=maxstep, tu=tu, flags=flags,
+                            radius=radius)
+    np.testing.assert_array_equal(xt, xl)
+    hist, skipped, wrapped = [], 0, 0
+    for k in range(iters):
+        g = Gz[k]
+        gamma = (hist[-1][0] @ hist[-1][1]) / (hist[-1][1] @ hist[-1][1]) if hist else step0
+        d = -_dense_inverse_bfgs(hist, gamma, g.size) @ g
+        assert g @ d < 0  # every kept pair has s.y > 0, so H is positive definite
+        assert np.linalg.norm(d - D[k]) <= 1e-9 * np.linalg.norm(d), k
+        dmax = np.sqrt(d[0::2] ** 2 + d[1::2] ** 2).max()
+        alpha = maxstep / dmax if dmax > maxstep else 1.0
+        assert abs(A[k] - alpha) <= 1e-9 * alpha
+        s_, y_ = Z[k + 1] - Z[k], Gz[k + 1] - Gz[k]
+        assert np.abs(s_ - A[k] * D[k]).max() <= 1e-13 * (1.0 + np.abs(Z[k]).max())
+        if s_ @ y_ > 1e-12 * np.linalg.norm(s_) * np.linalg.norm(y_):
+            wrapped += len(hist) == memory
+            hist = (hist + [(s_, y_)])[-memory:]
+        else:
+            skipped += 1
+    assert wrapped >= 5  # the ring was full and overwrote its oldest pair several times
+    if (seed, tu) in ((0, False), (5, True), (3, False)):
+        assert skipped >= 1
