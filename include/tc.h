@@ -142,6 +142,30 @@ tc_status tc_subdomain_delta_energy_mixed(const double* pos, int64_t n, const in
                                           const int64_t* offsets, int32_t n_sub, const double* new_active,
                                           double* delta, double* bound, tc_stream stream);
 
+/* Gradient of the subdomain objective E_sub of Sec. II D, and its local
+ * energies, for many subdomains at once: the pair pass that every step of
+ * tc_relax_subdomains runs, evaluated once.  For subdomain s with active set
+ * A = idx[offsets[s] .. offsets[s+1]) whose charges sit at
+ * a_k = act[2 offsets[s] + 2k ..] (act NULL: a_k = pos[idx[k]]) while every
+ * other charge j (the fixed set F) sits at pos[j]:
+ *   grad[k]  = dE_sub/da_k = sum_{j in F} -(a_k - p_j)/|a_k - p_j|^3
+ *                          + sum_{l in A, l != k} -(a_k - a_l)/|a_k - a_l|^3
+ *   local_e[k] = e_k = sum_{j in F} 1/|a_k - p_j| + 1/2 sum_{l in A, l != k} 1/|a_k - a_l|
+ *   e_sub[s] = E_sub = sum_{k in A} e_k
+ * Subdomains are evaluated independently against pos (they may overlap).
+ *   pos      [2n]               configuration (read)
+ *   idx      [offsets[n_sub]]   active indices, strictly ascending within a subdomain
+ *   offsets  [n_sub + 1]        int64 CSR offsets, offsets[0] = 0, non-decreasing
+ *   act      [2 offsets[n_sub]] nullable: positions of the active charges
+ *   prec     TC_FP64, TC_F64X or TC_MIXED (the float32 pair terms of the relaxation's bulk steps)
+ *   grad     [2 offsets[n_sub]] written, interleaved like pos
+ *   local_e  [offsets[n_sub]]   nullable, written
+ *   e_sub    [n_sub]            nullable, written
+ * Device errors: TC_ERR_INVALID_ARG (index set), TC_ERR_NONFINITE, TC_ERR_OUTSIDE_DISK. */
+tc_status tc_subdomain_grad(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
+                            int32_t n_sub, const double* act, tc_precision prec, double* grad, double* local_e,
+                            double* e_sub, tc_stream stream);
+
 /* Hard wall of Eq. (potential) as a projection, in place:
  *   r <- r min(1, radius/|r|);  a charge with flags[i] != 0 is pinned to the
  *   unit circle (the boundary population of Sec. II B): r <- r/|r| (unchanged

@@ -10,8 +10,10 @@ no CPU path: on a machine without a GPU or without libtc.so every call raises.
     local_energy(pos)      e_i = 1/2 sum_{j != i} 1/r_ij    (Sec. II C step 1)
     project_disk(pos)      hard wall of Eq. (potential) as a projection
     subdomain_delta_energy pairwise E_sub(new) - E_sub(old) (Sec. II D)
+    subdomain_grad         dE_sub/da, e_k and E_sub of many subdomains (Sec. II D)
     relax_subdomains       batched local relaxation of subdomains / instances
     coulomb_energy         torch.autograd.Function: energy forward, gradient backward
+    subdomain_energy       the same for E_sub of one subdomain as a function of its charges
 """
 
 from __future__ import annotations
@@ -28,7 +30,7 @@ __all__ = [
     "energy", "grad", "local_energy", "project_disk", "subdomain_delta_energy", "relax_subdomains",
     "coulomb_energy", "CoulombEnergy", "sync_status", "probe_pipes", "relax_last_profile", "TCError", "RelaxParams",
     "library_path", "zone_params", "zone_offsets", "select_subdomains", "cycle", "subdomain_delta_energy_mixed",
-    "boundary_count", "border_split", "voronoi_order",
+    "boundary_count", "border_split", "voronoi_order", "subdomain_grad", "subdomain_energy", "SubdomainEnergy",
 ]
 
 _PREC = {"fp64": L.TC_FP64, "mixed": L.TC_MIXED, "fp64x": L.TC_F64X}
@@ -133,6 +135,26 @@ def subdomain_delta_energy_mixed(pos, idx, offsets, new_active) -> tuple[torch.T
                                                     _p(new_active), _p(out), _p(bound), _stream()),
             "tc_subdomain_delta_energy_mixed")
     return out, bound
+
+
+def subdomain_grad(pos, idx, offsets, act=None, precision="fp64"):
+    """Gradient rows dE_sub/da (M, 2), local energies e_k (M,) and E_sub per subdomain (n_sub,) of the
+    subdomain objective (Sec. II D): the charges idx at act (default: their positions in pos) against
+    every other charge at pos."""
+    _pos(pos)
+    _csr(idx, offsets)
+    if act is not None:
+        _pos(act, "act")
+        if act.shape[0] != idx.numel():
+            raise ValueError("act must hold one position per active index")
+    n_sub = offsets.numel() - 1
+    m = idx.numel()
+    g = torch.empty((m, 2), dtype=torch.float64, device=pos.device)
+    e = torch.empty(m, dtype=torch.float64, device=pos.device)
+    es = torch.empty(max(n_sub, 0), dtype=torch.float64, device=pos.device)
+    L.check(L.lib().tc_subdomain_grad(_p(pos), pos.shape[0], _p(idx), _p(offsets), n_sub, _p(act), _prec(precision),
+                                      _p(g), _p(e), _p(es), _stream()), "tc_subdomain_grad")
+    return g, e, es
 
 
 @dataclass
@@ -309,6 +331,32 @@ class CoulombEnergy(torch.autograd.Function):
 
 def coulomb_energy(pos: torch.Tensor, precision="fp64") -> torch.Tensor:
     return CoulombEnergy.apply(pos, precision)
+
+
+class SubdomainEnergy(torch.autograd.Function):
+    """E_sub(act) of one subdomain (Sec. II D): the charges idx at act against the others held at pos.
+
+    Forward and backward are one tc_subdomain_grad call each (the backward recomputes the pair terms;
+    nothing m x N is stored).  Only act is differentiable."""
+
+    @staticmethod
+    def forward(ctx, act, pos, idx, precision="fp64"):
+        offsets = torch.tensor([0, idx.numel()], dtype=torch.int64, device=pos.device)
+        ctx.save_for_backward(act, pos, idx, offsets)
+        ctx.precision = precision
+        _, _, es = subdomain_grad(pos, idx, offsets, act.detach().contiguous(), precision)
+        return es[0]
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(ctx, gout):
+        act, pos, idx, offsets = ctx.saved_tensors
+        g, _, _ = subdomain_grad(pos, idx, offsets, act.detach().contiguous(), ctx.precision)
+        return gout * g, None, None, None
+
+
+def subdomain_energy(act: torch.Tensor, pos: torch.Tensor, idx: torch.Tensor, precision="fp64") -> torch.Tensor:
+    return SubdomainEnergy.apply(act, pos, idx, precision)
 
 
 def voronoi_order(pos, max_nbr: int = 0):

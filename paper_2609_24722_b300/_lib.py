@@ -120,6 +120,7 @@ def _lib() -> C.CDLL:
             "tc_energy_noalloc": ([vp, i64, i32, vp, vp, vp], C.c_int),
             "tc_subdomain_delta_energy": ([vp, i64, vp, vp, i32, vp, vp, vp], C.c_int),
             "tc_subdomain_delta_energy_mixed": ([vp, i64, vp, vp, i32, vp, vp, vp, vp], C.c_int),
+            "tc_subdomain_grad": ([vp, i64, vp, vp, i32, vp, i32, vp, vp, vp, vp], C.c_int),
             "tc_relax_subdomains": ([vp, i64, vp, vp, i32, vp, vp, C.POINTER(RelaxParams), vp, vp], C.c_int),
             "tc_project_disk": ([vp, i64, d, vp, vp], C.c_int),
             "tc_status_string": ([C.c_int], C.c_char_p),

@@ -1793,9 +1793,174 @@ static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, con
     return cuda_status(cudaGetLastError());
 }
 
+// ------------------------------------------------------ subdomain gradient ---
+
+// Rows of the subdomain gradient at caller-given active positions: the float64
+// copy and the split the pass of that precision reads.
+__global__ void k_rows_act(RelaxDev d, const double2* __restrict__ act)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const double2 x = act[rr];
+        if (!isfinite(x.x) || !isfinite(x.y)) set_status(d.st, ST_NONFINITE);
+        else if (!inside(x.x, x.y)) set_status(d.st, ST_OUTSIDE);
+        if (d.x) d.x[rr] = x;
+        if (d.xs) d.xs[rr] = split4(x.x, x.y);
+        if (d.x3) d.x3[rr] = split3(x.x, x.y);
+    }
+}
+
+// Per row: the slots of the pass added in order (the reduction every update
+// kernel starts with), written out as dE_sub/da and e_k.
+__global__ void k_rows_out(RelaxDev d, const double* __restrict__ part_e, const double2* __restrict__ part_g,
+                           SlotView v, double2* __restrict__ grad, double* __restrict__ local_e)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_row_prob(d.prob, d.S, rr);
+        const Prob p = d.prob[s];
+        const int64_t rl = rr - p.row_base;
+        const double2 g = sum_g(p, rl, part_g, v);
+        const double e = sum_e(p, rl, part_e, v);
+        if (!isfinite(g.x) || !isfinite(g.y) || !isfinite(e)) set_status(d.st, ST_NONFINITE);
+        grad[rr] = g;
+        if (local_e) local_e[rr] = e;
+    }
+}
+
+template <int KIND>
+static cudaError_t subgrad_pass(const PassArgs& a, int64_t G, cudaStream_t s)
+{
+    return launch_pass<KIND, true, true>(a, G, 0, 0, s);
+}
+
+// tc_subdomain_grad: the relaxation's pair pass, once, at given active positions.
+static tc_status subdomain_grad(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets,
+                                int32_t n_sub, const double* act, int prec, double* grad, double* local_e,
+                                double* e_sub, cudaStream_t s)
+{
+    if (prec != TC_FP64 && prec != TC_MIXED && prec != TC_F64X) return TC_ERR_INVALID_ARG;
+    if (n < 0 || n_sub < 0 || (n > 0 && !pos) || (n_sub > 0 && !offsets) || (reinterpret_cast<uintptr_t>(pos) & 15) ||
+        (reinterpret_cast<uintptr_t>(act) & 15) || (reinterpret_cast<uintptr_t>(grad) & 15) ||
+        (reinterpret_cast<uintptr_t>(local_e) & 7) || (reinterpret_cast<uintptr_t>(e_sub) & 7))
+        return TC_ERR_INVALID_ARG;
+    if (n_sub == 0) return TC_OK;
+    if (n > INT32_MAX) return TC_ERR_INVALID_ARG;
+    tc_status err = TC_OK;
+    int* st = device_status(&err);
+    if (!st) return err;
+    std::vector<int64_t> off(n_sub + 1);
+    if (cudaError_t e_ = cudaMemcpyAsync(off.data(), offsets, 8 * (size_t)(n_sub + 1), cudaMemcpyDeviceToHost, s);
+        e_ != cudaSuccess)
+        return cuda_fail(e_, "offsets read");
+    if (cudaError_t e_ = cudaStreamSynchronize(s); e_ != cudaSuccess) return cuda_fail(e_, "offsets read");
+    Plan P;
+    P.prob.resize(n_sub);
+    int64_t mask_words = 0;
+    if (off[0] != 0) return TC_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < n_sub; ++k) {
+        if (off[k + 1] < off[k] || off[k + 1] - off[k] > n) return TC_ERR_INVALID_ARG;
+        Prob& p = P.prob[k];
+        p.row_base = off[k];
+        p.m = (int32_t)(off[k + 1] - off[k]);
+        p.snap_b = 0;
+        p.snap_e = n;
+        p.mask_off = mask_words;
+        mask_words += (n + 31) / 32;
+    }
+    P.M = off[n_sub];
+    if (P.M > 0 && (!idx || !grad)) return TC_ERR_INVALID_ARG;
+    plan_units(P);
+    const int64_t G = prec == TC_MIXED  ? pass_grid<PASS_MIXED, true, true>(P.W)
+                      : prec == TC_F64X ? pass_grid<PASS_F64X, true, true>(P.W)
+                                        : pass_grid<PASS_F64, true, true>(P.W);
+    const int64_t slots = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G);
+    const int64_t M = P.M;
+    const int64_t Mp = std::max<int64_t>(M, 1);
+    Carver c;
+    float4* snap_split = nullptr;
+    fx3* snap3 = nullptr;
+    auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, double*& part_e, double2*& part_g) {
+        probd = cv.take<Prob>(n_sub);
+        d.gidx = cv.take<int32_t>(M);
+        d.x = cv.take<double2>(M);
+        d.xs = cv.take<float4>(prec == TC_MIXED ? M : 0);
+        d.x3 = cv.take<fx3>(prec == TC_F64X ? M : 0);
+        snap_split = cv.take<float4>(prec == TC_MIXED ? n : 0);
+        snap3 = cv.take<fx3>(prec == TC_F64X ? n : 0);
+        d.mask = cv.take<uint32_t>(mask_words);
+        part_e = cv.take<double>(slots * Mp);
+        part_g = cv.take<double2>(slots * Mp);
+    };
+    RelaxDev d{};
+    Prob* probd;
+    double* part_e;
+    double2* part_g;
+    layout(c, d, probd, part_e, part_g);
+    void* ws = workspace(s, c.off, &err);
+    if (!ws) return err;
+    c.base = static_cast<char*>(ws);
+    c.off = kCounterBytes;
+    layout(c, d, probd, part_e, part_g);
+    if (prec != TC_MIXED) d.xs = nullptr;
+    if (prec != TC_F64X) d.x3 = nullptr;
+    d.prob = probd;
+    d.S = n_sub;
+    d.M = M;
+    d.idx = idx;
+    d.pos = const_cast<double2*>(reinterpret_cast<const double2*>(pos));
+    d.st = st;
+    cudaError_t e = cudaMemcpyAsync(probd, P.prob.data(), sizeof(Prob) * n_sub, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.mask, 0, 4 * (size_t)mask_words, s);
+    if (e != cudaSuccess) return cuda_fail(e, "set-up");
+    const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((M + 255) / 256, 8L * sm_count()));
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8L * sm_count()));
+    if (M > 0) {
+        k_rows_init<<<eb, 256, 0, s>>>(d, n, 1.0, 0);
+        k_mask_build<<<eb, 256, 0, s>>>(d);
+        if (act) k_rows_act<<<eb, 256, 0, s>>>(d, reinterpret_cast<const double2*>(act));
+    }
+    if (prec == TC_MIXED) k_split_pos<<<nb, 256, 0, s>>>(reinterpret_cast<const double2*>(pos), n, snap_split, st);
+    if (prec == TC_F64X) k_split3_pos<<<nb, 256, 0, s>>>(reinterpret_cast<const double2*>(pos), n, snap3);
+    PassArgs a{};
+    a.prob = probd;
+    a.S = n_sub;
+    a.W = P.W;
+    a.M = Mp;
+    a.mask = d.mask;
+    a.active = nullptr;
+    a.part_e = part_e;
+    a.part_g = part_g;
+    if (prec == TC_MIXED) {
+        a.rows = d.xs;
+        a.snap = snap_split;
+        e = subgrad_pass<PASS_MIXED>(a, G, s);
+    } else if (prec == TC_F64X) {
+        a.rows = d.x3;
+        a.snap = snap3;
+        e = subgrad_pass<PASS_F64X>(a, G, s);
+    } else {
+        a.rows = d.x;
+        a.snap = pos;
+        e = subgrad_pass<PASS_F64>(a, G, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "launch");
+    SlotView v{P.W, G, 0, Mp, 0};
+    if (M > 0) k_rows_out<<<eb, 256, 0, s>>>(d, part_e, part_g, v, reinterpret_cast<double2*>(grad), local_e);
+    if (e_sub) k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, e_sub, nullptr);
+    return cuda_status(cudaGetLastError());
+}
+
 }  // namespace tc
 
 extern "C" {
+
+tc_status tc_subdomain_grad(const double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
+                            const double* act, tc_precision prec, double* grad, double* local_e, double* e_sub,
+                            tc_stream stream)
+{
+    tc::NvtxRange nvtx_range("tc_subdomain_grad");
+    return tc::subdomain_grad(pos, n, idx, offsets, n_sub, act, prec, grad, local_e, e_sub,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
 
 tc_status tc_relax_subdomains(double* pos, int64_t n, const int32_t* idx, const int64_t* offsets, int32_t n_sub,
                               const int64_t* world, const uint8_t* flags, const tc_relax_params* prm,
