@@ -309,9 +309,12 @@ typedef struct {
     tc_relax_params relax;  /* optimiser of step 4; accept is forced to 1, radius replaced by sigma */
     int32_t batch;          /* subdomains selected and relaxed together (1 = one at a time) */
     int32_t local_precision;/* tc_precision of the e_i that pick the centres */
-    double sigma0;          /* interior radius of the first batch (Sec. II B, Eq. sigma) ... */
+    double sigma0;          /* interior radius of the first batch (Sec. II B); <= 0: Eq. sigma,
+                               1 - 1/(2 sqrt(n)) ... */
     double sigma1;          /* ... rising linearly to this one at the last batch;
                                wall_tol < sigma0 <= sigma1 <= 1 (1, 1: the plain unit disk) */
+    int32_t disjoint;       /* 0: a batch is the next `batch` subdomains; 1: it is the longest
+                               prefix of pairwise disjoint zones among them (see tc_cycle) */
 } tc_cycle_params;
 
 /* One optimisation cycle (Sec. II C) of n_sub subdomains, in batches of
@@ -332,8 +335,20 @@ typedef struct {
  *   out      [n_sub]       device results, as tc_relax_subdomains
  *   energy   [n_batches+1] device; E (in local_precision) before each batch and
  *                          after the last; nullable
+ * With disjoint = 1 a batch is formed differently: the zones of the next
+ * `batch` subdomains are selected, and the batch is their longest prefix of
+ * pairwise disjoint zones (at least one zone).  The zones after that prefix
+ * are dropped and selected again, from the configuration and local energies
+ * after this batch, as the start of the next batch.  So no zone is skipped
+ * by the accept, every drawn centre is optimised, and the relaxations of a
+ * batch interact only through the long-range cross terms that the
+ * sequential accept then evaluates exactly.  The interior radius of a batch
+ * whose first subdomain is b0 is sigma0 + (sigma1 - sigma0) b0 / (n_sub - 1)
+ * (sigma1 for n_sub = 1), and `energy` needs n_sub + 1 entries, of which the
+ * first (batches run) + 1 are written.
  * Synchronises the stream once per batch (the zone sizes are host-known, the
- * relaxation reads its offsets back).  Device errors as tc_relax_subdomains. */
+ * relaxation reads its offsets back; the disjoint form reads its prefix
+ * length).  Device errors as tc_relax_subdomains. */
 tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_params* prm, int32_t n_sub,
                    const double* uniforms, tc_subdomain_result* out, double* energy, tc_stream stream);
 
@@ -347,7 +362,8 @@ int64_t tc_boundary_count(int64_t n);
  * (flags = 1, r <- r/|r|; unchanged at the origin) and the others interior
  * charges confined to radius sigma (flags = 0, r <- r min(1, sigma/|r|)).
  *   pos   [2n] device, in/out;  flags [n] device, written;
- *   0 <= n_b <= n;  0 < sigma <= 1.  Asynchronous on `stream`. */
+ *   0 <= n_b <= n;  sigma <= 1, where sigma <= 0 takes Eq. sigma, 1 - 1/(2 sqrt(n)).
+ *   Asynchronous on `stream`. */
 tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uint8_t* flags, tc_stream stream);
 
 /* Structure analysis of Sec. III C-D: Voronoi neighbours, the coordination

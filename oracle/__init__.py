@@ -73,6 +73,8 @@ def lib(openmp: bool = False) -> C.CDLL:
             "tco_cycle_opt": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, vp, i64, d, d, d, i64, d, i64, i64,
                               vp, vp, vp],
             "tco_subdomain_lbfgsb": [vp, i64, vp, i64, i64, i64, d, d, d, vp, i64, vp],
+            "tco_cycle_run": [vp, i64, vp, d, d, d, d, d, i64, i64, i64, i64, i64, i64, vp, i64, d, d, d, i64, d, i64,
+                              i64, vp, vp, vp, vp],
             "tco_border_split": [vp, i64, i64, d, vp],
         }
         for name, args in sig.items():
@@ -355,25 +357,28 @@ def zone_select(pos, local_e, uniforms, m_min: int, m_max: int, period: int, pha
 def cycle(pos, uniforms, m_min: int, m_max: int, period: int, batch: int, step0: float, alpha_min: float,
           alpha_max: float, steps: int, kappa: float = -1.0, p_defect: float = 0.8, sigma0: float = 1.0,
           sigma1: float = 1.0, wall_tol: float = 1e-9, flags=None, optimizer: str = "bb", memory: int = 8,
-          maxstep: float = 1e-3, line_search: int = 0):
+          maxstep: float = 1e-3, line_search: int = 0, disjoint: bool = False):
     """One optimisation cycle (Sec. II C) in batches; returns (pos, trace, delta, accepted).
 
     sigma0 -> sigma1: interior radius ramp over the batches; flags: pinned boundary charges;
-    optimizer "bb" (projected BB) or "lbfgsb_tu" (L-BFGS-B on (t, u) per zone)."""
+    optimizer "bb" (projected BB) or "lbfgsb_tu" (L-BFGS-B on (t, u) per zone).  disjoint=True: a batch
+    is the longest prefix of pairwise disjoint zones among the next `batch` subdomains (the rest are
+    selected again for the next batch); the trace then has one entry per batch run, plus one."""
     p = _pos(pos).copy()
     f = _flags(flags)
     u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1, 3))
     ns = u.shape[0]
-    nb = -(-ns // batch) if ns else 0
-    trace = np.zeros(nb + 1)
+    trace = np.zeros(ns + 1)
     d = np.zeros(max(ns, 1))
     acc = np.zeros(max(ns, 1), dtype=np.uint8)
+    nb = np.zeros(1, dtype=np.int64)
     opt = {"bb": 0, "lbfgsb_tu": 1}[optimizer]
-    _check(lib().tco_cycle_opt(_p(p), p.shape[0], _p(f), float(kappa), float(p_defect), float(sigma0),
+    _check(lib().tco_cycle_run(_p(p), p.shape[0], _p(f), float(kappa), float(p_defect), float(sigma0),
                                float(sigma1), float(wall_tol), int(m_min), int(m_max), int(period), ns, int(batch),
-                               _p(u), opt, float(step0), float(alpha_min), float(alpha_max), int(memory),
-                               float(maxstep), int(line_search), int(steps), _p(trace), _p(d), _p(acc)), "cycle")
-    return p, trace, d[:ns], acc[:ns]
+                               int(bool(disjoint)), _p(u), opt, float(step0), float(alpha_min), float(alpha_max),
+                               int(memory), float(maxstep), int(line_search), int(steps), _p(trace), _p(d), _p(acc),
+                               _p(nb)), "cycle")
+    return p, trace[:int(nb[0]) + 1], d[:ns], acc[:ns]
 
 
 def boundary_count(n: int) -> int:

@@ -1473,6 +1473,12 @@ int tco_cycle(double* pos, int64_t n, const unsigned char* flags, double kappa, 
                          uniforms, 0, step0, alpha_min, alpha_max, 1, 1.0, 0, steps, trace, delta, accepted);
 }
 
+int tco_cycle_run(double* pos, int64_t n, const unsigned char* flags, double kappa, double p_defect, double sigma0,
+                  double sigma1, double wall_tol, int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub,
+                  int64_t batch, int64_t disjoint, const double* uniforms, int64_t optimizer, double step0,
+                  double alpha_min, double alpha_max, int64_t memory, double maxstep, int64_t max_halvings,
+                  int64_t steps, double* trace, double* delta, unsigned char* accepted, int64_t* n_batches_out);
+
 /* tco_cycle with the zone optimiser chosen: 0 = projected BB (step0,
  * alpha_min, alpha_max), 1 = L-BFGS-B on (t, u) (memory, step0, maxstep,
  * at most max_halvings Armijo halvings per step). */
@@ -1482,7 +1488,41 @@ int tco_cycle_opt(double* pos, int64_t n, const unsigned char* flags, double kap
                   double alpha_max, int64_t memory, double maxstep, int64_t max_halvings, int64_t steps,
                   double* trace, double* delta, unsigned char* accepted)
 {
-    if (optimizer < 0 || optimizer > 1) return TCO_ERR_INVALID_ARG;
+    return tco_cycle_run(pos, n, flags, kappa, p_defect, sigma0, sigma1, wall_tol, m_min, m_max, period, n_sub,
+                         batch, 0, uniforms, optimizer, step0, alpha_min, alpha_max, memory, maxstep, max_halvings,
+                         steps, trace, delta, accepted, NULL);
+}
+
+/* Whether zone s of a CSR list shares a charge with one of the zones 0 .. s-1
+ * (mark: n bytes, the charges of zones 0 .. s-1 set; the zone is added when free). */
+static int zone_clashes(const int32_t* idx, const int64_t* off, int64_t s, unsigned char* mark)
+{
+    for (int64_t k = off[s]; k < off[s + 1]; ++k)
+        if (mark[idx[k]]) return 1;
+    for (int64_t k = off[s]; k < off[s + 1]; ++k) mark[idx[k]] = 1;
+    return 0;
+}
+
+/* The cycle, with two ways to form a batch from the subdomains not yet run:
+ *   disjoint = 0: the next `batch` subdomains (a zone that shares a charge
+ *     with a zone accepted earlier in the batch is skipped by the accept);
+ *   disjoint = 1: the zones of the next `batch` subdomains are selected, and
+ *     the batch is their longest prefix of pairwise disjoint zones (at least
+ *     one); the zones after it are dropped and selected again, from the
+ *     configuration and local energies after this batch, as the start of the
+ *     next batch.  No zone is then skipped, every drawn centre is optimised,
+ *     and batch = 1 is the paper's one-at-a-time cycle.  The interior radius
+ *     of a batch whose first subdomain is b0 is
+ *     sigma0 + (sigma1 - sigma0) b0 / (n_sub - 1) (sigma1 for n_sub = 1).
+ * trace (nullable): n_sub + 1 entries in the disjoint form, n_batches + 1 used.
+ * n_batches_out (nullable): the number of batches run. */
+int tco_cycle_run(double* pos, int64_t n, const unsigned char* flags, double kappa, double p_defect, double sigma0,
+                  double sigma1, double wall_tol, int64_t m_min, int64_t m_max, int64_t period, int64_t n_sub,
+                  int64_t batch, int64_t disjoint, const double* uniforms, int64_t optimizer, double step0,
+                  double alpha_min, double alpha_max, int64_t memory, double maxstep, int64_t max_halvings,
+                  int64_t steps, double* trace, double* delta, unsigned char* accepted, int64_t* n_batches_out)
+{
+    if (optimizer < 0 || optimizer > 1 || disjoint < 0 || disjoint > 1) return TCO_ERR_INVALID_ARG;
     if (n < 1 || n_sub < 0 || batch < 1 || !pos || (n_sub > 0 && (!uniforms || !delta || !accepted)))
         return TCO_ERR_INVALID_ARG;
     int64_t n_batches = (n_sub + batch - 1) / batch;
@@ -1491,18 +1531,29 @@ int tco_cycle_opt(double* pos, int64_t n, const unsigned char* flags, double kap
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
     int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(batch + 1));
     double* act = (double*)malloc(sizeof(double) * 2 * (size_t)(cap > 0 ? cap : 1));
-    if (!e || !idx || !off || !act) { free(e); free(idx); free(off); free(act); return TCO_ERR_NO_MEMORY; }
+    unsigned char* mark = (unsigned char*)malloc((size_t)n);
+    if (!e || !idx || !off || !act || !mark) {
+        free(e); free(idx); free(off); free(act); free(mark);
+        return TCO_ERR_NO_MEMORY;
+    }
     int st = TCO_OK;
     int64_t nb = 0;
-    for (int64_t b0 = 0; b0 < n_sub && !st; b0 += batch, ++nb) {
-        int64_t k = n_sub - b0 < batch ? n_sub - b0 : batch;
-        double radius = tco_sigma_ramp(sigma0, sigma1, nb, n_batches);
+    for (int64_t b0 = 0, k = 0; b0 < n_sub && !st; b0 += k, ++nb) {
+        k = n_sub - b0 < batch ? n_sub - b0 : batch;
+        double radius = !disjoint ? tco_sigma_ramp(sigma0, sigma1, nb, n_batches)
+                                  : tco_sigma_ramp(sigma0, sigma1, b0, n_sub);
         double E;
         st = tco_energy(pos, n, &E, e);
         if (st) break;
         if (trace) trace[nb] = E;
         st = tco_zone_select(pos, n, e, flags, kappa, p_defect, radius, wall_tol, m_min, m_max, period, b0, k,
                              uniforms + 3 * b0, idx, off, NULL, NULL);
+        if (!st && disjoint) {
+            memset(mark, 0, (size_t)n);
+            int64_t kk = 0;
+            while (kk < k && !zone_clashes(idx, off, kk, mark)) ++kk;
+            k = kk;
+        }
         for (int64_t s = 0; s < k && !st; ++s)
             st = optimizer == 0 ? tco_subdomain_bb(pos, n, idx + off[s], off[s + 1] - off[s], step0, alpha_min,
                                                    alpha_max, steps, radius, flags, act + 2 * off[s])
@@ -1511,6 +1562,7 @@ int tco_cycle_opt(double* pos, int64_t n, const unsigned char* flags, double kap
         if (!st) st = tco_accept_sequential(pos, n, idx, off, k, act, delta + b0, accepted + b0);
     }
     if (!st && trace) st = tco_energy(pos, n, &trace[nb], NULL);
-    free(e); free(idx); free(off); free(act);
+    if (n_batches_out) *n_batches_out = nb;
+    free(e); free(idx); free(off); free(act); free(mark);
     return st;
 }

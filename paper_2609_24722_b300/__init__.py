@@ -255,11 +255,13 @@ def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, peri
           kappa: float = -1.0, p_defect: float = 0.8, wall_tol: float = 1e-9, sigma0: float = 1.0, sigma1: float = 1.0,
           local_precision="mixed", precision="mixed", optimizer="bb", n_steps=200, memory=8, step0=1e-9,
           alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0, polish_steps=0, polish_gtol=0.0,
-          want_energy=False, profile=False, line_search=0):
+          want_energy=False, profile=False, line_search=0, disjoint=False):
     """One optimisation cycle (Sec. II C) of uniforms.shape[0] subdomains in batches, in place on pos.
 
-    flags (uint8, nullable): pinned boundary charges; sigma0 -> sigma1: interior radius ramp.
-    Returns (RelaxResult per subdomain, energy trace: E before each batch and after the last)."""
+    flags (uint8, nullable): pinned boundary charges; sigma0 -> sigma1: interior radius ramp (sigma0 <= 0:
+    Eq. sigma).  disjoint=True: each batch is the longest prefix of pairwise disjoint zones among the next
+    `batch` subdomains.  Returns (RelaxResult per subdomain, energy trace: E before each batch and after
+    the last)."""
     _pos(pos)
     _vec(uniforms, torch.float64, "uniforms")
     if flags is not None:
@@ -273,11 +275,14 @@ def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, peri
     prm.local_precision = _prec(local_precision)
     prm.sigma0 = float(sigma0)
     prm.sigma1 = float(sigma1)
-    n_batches = -(-n_sub // max(int(batch), 1)) if n_sub else 0
+    prm.disjoint = int(bool(disjoint))
+    n_batches = (n_sub if disjoint else -(-n_sub // max(int(batch), 1))) if n_sub else 0
     raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
     trace = torch.full((n_batches + 1,), float("nan"), dtype=torch.float64, device=pos.device)
     L.check(L.lib().tc_cycle(_p(pos), pos.shape[0], _p(flags), C.byref(prm), n_sub, _p(uniforms), _p(raw),
                              _p(trace), _stream()), "tc_cycle")
+    if disjoint:
+        trace = trace[~torch.isnan(trace)]
     return _results(raw, n_sub), trace
 
 
@@ -288,11 +293,12 @@ def boundary_count(n: int) -> int:
 
 def border_split(pos, n_b: int | None = None, sigma: float | None = None) -> torch.Tensor:
     """Sec. II B split in place: the n_b outermost charges pinned to the unit circle, the rest confined
-    to sigma.  Defaults: n_b from Eq. Nb, sigma = 1 - 1/(2 sqrt(n)) (Eq. sigma).  Returns the uint8 flags."""
+    to sigma.  Defaults: n_b from Eq. Nb, sigma from Eq. sigma (libtc takes sigma <= 0 as Eq. sigma).
+    Returns the uint8 flags."""
     _pos(pos)
     n = pos.shape[0]
     n_b = boundary_count(n) if n_b is None else int(n_b)
-    sigma = 1.0 - 0.5 / max(n, 1) ** 0.5 if sigma is None else float(sigma)
+    sigma = 0.0 if sigma is None else float(sigma)
     flags = torch.empty(n, dtype=torch.uint8, device=pos.device)
     L.check(L.lib().tc_border_split(_p(pos), n, n_b, sigma, _p(flags), _stream()), "tc_border_split")
     return flags

@@ -99,6 +99,7 @@ class CycleParams(C.Structure):
         ("local_precision", C.c_int32),
         ("sigma0", C.c_double),
         ("sigma1", C.c_double),
+        ("disjoint", C.c_int32),
     ]
 
 

@@ -14,7 +14,7 @@
 #include "tc_plan.cuh"
 
 static_assert(sizeof(tc_zone_params) == 48, "tc_zone_params layout");
-static_assert(sizeof(tc_cycle_params) == 168, "tc_cycle_params layout");
+static_assert(sizeof(tc_cycle_params) == 176, "tc_cycle_params layout");
 
 namespace tc {
 
@@ -350,7 +350,41 @@ bool misaligned(const void* p, uintptr_t a)
     return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0;
 }
 
+// Length of the longest prefix of pairwise disjoint zones among zones 0 .. k-1
+// (at least 1) into *out.  One CTA walks the zones in order, testing a zone's
+// charges against a bit map of the charges taken so far and adding them when
+// none is; `taken` (n bits) must be zero on entry.
+constexpr int kPrefixThreads = 1024;
+
+__global__ void __launch_bounds__(kPrefixThreads) k_disjoint_prefix(const int32_t* __restrict__ idx,
+                                                                     const int64_t* __restrict__ offs, int32_t k,
+                                                                     uint32_t* __restrict__ taken, int32_t* out)
+{
+    __shared__ int clash;
+    int32_t s = 0;
+    for (; s < k; ++s) {
+        if (threadIdx.x == 0) clash = 0;
+        __syncthreads();
+        const int64_t a = offs[s], b = offs[s + 1];
+        for (int64_t i = a + threadIdx.x; i < b; i += kPrefixThreads) {
+            const int32_t j = idx[i];
+            if ((taken[j >> 5] >> (j & 31)) & 1u) clash = 1;
+        }
+        __syncthreads();
+        if (clash) break;
+        for (int64_t i = a + threadIdx.x; i < b; i += kPrefixThreads) {
+            const int32_t j = idx[i];
+            atomicOr(&taken[j >> 5], 1u << (j & 31));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s > 0 ? s : 1;
+}
+
 }  // namespace
+
+// Eq. sigma (Sec. II B): the initial radius of the interior charges, 1 - 1/(2 sqrt(N)).
+inline double eq_sigma(int64_t n) { return 1.0 - 0.5 / std::sqrt((double)n); }
 
 }  // namespace tc
 
@@ -399,8 +433,10 @@ tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_
     if (err != TC_OK) return err;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const tc_precision lp = static_cast<tc_precision>(prm->local_precision);
+    // sigma0 <= 0 asks for the initial interior radius of Eq. sigma
+    const double sigma0 = prm->sigma0 <= 0.0 && n >= 1 ? eq_sigma(n) : prm->sigma0;
     if (n_sub < 0 || prm->batch < 1 || (lp != TC_FP64 && lp != TC_MIXED) || misaligned(energy, 8) ||
-        !(prm->sigma0 > prm->zone.wall_tol) || !(prm->sigma0 <= prm->sigma1) || !(prm->sigma1 <= 1.0)) {
+        !(sigma0 > prm->zone.wall_tol) || !(sigma0 <= prm->sigma1) || !(prm->sigma1 <= 1.0)) {
         set_last_error("tc_cycle: need n_sub >= 0, batch >= 1, a valid local_precision and "
                        "wall_tol < sigma0 <= sigma1 <= 1");
         return TC_ERR_INVALID_ARG;
@@ -411,19 +447,27 @@ tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_
         return TC_ERR_INVALID_ARG;
     const int32_t B = std::min(prm->batch, n_sub);
     const int64_t n_batches = (n_sub + B - 1) / B;
-    // the largest batch's zones fix the buffer sizes
+    if (prm->disjoint != 0 && prm->disjoint != 1) {
+        set_last_error("tc_cycle: disjoint must be 0 or 1");
+        return TC_ERR_INVALID_ARG;
+    }
+    const bool disjoint = prm->disjoint == 1;
+    // the largest batch's zones fix the buffer sizes (disjoint batches may start at any subdomain)
     int64_t cap = 0;
     std::vector<int64_t> off(B + 1);
-    for (int64_t b0 = 0; b0 < n_sub; b0 += B) {
+    for (int64_t b0 = 0; b0 < n_sub; b0 += disjoint ? 1 : B) {
         const int32_t k = (int32_t)std::min<int64_t>(B, n_sub - b0);
         zone_offsets(&prm->zone, prm->zone.phase + b0, n, k, off.data());
         cap = std::max(cap, off[k]);
     }
+    const int64_t taken_words = disjoint ? (n + 31) / 32 : 0;
     Carver c;
     c.take<double>(n);
     c.take<int32_t>(std::max<int64_t>(cap, 1));
     c.take<int64_t>(B + 1);
     c.take<double>(1);
+    c.take<uint32_t>(taken_words);
+    c.take<int32_t>(1);
     void* ws = workspace(s, c.off, &err, 1);
     if (!ws) return err;
     c.base = static_cast<char*>(ws);
@@ -432,26 +476,45 @@ tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_
     int32_t* idx = c.take<int32_t>(std::max<int64_t>(cap, 1));
     int64_t* offs = c.take<int64_t>(B + 1);
     double* e_tot = c.take<double>(1);
+    uint32_t* taken = c.take<uint32_t>(taken_words);
+    int32_t* prefix = c.take<int32_t>(1);
 
     tc_relax_params rp = prm->relax;
     rp.accept = 1;
     int64_t b = 0;
-    for (int64_t b0 = 0; b0 < n_sub; b0 += B, ++b) {
-        const int32_t k = (int32_t)std::min<int64_t>(B, n_sub - b0);
-        // interior radius of this batch: linear ramp sigma0 -> sigma1 over the batches
-        const double sigma = n_batches <= 1
-                                 ? prm->sigma1
-                                 : prm->sigma0 + (prm->sigma1 - prm->sigma0) * (double)b / (double)(n_batches - 1);
+    for (int64_t b0 = 0, k = 0; b0 < n_sub; b0 += k, ++b) {
+        k = std::min<int64_t>(B, n_sub - b0);
+        // interior radius of this batch: linear ramp sigma0 -> sigma1 over the batches (fixed
+        // batches) or over the subdomain index of the batch's first zone (disjoint batches)
+        double sigma;
+        if (!disjoint)
+            sigma = n_batches <= 1 ? prm->sigma1
+                                   : sigma0 + (prm->sigma1 - sigma0) * (double)b / (double)(n_batches - 1);
+        else
+            sigma = n_sub <= 1 ? prm->sigma1 : sigma0 + (prm->sigma1 - sigma0) * (double)b0 / (double)(n_sub - 1);
         rp.radius = sigma;
         err = allpairs(pos, n, lp, nullptr, energy ? energy + b : e_tot, e_loc, s);
         if (err != TC_OK) return err;
-        err = select_zones(pos, n, e_loc, flags, &prm->zone, sigma, prm->zone.phase + b0, k, uniforms + 3 * b0, idx,
-                           offs, nullptr, nullptr, s);
+        err = select_zones(pos, n, e_loc, flags, &prm->zone, sigma, prm->zone.phase + b0, (int32_t)k,
+                           uniforms + 3 * b0, idx, offs, nullptr, nullptr, s);
         if (err != TC_OK) return err;
-        err = relax(pos, n, idx, offs, k, nullptr, flags, &rp, out + b0, s);
+        if (disjoint && k > 1) {
+            int32_t kk = 1;
+            cudaError_t e = cudaMemsetAsync(taken, 0, 4 * (size_t)taken_words, s);
+            if (e == cudaSuccess) {
+                k_disjoint_prefix<<<1, kPrefixThreads, 0, s>>>(idx, offs, (int32_t)k, taken, prefix);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&kk, prefix, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "disjoint prefix");
+            if (kk < 1 || kk > k) return TC_ERR_CUDA;
+            k = kk;
+        }
+        err = relax(pos, n, idx, offs, (int32_t)k, nullptr, flags, &rp, out + b0, s);
         if (err != TC_OK) return err;
     }
-    if (energy) return allpairs(pos, n, lp, nullptr, energy + n_batches, nullptr, s);
+    if (energy) return allpairs(pos, n, lp, nullptr, energy + b, nullptr, s);
     return TC_OK;
 }
 
@@ -468,6 +531,7 @@ tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uin
 {
     tc::NvtxRange nvtx_range("tc_border_split");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (sigma <= 0.0 && n >= 1) sigma = eq_sigma(n);  // Eq. sigma
     if (n < 0 || n > INT32_MAX || n_b < 0 || n_b > n || !(sigma > 0.0) || !(sigma <= 1.0) ||
         (n > 0 && (!pos || !flags)) || misaligned(pos, 16))
         return TC_ERR_INVALID_ARG;

@@ -256,3 +256,46 @@ def test_cycle_lbfgsb_zones_fp64_matches_oracle(batch, line_search):
     assert abs(trace[-1].item() - eg) <= 1e-13 * eg
     d = r.delta_e.cpu().numpy()
     np.testing.assert_allclose(d[ao == 1], do[ao == 1], rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("optimizer", ["bb", "lbfgsb_tu"])
+def test_disjoint_cycle_fp64_matches_oracle(optimizer):
+    """Disjoint batches (the longest prefix of pairwise disjoint zones among the next `batch`
+    subdomains): the same batches, zones, accept decisions, positions and energy trace as the oracle,
+    no zone skipped.  The GPU call takes sigma0 <= 0 as Eq. sigma; the oracle is given the value."""
+    n = 1500
+    pos = synth.arcsine_disk(n, 17)
+    s0 = 1 - 1 / (2 * np.sqrt(n))
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
+    n_sub = 14
+    u = np.random.default_rng(18).random((n_sub, 3))
+    eta = 1e-4 / n
+    kw = dict(m_min=20, m_max=200, period=5)
+    opt = dict(memory=6, maxstep=0.02, step0=1e-4) if optimizer == "lbfgsb_tu" else dict(step0=eta)
+    po, trace_o, do, ao = oracle.cycle(p0, u, batch=5, alpha_min=0.0, alpha_max=10 * eta, steps=8, sigma0=s0,
+                                       sigma1=1.0, flags=f, disjoint=True, optimizer=optimizer, **opt, **kw)
+    assert len(trace_o) - 1 > -(-n_sub // 5)  # some batch was cut short by an overlap
+    p = T(p0.copy())
+    r, trace = tc.cycle(p, T(u), T(f), batch=5, local_precision="fp64", precision="fp64", optimizer=optimizer,
+                        n_steps=8, alpha_min=0.0, alpha_max=10 * eta, sigma0=0.0, sigma1=1.0, disjoint=True,
+                        **opt, **kw)
+    tc.sync_status()
+    st = r.status.cpu().numpy()
+    np.testing.assert_array_equal(st, ao)
+    assert np.all(st != 2)
+    np.testing.assert_allclose(p.cpu().numpy(), po, rtol=0, atol=1e-11)
+    tr = trace.cpu().numpy()
+    assert tr.shape == trace_o.shape
+    np.testing.assert_allclose(tr, trace_o, rtol=1e-13)
+
+
+def test_border_split_default_sigma_is_eq_sigma():
+    """sigma left out: the interior radius of Eq. sigma, 1 - 1/(2 sqrt(N)) (Sec. II B)."""
+    n = 4000
+    pos = synth.arcsine_disk(n, 19)
+    po, fo = oracle.border_split(pos, oracle.boundary_count(n), 1 - 1 / (2 * np.sqrt(n)))
+    p = T(pos.copy())
+    f = tc.border_split(p)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(f.cpu().numpy(), fo)
+    np.testing.assert_array_equal(p.cpu().numpy(), po)

@@ -1081,3 +1081,59 @@ def test_lbfgs_direction_is_the_dense_inverse_bfgs_product(n, seed, memory, iter
     assert wrapped >= 5  # the ring was full and overwrote its oldest pair several times
     if (seed, tu) in ((0, False), (5, True), (3, False)):
         assert skipped >= 1
+
+
+def test_disjoint_cycle_is_its_steps_in_order():
+    """The disjoint batch rule, rebuilt from the oracle's pieces: at each batch start the local
+    energies, the zones of the next `batch` subdomains at sigma(b0) = s0 + (1 - s0) b0 / (n_sub - 1),
+    their longest prefix of pairwise disjoint zones (set intersections here), each prefix zone
+    relaxed against the batch-start configuration, the float64 accept in order.  No zone is skipped,
+    every subdomain is optimised, and at least one batch is cut short by an overlap."""
+    n = 600
+    eta = 1e-4 / n
+    pos = synth.arcsine_disk(n, 41)
+    s0 = 1 - 1 / (2 * math.sqrt(n))
+    p0, f = oracle.border_split(pos, oracle.boundary_count(n), s0)
+    n_sub, cap = 12, 4
+    u = np.random.default_rng(42).random((n_sub, 3))
+    kw = dict(m_min=15, m_max=90, period=5)
+    p, trace, d, acc = oracle.cycle(p0, u, batch=cap, step0=eta, alpha_min=0.0, alpha_max=10 * eta, steps=5,
+                                    sigma0=s0, sigma1=1.0, flags=f, disjoint=True, **kw)
+    q = p0.copy()
+    b0, b, cut = 0, 0, 0
+    while b0 < n_sub:
+        k = min(cap, n_sub - b0)
+        radius = s0 + (1.0 - s0) * b0 / (n_sub - 1)
+        e_tot, e_loc = oracle.energy(q, local=True)
+        assert trace[b] == e_tot
+        idx, off, _, _ = oracle.zone_select(q, e_loc, u[b0:b0 + k], phase=b0, radius=radius, flags=f, **kw)
+        zones = [set(idx[off[s]:off[s + 1]].tolist()) for s in range(k)]
+        kk = 1
+        while kk < k and all(not (zones[kk] & zones[j]) for j in range(kk)):
+            kk += 1
+        cut += kk < k
+        act = np.concatenate([oracle.subdomain_bb(q, idx[off[s]:off[s + 1]], eta, 0.0, 10 * eta, 5, radius=radius,
+                                                  flags=f) for s in range(kk)])
+        q, db, ab = oracle.accept_sequential(q, idx[:off[kk]], off[:kk + 1], act)
+        np.testing.assert_array_equal(db, d[b0:b0 + kk])
+        np.testing.assert_array_equal(ab, acc[b0:b0 + kk])
+        b0 += kk
+        b += 1
+    np.testing.assert_array_equal(p, q)
+    assert len(trace) == b + 1 and trace[b] == oracle.energy(q)
+    assert cut >= 1 and np.all(acc != 2) and (acc == 1).sum() >= 6
+
+
+def test_disjoint_cycle_with_batch_one_is_the_plain_cycle():
+    """batch = 1 is the paper's one-zone-at-a-time cycle in both forms (the ramp in b0 / (n_sub - 1)
+    equals the ramp in b / (n_batches - 1) there)."""
+    n = 300
+    eta = 1e-4 / n
+    pos = synth.arcsine_disk(n, 43)
+    u = np.random.default_rng(44).random((6, 3))
+    kw = dict(m_min=10, m_max=50, period=3, batch=1, step0=eta, alpha_min=0.0, alpha_max=10 * eta, steps=4,
+              sigma0=0.97, sigma1=1.0)
+    a = oracle.cycle(oracle.project(pos, 0.97), u, **kw)
+    b = oracle.cycle(oracle.project(pos, 0.97), u, disjoint=True, **kw)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
