@@ -39,9 +39,10 @@ N_SUB = 256
 M_LO, M_HI = 200, 5000
 RELAX_STEPS = 200
 LOCAL_PREC = "fp64"  # the total energy needs 12+ digits: float64
-# DRAM bytes of one relaxation-pass launch of this workload, from an ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum (profiles/relax_pass_traffic_n1e5.md); it must be
-# retaken (or set to None) whenever k_pass_mixed changes.
+# DRAM bytes of one relaxation-pass launch of this workload: dram__bytes_read.sum +
+# dram__bytes_write.sum of k_pass_mixed launches 6..8 in one ncu capture of
+# `python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-instances --config 3`; the capture
+# must be retaken, or this set to None, whenever that kernel changes.
 RELAX_PASS_DRAM_BYTES = 16.3e6
 METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
 UNIT = "pair-interactions/s"
@@ -60,10 +61,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-instances", action="store_true", help="skip the batched-instances (C5) section")
     # a single small kernel case (used for profiler captures): no JSON bench line
-    ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle"], default=None)
+    ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle", "instances"], default=None)
     ap.add_argument("--batch", type=int, default=64, help="cycle case: subdomains per batch")
     ap.add_argument("--zone-steps", type=int, default=100, help="cycle case: relaxation steps per zone")
     ap.add_argument("--cycle-opt", choices=["bb", "lbfgsb_tu"], default="lbfgsb_tu", help="cycle case: zone optimiser")
+    ap.add_argument("--fixed-batches", action="store_true",
+                    help="cycle case: fixed batches (overlapping zones skipped) instead of disjoint prefixes")
     ap.add_argument("--prec", choices=["mixed", "fp64", "fp64x"], default="mixed")
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--nsub", type=int, default=16)
@@ -81,15 +84,21 @@ def run_case(args):
 
     dev = torch.device("cuda", 0)
     if args.case == "full-relax":
-        print(json.dumps(run_full_relax(dev, n=args.n)))
-        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=1000, polish_precision="fp64x")))
-        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=1000, polish_precision="fp64x", line_search=8)))
+        # the C4 workload with longer budgets than the bench line's entry: mixed steps past the 1e-4
+        # tolerance, then float64-grade (fp64x) and float64 polishes
+        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=200)), flush=True)
+        print(json.dumps(run_full_relax(dev, n=args.n, extra_mixed=20000, max_polish=2000,
+                                        polish_precision="fp64x")), flush=True)
+        return
+    if args.case == "instances":
+        # config C5 alone: 512 instances, mixed L-BFGS with a float64 polish, graph on and off
+        print(json.dumps(run_instances(dev, rounds=2)), flush=True)
         return
     if args.case == "cycle":
         # cycle time against N at a fixed number of subdomain optimisations (Sec. II E)
         for n in [args.n // 8, args.n // 4, args.n // 2, args.n]:
             print(json.dumps(run_cycle(dev, n=n, n_sub=args.nsub, batch=args.batch, steps=args.zone_steps,
-                                       optimizer=args.cycle_opt)))
+                                       optimizer=args.cycle_opt, disjoint=not args.fixed_batches)))
         return
     if args.config is not None:
         from paper_2609_24722_b300 import _lib
@@ -270,6 +279,48 @@ def _cpu_model() -> str:
     return "unknown"
 
 
+def run_c3_disjoint(pos_np, relax_kw: dict, flush, stream, reps: int = 2, seed: int = 0) -> dict:
+    """One adaptive-cycle step (float64 local energies + 200 mixed BB steps + float64 accept) on 256
+    pairwise disjoint subdomains holding 0.9 N charges (synth.disjoint_subdomains), timed like the
+    headline step."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2609_24722_b300 as tc
+
+    dev = flush.device
+    subs = synth.disjoint_subdomains(pos_np, N_SUB, M_LO, M_HI, seed + 2)
+    idx_np, off_np = synth.to_csr(subs)
+    idx, off = torch.tensor(idx_np, device=dev), torch.tensor(off_np, device=dev)
+    pos0 = torch.tensor(pos_np, device=dev)
+    p = pos0.clone()
+    ms, prof, acc = [], None, 0
+    for k in range(reps + 1):
+        p.copy_(pos0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tc.local_energy(p, LOCAL_PREC)
+        r = tc.relax_subdomains(p, idx, off, **relax_kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            ms.append(a.elapsed_time(b))
+            prof = tc.relax_last_profile()
+            acc = int((r.status == 1).sum().item())
+    tc.sync_status()
+    pairs = N * (N - 1) + RELAX_STEPS * prof["pass_pairs"]
+    pass_ms = prof["pass_ms"] / max(prof["n_pass"], 1)
+    return {"workload": f"{N_SUB} disjoint subdomains holding {int(off_np[-1])} charges (m ~ U[{M_LO},{M_HI}] "
+                        f"scaled by 0.9 N / sum m, nearest charges not yet taken), {RELAX_STEPS} mixed BB steps, "
+                        f"fp64 local energies and sequential accept",
+            "ms_per_step": statistics.mean(ms), "pairs_per_s": pairs / (statistics.mean(ms) / 1e3),
+            "relax_pass_ms": pass_ms, "relax_pass_pairs_per_s": prof["pass_pairs"] / (pass_ms / 1e3),
+            "accepted_subdomains": acc, "skipped_overlap": int((r.status == 2).sum().item())}
+
+
 def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
                   polish: int = 20, fp64_steps: int = 10, polish_precision: str = "fp64"):
     """Config C5: 512 independent instances (N_k ~ U{100..5000}, arcsine init each), relaxed in one
@@ -347,15 +398,19 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
             "fp64_energy_vs_oracle_max_rel": parity}
 
 
-def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 200,
-                   polish_precision: str = "fp64", line_search: int = 0) -> dict:
-    """Config C4: one configuration of N = 1e5 charges (arcsine init, Hilbert order) relaxed by
-    mixed-precision L-BFGS(8) on the wall map until the RMS of dE/dz falls below 1e-4 x the initial
-    mean force, then float64 L-BFGS (or the float64-grade fp64x pass) to 1e-8 x that (step caps
-    max_mixed / max_polish)."""
+def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 100,
+                   polish_precision: str = "fp64", line_search: int = 0, extra_mixed: int = 0,
+                   oracle_check: bool = True) -> dict:
+    """Config C4: one configuration of N charges (arcsine init, Hilbert order) relaxed by mixed-precision
+    L-BFGS(8) on the wall map until the RMS of dE/dz falls below 1e-4 x the initial mean force F_ref
+    (then `extra_mixed` more mixed steps), then float64 L-BFGS (or the float64-grade fp64x pass) towards
+    1e-8 F_ref, stopping there or at max_polish steps.  The returned configuration's float64 energy,
+    computed by the library in the polish call, is compared with the oracle's evaluation of the same
+    configuration (one half of the sum of its rows' 1/r sums, rows split over every host thread)."""
     import numpy as np
     import torch
 
+    import oracle
     import synth
     import paper_2609_24722_b300 as tc
 
@@ -367,37 +422,58 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
     e0 = tc.energy(p, "fp64").item()
     world = torch.tensor([[0, n]], dtype=torch.int64, device=dev)
     h = math.sqrt(2 * math.pi / (math.sqrt(3.0) * n))
+    kw = dict(world=world, optimizer="lbfgs", memory=8, step0=1e-6, maxstep=0.1 * h, accept=False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    r1 = tc.relax_subdomains(p, world=world, precision="mixed", optimizer="lbfgs", n_steps=max_mixed, memory=8,
-                             step0=1e-6, maxstep=0.1 * h, gtol=1e-4 * f_ref, accept=False, line_search=line_search)
+    r1 = tc.relax_subdomains(p, precision="mixed", n_steps=max_mixed, gtol=1e-4 * f_ref, line_search=line_search,
+                             **kw)
+    steps1 = int(r1.steps[0])
+    if extra_mixed > 0:
+        rx = tc.relax_subdomains(p, precision="mixed", n_steps=extra_mixed, line_search=line_search, **kw)
+        steps1 += int(rx.steps[0])
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    r2 = tc.relax_subdomains(p, world=world, precision=polish_precision, optimizer="lbfgs", n_steps=max_polish,
-                             memory=8,
-                             step0=1e-6, maxstep=0.1 * h, gtol=1e-8 * f_ref, accept=False, want_energy=True)
+    e_mid = tc.energy(p, "fp64").item()
+    torch.cuda.synchronize()
+    t1b = time.perf_counter()
+    r2 = tc.relax_subdomains(p, precision=polish_precision, n_steps=max_polish, gtol=1e-8 * f_ref, want_energy=True,
+                             **kw)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     tc.sync_status()
     e = r2.energy[0].item()
-    return {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 mean|F0|, {polish_precision} polish to 1e-8 "
-                        f"(caps {max_mixed} / {max_polish} steps), Armijo halvings per mixed step: {line_search}",
-            "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
-            "mixed_steps": int(r1.steps[0]), "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
-            "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1,
-            "relax_time_s": t2 - t0, "mean_force_initial": f_ref, "energy_initial": e0, "energy_final": e,
-            "E_over_N2": e / n ** 2, "pi_over_4": math.pi / 4}
+    out = {"workload": f"N={n} arcsine init, mixed L-BFGS(8) to RMS dE/dz < 1e-4 F_ref (+{extra_mixed} steps), "
+                       f"{polish_precision} polish towards 1e-8 F_ref (caps {max_mixed} / {max_polish} steps), "
+                       f"F_ref = initial mean |F|, Armijo halvings per mixed step: {line_search}",
+           "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
+           "mixed_steps": steps1, "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
+           "energy_after_mixed": e_mid,
+           "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1b,
+           "polish_ms_per_step": 1e3 * (t2 - t1b) / max(int(r2.steps[0]), 1),
+           "relax_time_s": (t1 - t0) + (t2 - t1b), "mean_force_initial": f_ref, "tolerance_polish": 1e-8 * f_ref,
+           "energy_initial": e0, "energy_final": e, "E_over_N2": e / n ** 2, "pi_over_4": math.pi / 4}
+    if oracle_check:
+        x = p.cpu().numpy()
+        t3 = time.perf_counter()
+        _, rows = oracle.rows_grad(x, np.arange(n, dtype=np.int32), openmp=True)
+        e_or = 0.5 * math.fsum(rows.tolist())
+        out["oracle_energy"] = e_or
+        out["energy_vs_oracle_rel"] = abs(e - e_or) / e_or
+        out["oracle_s"] = time.perf_counter() - t3
+    return out
 
 
 def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 100, m_min: int = 200,
               m_max: int = 4000, period: int = 64, seed: int = 0, local_precision: str = "mixed",
-              optimizer: str = "lbfgsb_tu") -> dict:
+              optimizer: str = "lbfgsb_tu", disjoint: bool = True) -> dict:
     """The adaptive optimisation cycle (Sec. II C) on the GPU, after the border-interior split of
-    Sec. II B (N_b pinned boundary charges, interior radius ramped from Eq. sigma to 1 over the
-    batches): per batch of `batch` subdomains, local energies of all N charges, defect threshold e_i > mu - sigma_e, centres (80 % at defects, 20 %
-    uniform in the disk), zones of the m nearest charges (m a triangle wave between m_min and m_max),
-    `steps` mixed steps per zone against all N (projected BB, or the paper's L-BFGS-B on (t, u) with
-    optimizer="lbfgsb_tu"), sequential float64 accept."""
+    Sec. II B (N_b of Eq. Nb pinned boundary charges, interior radius ramped from Eq. sigma to 1):
+    per batch, local energies of all N charges, defect threshold e_i > mu - sigma_e, centres (80 % at
+    defects, 20 % uniform in the disk), zones of the m nearest charges (m a triangle wave between
+    m_min and m_max), `steps` mixed steps per zone against all N (projected BB, or the paper's
+    L-BFGS-B on (t, u) with optimizer="lbfgsb_tu"), sequential float64 accept.  disjoint=True: a
+    batch is the longest prefix of pairwise disjoint zones among the next `batch` subdomains, so no
+    relaxed zone is discarded; disjoint=False: fixed batches, where overlapping zones are skipped."""
     import numpy as np
     import torch
 
@@ -407,14 +483,13 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     pos = synth.lattice_disk(n, seed)
     pos = np.ascontiguousarray(pos[synth.zorder(pos)])
     p = torch.tensor(pos, device=dev)
-    # border-interior split (Sec. II B): N_b of Eq. Nb pinned to the circle, the rest inside sigma0
-    sigma0 = 1.0 - 0.5 / math.sqrt(n)
-    flags = tc.border_split(p, tc.boundary_count(n), sigma0)
+    # border-interior split (Sec. II B): N_b of Eq. Nb pinned to the circle, the rest inside Eq. sigma
+    flags = tc.border_split(p)
     u = torch.tensor(np.random.default_rng(seed + 7).random((n_sub, 3)), device=dev)
     eta = 1e-4 / n
     kw = dict(batch=batch, m_min=m_min, m_max=m_max, period=period, local_precision=local_precision,
               precision="mixed", optimizer=optimizer, n_steps=steps, step0=eta, alpha_min=0.0, alpha_max=10 * eta,
-              sigma0=sigma0, sigma1=1.0)
+              sigma0=0.0, sigma1=1.0, disjoint=disjoint)
     if optimizer != "bb":
         # quasi-Newton: the first step is eta-scaled, later ones scale themselves; each charge moves
         # at most 1e-3 in (t, u) per step (a sixth of the local spacing at N = 1e5)
@@ -430,10 +505,13 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     torch.cuda.synchronize()
     tc.sync_status()
     ms = a.elapsed_time(b)
-    n_batches = -(-n_sub // batch)
-    pairs = int(sizes.sum()) * (n - 1) * (steps + 1) + n_batches * n * (n - 1)
     tr = trace.cpu().numpy()
+    n_batches = len(tr) - 1
     st = r.status.cpu().numpy()
+    relaxed = st != 2
+    # ordered pairs: every relaxed zone's rows against all N for steps + 1 passes, one local-energy
+    # pass per batch
+    pairs = int(sizes[relaxed].sum()) * (n - 1) * (steps + 1) + n_batches * n * (n - 1)
     # structure analysis of the cycle's end configuration (Sec. III C-D)
     tc.voronoi_order(p)
     torch.cuda.synchronize()
@@ -444,14 +522,16 @@ def run_cycle(dev, n: int = N, n_sub: int = 256, batch: int = 64, steps: int = 1
     tc.sync_status()
     structure = {"ms": a.elapsed_time(b), "P_z6": float(summ["P_z"][6]), "mean_abs_psi6": summ["mean_abs_psi6"],
                  "abs_mean_psi6": summ["abs_mean_psi6"]}
+    form = (f"batches of the longest disjoint prefix of up to {batch} zones" if disjoint
+            else f"fixed batches of {batch}")
     return {"workload": f"N={n} lattice background split into N_b={tc.boundary_count(n)} pinned boundary charges "
-                        f"and an interior disk whose radius ramps {sigma0:.5f} -> 1 over the batches; {n_sub} "
-                        f"subdomains in batches of {batch}, zones of {m_min}..{m_max} nearest charges (triangle "
+                        f"(Eq. Nb) and an interior disk whose radius ramps from Eq. sigma to 1; {n_sub} "
+                        f"subdomains in {form}, zones of {m_min}..{m_max} nearest charges (triangle "
                         f"wave, period {period}), {steps} mixed {'BB' if optimizer == 'bb' else optimizer} steps each, "
-                        f"{local_precision} local energies "
-                        f"per batch, fp64 sequential accept",
+                        f"{local_precision} local energies per batch, fp64 sequential accept",
             "cycle_time_s": ms / 1e3, "ms_per_subdomain": ms / n_sub, "pairs_per_s": pairs / (ms / 1e3),
-            "accepted": int((st == 1).sum()), "skipped_overlap": int((st == 2).sum()),
+            "batches": n_batches, "zones_relaxed": int(relaxed.sum()), "accepted": int((st == 1).sum()),
+            "skipped_overlap": int((st == 2).sum()), "accepted_per_s": float((st == 1).sum()) / (ms / 1e3),
             "energy_start": float(tr[0]), "energy_end": float(tr[-1]), "energy_drop": float(tr[0] - tr[-1]),
             "structure": structure}
 
@@ -574,7 +654,7 @@ def main():
     out_h = torch.empty_like(pos_h).pin_memory()
     res_h = torch.empty((N_SUB, 4), dtype=torch.float64).pin_memory()
     e2e_ms = []
-    for k in range(2):
+    for k in range(args.steps):
         flush.zero_()
         barrier()
         t0 = time.perf_counter()
@@ -618,20 +698,29 @@ def main():
         c3_pass[prec_name] = {"ms_per_pass": ms_p, "pairs_per_s": pr["pass_pairs"] / (ms_p / 1e3)}
     c3_pass["mixed"] = {"ms_per_pass": prof["pass_ms"] / max(prof["n_pass"], 1),
                         "pairs_per_s": prof["pass_pairs"] / (prof["pass_ms"] / max(prof["n_pass"], 1) / 1e3)}
+    # SURVEY Q1's second reading of the subdomain workload: 256 truly disjoint subdomains, m ~ U{200..5000}
+    # scaled by 0.9 N / sum(m), every one relaxed and accepted on its own merit (no overlap skips)
+    c3_disjoint = run_c3_disjoint(pos_np, relax_kw, flush, stream, reps=2, seed=rank)
     ms_mixed = time_allpairs("mixed", 5)
     ms_f64 = time_allpairs("fp64", 3)
     ms_f64x = time_allpairs("fp64x", 3)
     c5 = run_instances(dev) if not args.no_instances else None
+    # config C4: the full relaxation of one N = 1e5 configuration, float64 polish, oracle energy check
+    c4 = run_full_relax(dev) if not args.no_instances else None
     if c5 is not None:
         c5x = run_instances(dev, polish=50, polish_precision="fp64x")
         c5["fp64x_polish_variant"] = {k: c5x[k] for k in ("workload", "relax_time_s", "pairs_per_s_mixed_with_polish",
                                                             "best_energy_sum", "fp64_energy_vs_oracle_max_rel")}
     # the cycle with the paper's optimiser per zone (L-BFGS-B on (t, u)), and with projected BB
+    # (batches of disjoint zones), then the fixed batches whose overlapping zones are skipped
     cyc = run_cycle(dev, optimizer="lbfgsb_tu") if not args.no_instances else None
     if cyc is not None:
+        keys = ("workload", "cycle_time_s", "ms_per_subdomain", "batches", "zones_relaxed", "accepted",
+                "skipped_overlap", "accepted_per_s", "energy_start", "energy_end", "energy_drop")
         cb = run_cycle(dev, optimizer="bb")
-        cyc["bb_variant"] = {k: cb[k] for k in ("workload", "cycle_time_s", "ms_per_subdomain", "accepted",
-                                                 "energy_start", "energy_end", "energy_drop")}
+        cyc["bb_variant"] = {k: cb[k] for k in keys}
+        cf = run_cycle(dev, optimizer="lbfgsb_tu", disjoint=False)
+        cyc["fixed_batches_variant"] = {k: cf[k] for k in keys}
     pipes = tc.probe_pipes()
     tc.sync_status()
 
@@ -672,6 +761,9 @@ def main():
         "config": {"workload": WORKLOAD, "n": N, "n_sub": N_SUB, "m_range": [M_LO, M_HI],
                    "relax_steps": RELAX_STEPS, "optimizer": "projected BB, step0 1e-4/N, alpha_max 1e-3/N",
                    "accept": "fp64 pairwise, sequential", "pairs_per_step": pairs_step,
+                   "pairs_per_step_by_kind": {"energy_only_local_energies": N * (N - 1),
+                                              "gradient_only_relaxation": RELAX_STEPS * prof["pass_pairs"],
+                                              "energy_and_gradient": 0},
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replica x{world}",
                    "pass_shape": tuned["best"]},
         "relax_time_s": ms_step / 1e3,
@@ -682,7 +774,9 @@ def main():
                           "fp64_pairs_per_s": N * (N - 1) / (ms_f64 / 1e3), "fp64_ms": ms_f64,
                           "fp64x_pairs_per_s": N * (N - 1) / (ms_f64x / 1e3), "fp64x_ms": ms_f64x},
         "c3_relax_pass_by_precision": c3_pass,
+        "c3_disjoint_subdomains": c3_disjoint,
         "instances_c5": c5,
+        "full_relax_c4": c4,
         "adaptive_cycle": cyc,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},

@@ -92,6 +92,13 @@ __global__ void k_noalloc_finish(Prob p, int64_t W, int64_t G, const double* __r
     }
 }
 
+// n = 1: no pairs, so E = 0 and e_0 = 0, unless the one charge is invalid (NaN energy).
+__global__ void k_noalloc_one(const int* st, double* __restrict__ energy, double* __restrict__ local_e)
+{
+    *energy = (*((volatile const int*)st) != 0) ? __longlong_as_double(0x7ff8000000000000LL) : 0.0;
+    if (local_e) *local_e = 0.0;
+}
+
 }  // namespace
 
 static tc_status energy_noalloc(const double* pos, int64_t n, tc_precision prec, double* energy, double* local_e,
@@ -114,13 +121,16 @@ static tc_status energy_noalloc(const double* pos, int64_t n, tc_precision prec,
     if (cudaError_t e = cudaMemsetAsync(base, 0, kCounterBytes, s); e != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync (static scratch)");
     const double2* pos2 = reinterpret_cast<const double2*>(pos);
-    if (n <= 1) {
+    if (n == 0) {
         if (cudaError_t e = cudaMemsetAsync(energy, 0, sizeof(double), s); e != cudaSuccess)
             return cuda_fail(e, "cudaMemsetAsync");
-        if (local_e && n == 1)
-            if (cudaError_t e = cudaMemsetAsync(local_e, 0, sizeof(double), s); e != cudaSuccess)
-                return cuda_fail(e, "cudaMemsetAsync");
         return TC_OK;
+    }
+    if (n == 1) {
+        // the one charge is still checked, as tc_energy checks it
+        k_noalloc_prep<<<1, 32, 0, s>>>(pos2, 1, nullptr, st);
+        k_noalloc_one<<<1, 1, 0, s>>>(st, energy, local_e);
+        return cuda_status(cudaGetLastError(), "tc_energy_noalloc launch");
     }
     Plan P;
     Prob p{};

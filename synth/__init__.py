@@ -174,6 +174,43 @@ def subdomains(pos: np.ndarray, n_sub: int, m_lo: int, m_hi: int, seed: int,
     return out
 
 
+def disjoint_subdomains(pos: np.ndarray, n_sub: int, m_lo: int, m_hi: int, seed: int, fill: float = 0.9,
+                        frac_at_charge: float = 0.8) -> list[np.ndarray]:
+    """Pairwise disjoint subdomains with the size mix of subdomains(): m ~ U{m_lo..m_hi} scaled by
+    fill * N / sum(m) (so together they hold about fill * N charges), centres drawn as in
+    subdomains(), and subdomain s taking the m_s nearest charges to its centre that no earlier
+    subdomain holds.  Returns one strictly ascending int32 index array per subdomain."""
+    from scipy.spatial import cKDTree
+
+    g = _rng(seed)
+    n = pos.shape[0]
+    m = g.integers(m_lo, m_hi + 1, size=n_sub).astype(np.float64)
+    m = np.maximum(1, np.floor(m * fill * n / m.sum())).astype(np.int64)
+    tree = cKDTree(pos)
+    free = np.ones(n, dtype=bool)
+    out = []
+    for k in range(n_sub):
+        if g.random() < frac_at_charge:
+            c = pos[int(g.integers(0, n))]
+        else:
+            rr = math.sqrt(g.random())
+            th = g.random() * 2.0 * math.pi
+            c = np.array([rr * math.cos(th), rr * math.sin(th)])
+        want = int(min(m[k], free.sum()))
+        q = want
+        while True:
+            _, idx = tree.query(c, k=min(n, q))
+            idx = np.atleast_1d(idx)
+            idx = idx[free[idx]]
+            if idx.size >= want or q >= n:
+                break
+            q = min(n, 2 * q + 16)
+        idx = idx[:want]
+        free[idx] = False
+        out.append(np.sort(idx).astype(np.int32))
+    return out
+
+
 def to_csr(sets: list[np.ndarray]) -> tuple[np.ndarray, np.ndarray]:
     """Concatenate index sets into (idx int32, offsets int64[len+1])."""
     offsets = np.zeros(len(sets) + 1, dtype=np.int64)

@@ -283,10 +283,13 @@ def test_disjoint_cycle_fp64_matches_oracle(optimizer):
     st = r.status.cpu().numpy()
     np.testing.assert_array_equal(st, ao)
     assert np.all(st != 2)
-    np.testing.assert_allclose(p.cpu().numpy(), po, rtol=0, atol=1e-11)
+    # later batches start from positions moved by earlier ones, so float64 rounding differences
+    # (fused multiply-adds on the GPU, none in the oracle) carry through: ~1e-10 after 14 zones,
+    # which moves E (~1.8e6, wall forces ~1e5) by ~5e-6, i.e. ~3e-12 relative
+    np.testing.assert_allclose(p.cpu().numpy(), po, rtol=0, atol=1e-9)
     tr = trace.cpu().numpy()
     assert tr.shape == trace_o.shape
-    np.testing.assert_allclose(tr, trace_o, rtol=1e-13)
+    np.testing.assert_allclose(tr, trace_o, rtol=1e-11)
 
 
 def test_border_split_default_sigma_is_eq_sigma():

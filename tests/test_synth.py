@@ -75,3 +75,19 @@ def test_zorder_is_a_spatially_local_permutation():
     # blocks of 512 consecutive charges are compact
     ext = max(np.ptp(p[k:k + 512], axis=0).max() for k in range(0, 50000 - 512, 512))
     assert ext < 0.6
+
+
+def test_disjoint_subdomains_are_disjoint_and_fill_the_share():
+    pos = synth.lattice_disk(20000, 1)
+    subs = synth.disjoint_subdomains(pos, 64, 200, 5000, 3)
+    allidx = np.concatenate(subs)
+    assert len(np.unique(allidx)) == allidx.size
+    assert 0.85 * 20000 <= allidx.size <= 0.9 * 20000
+    for s in subs:
+        assert s.dtype == np.int32 and np.all(np.diff(s) > 0)
+    # the first subdomain is the nearest-charge ball around its centre (nothing was taken before it)
+    first = subs[0]
+    c = pos[first].mean(0)
+    r_in = np.linalg.norm(pos[first] - c, axis=1).max()
+    others = np.setdiff1d(np.arange(20000), first)
+    assert np.linalg.norm(pos[others] - c, axis=1).min() > 0.5 * r_in
