@@ -61,10 +61,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-instances", action="store_true", help="skip the batched-instances (C5) section")
     # a single small kernel case (used for profiler captures): no JSON bench line
-    ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle", "instances"], default=None)
+    ap.add_argument("--case", choices=["allpairs", "relax", "full-relax", "cycle", "instances", "delta"], default=None)
     ap.add_argument("--batch", type=int, default=64, help="cycle case: subdomains per batch")
     ap.add_argument("--zone-steps", type=int, default=100, help="cycle case: relaxation steps per zone")
     ap.add_argument("--cycle-opt", choices=["bb", "lbfgsb_tu"], default="lbfgsb_tu", help="cycle case: zone optimiser")
+    ap.add_argument("--single", action="store_true", help="cycle case: only N = --n (no N/8, N/4, N/2 runs)")
     ap.add_argument("--fixed-batches", action="store_true",
                     help="cycle case: fixed batches (overlapping zones skipped) instead of disjoint prefixes")
     ap.add_argument("--prec", choices=["mixed", "fp64", "fp64x"], default="mixed")
@@ -96,7 +97,7 @@ def run_case(args):
         return
     if args.case == "cycle":
         # cycle time against N at a fixed number of subdomain optimisations (Sec. II E)
-        for n in [args.n // 8, args.n // 4, args.n // 2, args.n]:
+        for n in ([args.n] if args.single else [args.n // 8, args.n // 4, args.n // 2, args.n]):
             print(json.dumps(run_cycle(dev, n=n, n_sub=args.nsub, batch=args.batch, steps=args.zone_steps,
                                        optimizer=args.cycle_opt, disjoint=not args.fixed_batches)))
         return
@@ -109,6 +110,22 @@ def run_case(args):
         p = torch.tensor(pa[synth.zorder(pa)], device=dev)
         work = lambda: tc.grad(p, args.prec, with_energy=True)  # noqa: E731
         pairs = args.n * (args.n - 1)
+    elif args.case == "delta":
+        # the float64 pairwise energy change of the accept (k_pass<DELTA>): subdomains moved by ~1e-4
+        import numpy as np
+
+        pos = synth.lattice_disk(args.n, 0)
+        pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+        subs = synth.subdomains(pos, args.nsub, 200, 2000, 2)
+        idx, off = synth.to_csr(subs)
+        new = pos[idx] + np.random.default_rng(3).normal(0.0, 1e-4, (idx.size, 2))
+        new *= np.minimum(1.0, 1.0 / np.linalg.norm(new, axis=1))[:, None]
+        p, it, of, nw = (torch.tensor(a, device=dev) for a in (pos, idx, off, new))
+        if args.prec == "mixed":
+            work = lambda: tc.subdomain_delta_energy_mixed(p, it, of, nw)  # noqa: E731
+        else:
+            work = lambda: tc.subdomain_delta_energy(p, it, of, nw)  # noqa: E731
+        pairs = sum(len(s) for s in subs) * (args.n - 1)
     else:
         pos = synth.lattice_disk(args.n, 0)
         pos = pos[synth.zorder(pos)]
@@ -379,6 +396,7 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
     b.record()
     torch.cuda.synchronize()
     ms_nograph = a.elapsed_time(b)
+    prof0 = tc.relax_last_profile()
     # float64 pair terms, same instances, a few steps
     p = torch.tensor(pos_np, device=dev)
     torch.cuda.synchronize()
@@ -393,6 +411,7 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
                         f"{rounds - 1} kick restarts, mixed L-BFGS(8) {steps} steps + {polish_precision} polish {polish}",
             "relax_time_s": ms_total / 1e3, "pairs_per_s_mixed_with_polish": pairs_total / (ms_total / 1e3),
             "round0_s_graph": ms_rounds[0] / 1e3, "round0_s_no_graph": ms_nograph / 1e3,
+            "round0_breakdown_ms": {k: prof0[k] for k in ("pass_ms", "update_ms", "relax_ms", "n_pass")},
             "pairs_per_s_fp64": pairs64 / (ms64 / 1e3), "fp64_steps": fp64_steps,
             "best_energy_sum": float(best_e.sum()),
             "fp64_energy_vs_oracle_max_rel": parity}

@@ -85,7 +85,8 @@ const char* tc_last_error(void);
 /* Waits for `stream`, then returns and clears the current device's status word. */
 tc_status tc_sync_status(tc_stream stream);
 
-/* Frees every workspace of every device this process used. */
+/* Frees every workspace of every device this process used, and the kept
+ * executable step-loop graphs. */
 void tc_shutdown(void);
 
 /* Total energy, Eq. (hamiltonian):  E = sum_{i<j} 1/|r_i - r_j|.
@@ -243,7 +244,9 @@ typedef struct {
  *   out     [n_sub]     DEVICE results
  * Synchronises `stream`: it reads the sizes to the host first and returns
  * when the results are written.  The step loop runs as a 64-step CUDA graph
- * replayed on `stream`.  With gtol (or polish_gtol) > 0, the host checks
+ * replayed on `stream`; the executable graph is kept after the call, and a
+ * later call whose step loop has the same shape updates it in place instead
+ * of instantiating a new one.  With gtol (or polish_gtol) > 0, the host checks
  * between replays whether any problem still steps, and stops once none
  * does.  Called while `stream` is being captured, every step joins the
  * caller's graph instead.
@@ -315,6 +318,11 @@ typedef struct {
                                wall_tol < sigma0 <= sigma1 <= 1 (1, 1: the plain unit disk) */
     int32_t disjoint;       /* 0: a batch is the next `batch` subdomains; 1: it is the longest
                                prefix of pairwise disjoint zones among them (see tc_cycle) */
+    int32_t ramp_first;     /* this call runs subdomains ramp_first .. ramp_first + n_sub - 1 of a */
+    int32_t ramp_total;     /* cycle of ramp_total (0: of n_sub, ramp_first = 0): the sigma ramp runs
+                               over the whole cycle, so a cycle run as several calls (a checkpoint
+                               after each) takes the radii of one call; with fixed batches
+                               ramp_first must be a multiple of `batch` */
 } tc_cycle_params;
 
 /* One optimisation cycle (Sec. II C) of n_sub subdomains, in batches of
@@ -388,24 +396,25 @@ tc_status tc_border_split(double* pos, int64_t n, int64_t n_b, double sigma, uin
 tc_status tc_voronoi_order(const double* pos, int64_t n, int32_t* z, double* psi6, int32_t* nbr, int32_t max_nbr,
                            double* summary, tc_stream stream);
 
-/* Total energy (and local energies) exactly as tc_energy computes them, but
- * without allocating any device memory.  The paper has no counterpart; this
- * entry point exists for callers that cannot call cudaMalloc: code that runs
- * while a CUDA graph is being captured or inside a host callback, processes
- * whose device memory is handed out by a framework's own pool, and real-time
- * hosts that forbid allocation (and its implicit synchronisation) after
- * start-up.
+/* Total energy (and local energies) as tc_energy computes them for TC_FP64
+ * and TC_MIXED (same pair kernels, same sums, within the same tolerances),
+ * but without allocating any device memory.  The paper has no counterpart.
+ * This entry point is for callers that cannot call cudaMalloc: processes
+ * whose device memory is all handed out by a framework's own pool allocator,
+ * and real-time or embedded hosts that forbid allocation after start-up
+ * (cudaMalloc can block and synchronise the device).
  *   pos [2n], energy [1], local_e [n] (nullable): as for tc_energy.
+ *   prec: TC_FP64 or TC_MIXED (TC_F64X returns TC_ERR_INVALID_ARG).
  *   n <= 200 000; larger n returns TC_ERR_INVALID_ARG (tc_last_error() says why).
  * Scratch: one fixed 16 MiB array in the library's device image, present on
  * every GPU that loads libtc until the process exits.  Every call shares it,
  * so calls that overlap on the GPU (other streams, other host threads) race:
  * the caller must order them.  Each call clears the part that must start at
  * zero.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Device-side errors (coincident charges,
- * non-finite values, charges outside the disk) make *energy NaN; they are not
- * recorded in the status word that tc_sync_status() reads. */
+ * (cudaGetSymbolAddress) with that device current.  Device-side errors
+ * (coincident charges, non-finite values, charges outside the disk, n = 1
+ * included) make *energy NaN; they are not recorded in the status word that
+ * tc_sync_status() reads. */
 tc_status tc_energy_noalloc(const double* pos, int64_t n, tc_precision prec, double* energy,
                             double* local_e, tc_stream stream);
 

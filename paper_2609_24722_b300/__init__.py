@@ -255,13 +255,14 @@ def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, peri
           kappa: float = -1.0, p_defect: float = 0.8, wall_tol: float = 1e-9, sigma0: float = 1.0, sigma1: float = 1.0,
           local_precision="mixed", precision="mixed", optimizer="bb", n_steps=200, memory=8, step0=1e-9,
           alpha_min=0.0, alpha_max=1e-8, maxstep=1e-3, gtol=0.0, polish_steps=0, polish_gtol=0.0,
-          want_energy=False, profile=False, line_search=0, disjoint=False):
+          want_energy=False, profile=False, line_search=0, disjoint=False, ramp_first=0, ramp_total=0):
     """One optimisation cycle (Sec. II C) of uniforms.shape[0] subdomains in batches, in place on pos.
 
     flags (uint8, nullable): pinned boundary charges; sigma0 -> sigma1: interior radius ramp (sigma0 <= 0:
     Eq. sigma).  disjoint=True: each batch is the longest prefix of pairwise disjoint zones among the next
-    `batch` subdomains.  Returns (RelaxResult per subdomain, energy trace: E before each batch and after
-    the last)."""
+    `batch` subdomains.  ramp_first / ramp_total: this call is subdomains ramp_first .. of a cycle of
+    ramp_total (the sigma ramp spans the whole cycle; 0 = this call alone).  Returns (RelaxResult per
+    subdomain, energy trace: E before each batch and after the last)."""
     _pos(pos)
     _vec(uniforms, torch.float64, "uniforms")
     if flags is not None:
@@ -276,6 +277,8 @@ def cycle(pos, uniforms, flags=None, *, batch: int, m_min: int, m_max: int, peri
     prm.sigma0 = float(sigma0)
     prm.sigma1 = float(sigma1)
     prm.disjoint = int(bool(disjoint))
+    prm.ramp_first = int(ramp_first)
+    prm.ramp_total = int(ramp_total)
     n_batches = (n_sub if disjoint else -(-n_sub // max(int(batch), 1))) if n_sub else 0
     raw = torch.empty((max(n_sub, 1), 4), dtype=torch.float64, device=pos.device)
     trace = torch.full((n_batches + 1,), float("nan"), dtype=torch.float64, device=pos.device)

@@ -100,6 +100,8 @@ class CycleParams(C.Structure):
         ("sigma0", C.c_double),
         ("sigma1", C.c_double),
         ("disjoint", C.c_int32),
+        ("ramp_first", C.c_int32),
+        ("ramp_total", C.c_int32),
     ]
 
 

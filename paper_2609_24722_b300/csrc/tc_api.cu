@@ -5,6 +5,7 @@
 #include <string>
 #include <tuple>
 #include <utility>
+#include <vector>
 
 #include "tc_plan.cuh"
 
@@ -26,7 +27,100 @@ std::map<int, cudaStream_t> g_cap;
 
 thread_local std::string g_last_error;
 
+constexpr size_t kExecCacheMax = 8;  // executable graphs kept per device
+
+// An executable graph and the signature of the graph it was made from: per
+// node its type and, for a kernel node, the kernel, grid and block.  Only an
+// executable graph with the same signature is updated in place, so an update
+// changes kernel arguments and nothing else.
+struct CachedExec {
+    cudaGraphExec_t exec;
+    std::vector<uintptr_t> sig;
+};
+std::mutex g_exec_mu;
+std::map<int, std::vector<CachedExec>> g_exec;  // most recently returned last
+thread_local std::vector<uintptr_t> g_taken_sig;  // signature of the graph last handed out on this thread
+
+bool graph_signature(cudaGraph_t g, std::vector<uintptr_t>& sig)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return false;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return false;
+    sig.clear();
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(node, &t) != cudaSuccess) return false;
+        sig.push_back((uintptr_t)t);
+        if (t == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) return false;
+            sig.push_back((uintptr_t)kp.func);
+            sig.push_back(((uintptr_t)kp.gridDim.x << 32) | ((uintptr_t)kp.gridDim.y << 16) | kp.gridDim.z);
+            sig.push_back(((uintptr_t)kp.blockDim.x << 32) | ((uintptr_t)kp.blockDim.y << 16) | kp.blockDim.z);
+        }
+    }
+    return true;
+}
+
 }  // namespace
+
+cudaGraphExec_t take_graph_exec(cudaGraph_t graph, cudaError_t* e)
+{
+    int dev = 0;
+    if ((*e = cudaGetDevice(&dev)) != cudaSuccess) return nullptr;
+    g_taken_sig.clear();
+    if (graph_signature(graph, g_taken_sig)) {
+        std::lock_guard<std::mutex> lk(g_exec_mu);
+        auto& v = g_exec[dev];
+        for (size_t i = v.size(); i-- > 0;) {
+            if (v[i].sig != g_taken_sig) continue;
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(v[i].exec, graph, &info) == cudaSuccess) {
+                cudaGraphExec_t x = v[i].exec;
+                v.erase(v.begin() + (std::ptrdiff_t)i);
+                return x;
+            }
+            cudaGetLastError();  // refused: instantiate below
+        }
+    } else {
+        cudaGetLastError();
+        g_taken_sig.clear();
+    }
+    cudaGraphExec_t x = nullptr;
+    *e = cudaGraphInstantiate(&x, graph, 0);
+    return *e == cudaSuccess ? x : nullptr;
+}
+
+void give_graph_exec(cudaGraphExec_t exec)
+{
+    if (!exec) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || g_taken_sig.empty()) {
+        cudaGraphExecDestroy(exec);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_exec_mu);
+    auto& v = g_exec[dev];
+    v.push_back(CachedExec{exec, g_taken_sig});
+    if (v.size() > kExecCacheMax) {
+        cudaGraphExecDestroy(v.front().exec);
+        v.erase(v.begin());
+    }
+}
+
+void release_graph_execs()
+{
+    std::lock_guard<std::mutex> lk(g_exec_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : g_exec) {
+        cudaSetDevice(kv.first);
+        for (const CachedExec& x : kv.second) cudaGraphExecDestroy(x.exec);
+    }
+    g_exec.clear();
+    cudaSetDevice(cur);
+}
 
 tc_status cuda_fail(cudaError_t e, const char* where)
 {
@@ -205,6 +299,7 @@ void tc_shutdown(void)
     }
     tc::g_cap.clear();
     cudaSetDevice(cur);
+    tc::release_graph_execs();
 }
 
 }  // extern "C"

@@ -14,7 +14,7 @@
 #include "tc_plan.cuh"
 
 static_assert(sizeof(tc_zone_params) == 48, "tc_zone_params layout");
-static_assert(sizeof(tc_cycle_params) == 176, "tc_cycle_params layout");
+static_assert(sizeof(tc_cycle_params) == 184, "tc_cycle_params layout");
 
 namespace tc {
 
@@ -446,7 +446,17 @@ tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_
         misaligned(out, 8))
         return TC_ERR_INVALID_ARG;
     const int32_t B = std::min(prm->batch, n_sub);
-    const int64_t n_batches = (n_sub + B - 1) / B;
+    // the sigma ramp runs over the whole cycle: subdomains ramp_first .. of ramp_total
+    const int64_t total = prm->ramp_total > 0 ? prm->ramp_total : n_sub;
+    const int64_t first = prm->ramp_total > 0 ? prm->ramp_first : 0;
+    if (first < 0 || first + n_sub > total || (prm->disjoint == 0 && first % prm->batch != 0)) {
+        set_last_error("tc_cycle: need 0 <= ramp_first, ramp_first + n_sub <= ramp_total, and (fixed batches) "
+                       "ramp_first a multiple of batch");
+        return TC_ERR_INVALID_ARG;
+    }
+    const int32_t Bt = std::min<int64_t>(prm->batch, total);
+    const int64_t n_batches = (total + Bt - 1) / Bt;  // of the whole cycle (fixed batches)
+    const int64_t b_first = first / Bt;
     if (prm->disjoint != 0 && prm->disjoint != 1) {
         set_last_error("tc_cycle: disjoint must be 0 or 1");
         return TC_ERR_INVALID_ARG;
@@ -489,9 +499,10 @@ tc_status tc_cycle(double* pos, int64_t n, const uint8_t* flags, const tc_cycle_
         double sigma;
         if (!disjoint)
             sigma = n_batches <= 1 ? prm->sigma1
-                                   : sigma0 + (prm->sigma1 - sigma0) * (double)b / (double)(n_batches - 1);
+                                   : sigma0 + (prm->sigma1 - sigma0) * (double)(b_first + b) / (double)(n_batches - 1);
         else
-            sigma = n_sub <= 1 ? prm->sigma1 : sigma0 + (prm->sigma1 - sigma0) * (double)b0 / (double)(n_sub - 1);
+            sigma = total <= 1 ? prm->sigma1
+                               : sigma0 + (prm->sigma1 - sigma0) * (double)(first + b0) / (double)(total - 1);
         rp.radius = sigma;
         err = allpairs(pos, n, lp, nullptr, energy ? energy + b : e_tot, e_loc, s);
         if (err != TC_OK) return err;

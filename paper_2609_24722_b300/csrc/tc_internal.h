@@ -24,6 +24,17 @@ int* device_status(tc_status* err);
 // (the legacy default stream cannot be captured).
 cudaStream_t capture_stream(tc_status* err);
 
+// Executable step-loop graphs kept across calls, per device.  take_graph_exec
+// returns an executable graph for `graph`: a cached one updated in place with
+// cudaGraphExecUpdate when one has the same shape (only kernel arguments
+// differ), else a new instantiation (nullptr and *e set on failure).  The
+// caller owns it until give_graph_exec returns it to the cache (the cache
+// keeps a few per device and destroys the rest).  release_graph_execs
+// destroys every cached one (tc_shutdown).
+cudaGraphExec_t take_graph_exec(cudaGraph_t graph, cudaError_t* e);
+void give_graph_exec(cudaGraphExec_t exec);
+void release_graph_execs();
+
 // SM count and current device.
 int sm_count();
 

@@ -108,36 +108,62 @@ __device__ void block_argmin(double& t, int& r, double* sht, int* shr)
     __syncthreads();
 }
 
+// Row of the largest |a[r * ld + col]| over rows col .. kBQ-1, the first such
+// row on ties (as a search that keeps the first maximum), or -1 if that value
+// is 0; computed by warp 0 and returned to every thread.
+__device__ int block_pivot(const double* a, int ld, int col, int* sh_piv)
+{
+    if (threadIdx.x < 32) {
+        const int r0 = threadIdx.x;
+        double v = (r0 >= col && r0 < kBQ) ? fabs(a[r0 * ld + col]) : -1.0;
+        int r = r0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+            if (v2 > v || (v2 == v && r2 < r)) {
+                v = v2;
+                r = r2;
+            }
+        }
+        if (threadIdx.x == 0) *sh_piv = v > 0.0 ? r : -1;
+    }
+    __syncthreads();
+    const int piv = *sh_piv;
+    __syncthreads();
+    return piv;
+}
+
 // [K | I] -> [I | K^{-1}] by Gauss-Jordan elimination with partial pivoting,
-// on warp 0 with one of the 2 kBQ = 32 columns per lane.  False if a pivot is 0.
-__device__ bool warp_gauss_jordan(double* aug)
+// the whole CTA taking part (two of the 16 x 32 entries per thread).  Every
+// entry sees the same operations in the same order as a one-lane-per-column
+// elimination.  False (for every thread) if a pivot is 0.
+__device__ bool block_gauss_jordan(double* aug, double* fcol, int* sh_piv)
 {
     constexpr int ld = 2 * kBQ;
-    static_assert(ld == 32, "one column per lane");
-    const int lane = threadIdx.x & 31;
+    static_assert(ld == 32 && kBQ * ld == 2 * kUpd, "two entries per thread");
+    const int t = threadIdx.x;
     for (int col = 0; col < kBQ; ++col) {
-        int piv = col;
-        for (int r = col + 1; r < kBQ; ++r)
-            if (fabs(aug[r * ld + col]) > fabs(aug[piv * ld + col])) piv = r;
-        if (!(fabs(aug[piv * ld + col]) > 0.0)) return false;
-        __syncwarp();
-        if (piv != col) {
-            const double t = aug[col * ld + lane];
-            aug[col * ld + lane] = aug[piv * ld + lane];
-            aug[piv * ld + lane] = t;
-        }
-        __syncwarp();
-        const double pv = aug[col * ld + col];
-        __syncwarp();
-        aug[col * ld + lane] = __ddiv_rn(aug[col * ld + lane], pv);
-        __syncwarp();
-        for (int r = 0; r < kBQ; ++r) {
-            if (r == col) continue;
-            const double f = aug[r * ld + col];
+        const int piv = block_pivot(aug, ld, col, sh_piv);
+        if (piv < 0) return false;
+        if (t < ld) {
+            // swap rows col and piv, then divide the pivot row by the pivot
+            const double pv = aug[piv * ld + col];
+            const double a = aug[col * ld + t], b = aug[piv * ld + t];
             __syncwarp();
-            if (f != 0.0) aug[r * ld + lane] = __dsub_rn(aug[r * ld + lane], __dmul_rn(f, aug[col * ld + lane]));
-            __syncwarp();
+            if (piv != col) aug[piv * ld + t] = a;
+            aug[col * ld + t] = __ddiv_rn(b, pv);
         }
+        __syncthreads();
+        if (t < kBQ) fcol[t] = aug[t * ld + col];
+        __syncthreads();
+#pragma unroll
+        for (int e = t; e < kBQ * ld; e += kUpd) {
+            const int r = e / ld, c = e % ld;
+            const double f = fcol[r];
+            if (r != col && f != 0.0) aug[e] = __dsub_rn(aug[e], __dmul_rn(f, aug[col * ld + c]));
+        }
+        __syncthreads();
     }
     return true;
 }
@@ -185,6 +211,100 @@ __device__ __forceinline__ double lanes_sum16(double v)
     return v;
 }
 
+// ---- one problem stepped by a cluster of CL CTAs ----
+// The rows of a problem are dealt to the CTAs in blocks of kUpd (CTA r takes
+// rows r kUpd .. r kUpd + kUpd - 1, then (r + CL) kUpd .., and so on).  A
+// reduction first reduces within each CTA (every thread gets the CTA's totals),
+// then each CTA posts its totals in its own shared memory, the cluster waits
+// at its barrier, and every CTA adds the CL posts in rank order: all CTAs hold
+// the same totals, bit for bit, and repeat the small dense algebra on them.
+// Posts alternate between two buffers; a CTA writes a buffer again only two
+// reductions later, after a barrier that every other CTA reaches only once it
+// has read that buffer.  With CL = 1 the cluster steps drop out.
+#define TC_CROWS(p) for (int64_t rl = (int64_t)crank * kUpd + threadIdx.x; rl < (p).m; rl += (int64_t)CL * kUpd)
+
+struct ClRed {
+    double* post;  // shared [2][kRed]
+    int phase;
+};
+
+template <int CL> __device__ __forceinline__ void cl_barrier()
+{
+    if constexpr (CL > 1) cg::this_cluster().sync();
+}
+
+// Sums of N doubles over the problem's rows (block_sums_w, then the cluster).
+template <int CL, int N> __device__ void cl_sums(double (&v)[N], double (*red)[kRed], ClRed& cr)
+{
+    block_sums_w<N>(v, red);
+    if constexpr (CL > 1) {
+        auto cl = cg::this_cluster();
+        double* mine = cr.post + cr.phase * kRed;
+        if (threadIdx.x < N) mine[threadIdx.x] = red[0][threadIdx.x];  // the CTA's totals
+        cl.sync();
+        if (threadIdx.x < N) {
+            double t = 0.0;
+            for (int r = 0; r < CL; ++r) t += cl.map_shared_rank(mine, r)[threadIdx.x];
+            red[0][threadIdx.x] = t;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = red[0][i];
+        __syncthreads();
+        cr.phase ^= 1;
+    }
+}
+
+// Maximum (take_max) or minimum of a value every thread holds as its CTA's result.
+template <int CL> __device__ double cl_fold(double x, bool take_max, ClRed& cr)
+{
+    if constexpr (CL > 1) {
+        auto cl = cg::this_cluster();
+        double* mine = cr.post + cr.phase * kRed;
+        if (threadIdx.x == 0) mine[0] = x;
+        cl.sync();
+        x = cl.map_shared_rank(mine, 0)[0];
+        for (int r = 1; r < CL; ++r) {
+            const double y = cl.map_shared_rank(mine, r)[0];
+            x = take_max ? fmax(x, y) : fmin(x, y);
+        }
+        cr.phase ^= 1;
+    }
+    return x;
+}
+
+// Some thread of the problem's CTAs has flag set.
+template <int CL> __device__ bool cl_any(int flag, ClRed& cr)
+{
+    const int b = __syncthreads_or(flag);
+    return cl_fold<CL>(b ? 1.0 : 0.0, true, cr) > 0.0;
+}
+
+// Smallest (t, row) over the problem's rows, ties to the lower row.
+template <int CL> __device__ void cl_argmin(double& t, int& r, double* sht, int* shr, ClRed& cr)
+{
+    block_argmin(t, r, sht, shr);
+    if constexpr (CL > 1) {
+        auto cl = cg::this_cluster();
+        double* mine = cr.post + cr.phase * kRed;
+        if (threadIdx.x == 0) {
+            mine[0] = t;
+            mine[1] = (double)r;
+        }
+        cl.sync();
+        for (int q = 0; q < CL; ++q) {
+            const double* o = cl.map_shared_rank(mine, q);
+            const double t2 = o[0];
+            const int r2 = (int)o[1];
+            if (t2 < t || (t2 == t && r2 < r)) {
+                t = t2;
+                r = r2;
+            }
+        }
+        cr.phase ^= 1;
+    }
+}
+
 // Entries [C0, C0 + NC) of the upper triangle (row-major) of w w^T.
 template <int C0, int NC> __device__ __forceinline__ void gram_add(const double (&w)[kBQ], double (&acc)[NC])
 {
@@ -211,13 +331,14 @@ template <int C0, int NC> __device__ __forceinline__ void gram_store(const doubl
 // One chunk of W'^T W' over the variables at a bound in xc whose W' row is not
 // zero: the t of a free charge at 0 or pi/2 (a pinned charge's fixed second
 // variable has y = s = 0).
-template <int C0, int NC>
-__device__ void gram_chunk(const RelaxDev& d, const Prob& p, const int* slot, int hb, double* A, double (*red)[kRed])
+template <int CL, int C0, int NC>
+__device__ void gram_chunk(const RelaxDev& d, const Prob& p, const int* slot, int hb, double* A, double (*red)[kRed],
+                           ClRed& cr, int crank)
 {
     double acc[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) acc[i] = 0.0;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
@@ -229,10 +350,11 @@ __device__ void gram_chunk(const RelaxDev& d, const Prob& p, const int* slot, in
         w_rows(d, row, slot, hb, wx, wy);
         gram_add<C0, NC>(wx, acc);
     }
-    block_sums_w<NC>(acc, red);
+    cl_sums<CL, NC>(acc, red, cr);
     if (threadIdx.x == 0) gram_store<C0, NC>(acc, A);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
                                                          StepParams sp)
 {
@@ -247,21 +369,29 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     __shared__ int slot[kBMem], oth[kBMem];
     __shared__ double bc[4];                // told, dtm, fp, fpp of the Cauchy search
     __shared__ int bflag[2];
-    const int s = blockIdx.x;
+    __shared__ double post[2 * kRed];       // this CTA's posts to the cluster's reductions
+    __shared__ double bs[kBSmall];          // this CTA's copy of the problem's small products
+    const int s = blockIdx.x / CL;
+    int crank = 0;
+    if constexpr (CL > 1) crank = (int)cg::this_cluster().block_rank();
+    const bool lead = crank == 0;          // the CTA that writes the problem's scalars
+    ClRed cr{post, 0};
     if (!d.active[s]) return;
     const Prob p = d.prob[s];
     const int k = d.steps[s];
     const int mem = sp.memory;
     const int64_t M = d.M;
-    double* sy_t = d.bsmall + (int64_t)s * kBSmall;  // [slot a][slot b] = s_a . y_b
-    double* ss_t = sy_t + kBMem * kBMem;              // s_a . s_b
-    double* yy_t = ss_t + kBMem * kBMem;              // y_a . y_b
-    double* theta_t = yy_t + kBMem * kBMem;           // y.y / s.y of the newest pair
+    for (int e = threadIdx.x; e < kBSmall; e += kUpd) bs[e] = d.bsmall[(int64_t)s * kBSmall + e];
+    __syncthreads();
+    double* sy_t = bs;                     // [slot a][slot b] = s_a . y_b
+    double* ss_t = sy_t + kBMem * kBMem;   // s_a . s_b
+    double* yy_t = ss_t + kBMem * kBMem;   // y_a . y_b
+    double* theta_t = yy_t + kBMem * kBMem;  // y.y / s.y of the newest pair
 
     // 1. dE/d(t, u) of the new point into q, pair statistics, projected-gradient RMS
     double acc[4] = {0.0, 0.0, 0.0, 0.0};  // |P(z - g) - z|^2, s.y, s.s, y.y
     bool bad = false;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const double2 g = sum_g(p, rl, part_g, v);
@@ -283,10 +413,11 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         }
     }
     if (bad) set_status(d.st, ST_NONFINITE);
-    block_sums(acc, sh);
+    cl_sums<CL, 4>(acc, red, cr);
     const double rms = sqrt(acc[0] / (double)max(p.m, 1));
     if (sp.measure) {
-        if (threadIdx.x == 0) d.rms[s] = rms;
+        if (lead && threadIdx.x == 0) d.rms[s] = rms;
+        cl_barrier<CL>();  // no CTA leaves while another may still read its posts
         return;
     }
     int hist = d.hist[s], head = d.head[s];
@@ -306,7 +437,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         double dots[4 * (kBMem - 1)];
 #pragma unroll
         for (int i = 0; i < 4 * (kBMem - 1); ++i) dots[i] = 0.0;
-        TC_ROWS(p)
+        TC_CROWS(p)
         {
             const int64_t row = p.row_base + rl;
             const double2 z = d.z[row], zo = d.xp[row], gz = d.q[row], go = d.gp[row];
@@ -325,7 +456,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
             d.Yh[(int64_t)head * M + row] = yn;
             d.gp[row] = gz;
         }
-        block_sums_w<4 * (kBMem - 1)>(dots, red);
+        cl_sums<CL, 4 * (kBMem - 1)>(dots, red, cr);
         if (threadIdx.x == 0) {
             for (int o = 0; o < kBMem - 1; ++o) {
                 const int j = oth[o];
@@ -340,18 +471,22 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
             yy_t[head * kBMem + head] = acc[3];
             *theta_t = acc[3] / acc[1];
         }
+        __syncthreads();
+        if (lead)
+            for (int e = threadIdx.x; e < kBSmall; e += kUpd) d.bsmall[(int64_t)s * kBSmall + e] = bs[e];
         head = (head + 1) % mem;
         hist = min(hist + 1, mem);
     } else {
-        TC_ROWS(p) d.gp[p.row_base + rl] = d.q[p.row_base + rl];
+        TC_CROWS(p) d.gp[p.row_base + rl] = d.q[p.row_base + rl];
     }
     if (sp.gtol > 0.0 && rms < sp.gtol) {
-        if (threadIdx.x == 0) {
+        if (lead && threadIdx.x == 0) {
             d.active[s] = 0;
             d.rms[s] = rms;
             d.hist[s] = hist;
             d.head[s] = head;
         }
+        cl_barrier<CL>();
         return;
     }
     __syncthreads();
@@ -383,14 +518,15 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         aug[a * 2 * kBQ + kBQ + b] = a == b ? 1.0 : 0.0;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const bool ok = warp_gauss_jordan(aug);
+    {
+        const bool ok = block_gauss_jordan(aug, pv, shi);  // pv, shi: scratch until the Cauchy search
         if (threadIdx.x == 0) bflag[0] = ok ? 1 : 0;
     }
     __syncthreads();
     if (!bflag[0]) {
         set_status(d.st, ST_NONFINITE);
-        if (threadIdx.x == 0) d.active[s] = 0;
+        if (lead && threadIdx.x == 0) d.active[s] = 0;
+        cl_barrier<CL>();
         return;
     }
     for (int e = threadIdx.x; e < kBQ * kBQ; e += kUpd) Mm[e] = aug[(e / kBQ) * 2 * kBQ + kBQ + e % kBQ];
@@ -400,7 +536,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     double pd[kBQ + 1];
 #pragma unroll
     for (int i = 0; i <= kBQ; ++i) pd[i] = 0.0;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
@@ -417,7 +553,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         for (int a = 0; a < kBQ; ++a) pd[a] += wx[a] * dv.x + wy[a] * dv.y;
         pd[kBQ] += dv.x * dv.x + dv.y * dv.y;
     }
-    block_sums_w<kBQ + 1>(pd, red);
+    cl_sums<CL, kBQ + 1>(pd, red, cr);
     // The small dense algebra runs on warp 0, one lane per entry: a float64
     // instruction of one thread takes the SM's float64 pipe as long as a warp's.
     const int lane = threadIdx.x & 31;
@@ -448,7 +584,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     // breakpoint just fixed was one of them
     double own_t = INFINITY;
     int own_r = INT_MAX;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const double t = d.bp[p.row_base + rl];
         if (t > 0.0 && t < own_t) {
@@ -459,41 +595,62 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     while (bflag[1]) {
         double tmin = own_t;
         int rmin = own_r;
-        block_argmin(tmin, rmin, sh, shi);
-        if (threadIdx.x < 32) {
-            const double told = bc[0], dtm = bc[1];
-            const double dt = tmin - told;
-            if (rmin == INT_MAX || dtm < dt) {
-                if (lane == 0) bflag[1] = 0;
-            } else {
-                const int64_t b = p.row_base + rmin;
-                const double gb = d.gp[b].x;
-                double wa = 0.0;  // entry `lane` of w_b (row b of W, variable t)
-                if (lane < kBQ) {
-                    const int ia = lane < kBMem ? lane : lane - kBMem;
-                    if (ia < hb) {
-                        const int64_t o = (int64_t)slot[ia] * M + b;
-                        wa = lane < kBMem ? d.Yh[o].x : theta * d.Sh[o].x;
-                    }
-                    wbs[lane] = wa;
-                    cv[lane] += dt * pv[lane];
-                }
-                __syncwarp();
-                double mcl = 0.0, mpl = 0.0, mwl = 0.0;
-                if (lane < kBQ) {
-                    mcl = row_dot16(Mm, cv, lane);
-                    mpl = row_dot16(Mm, pv, lane);
-                    mwl = row_dot16(Mm, wbs, lane);
-                }
-                const double wMc = lanes_sum16(wa * mcl), wMp = lanes_sum16(wa * mpl), wMw = lanes_sum16(wa * mwl);
-                __syncwarp();
-                if (lane < kBQ) pv[lane] += gb * wa;
-                if (lane == 0) {
+        cl_argmin<CL>(tmin, rmin, sh, shi, cr);
+        // every CTA holds the same (tmin, rmin) and bc, so all take the same branch
+        const double told = bc[0], dtm = bc[1];
+        const double dt = tmin - told;
+        if (rmin == INT_MAX || dtm < dt) {
+            __syncthreads();
+            if (threadIdx.x == 0) bflag[1] = 0;
+            __syncthreads();
+            break;
+        }
+        const int64_t b = p.row_base + rmin;
+        const int orank = (rmin / kUpd) % CL;  // the CTA that holds row b
+        // the row's own CTA posts what the search needs of row b: g, the bound it reaches, z, and
+        // its row of W' (unscaled); the others read the post after the cluster barrier
+        double* bpost = cr.post + cr.phase * kRed;
+        if (orank == crank && threadIdx.x < 32) {
+            if (lane == 0) {
                 const bool pinned = d.flags && d.flags[d.gidx[b]];
                 double2 lo, hi;
                 tu_bounds(pinned, lo, hi);
-                const double xb = d.q[b].x > 0.0 ? hi.x : lo.x;
-                const double zb = xb - d.z[b].x;
+                bpost[0] = d.gp[b].x;
+                bpost[1] = d.q[b].x > 0.0 ? hi.x : lo.x;
+                bpost[2] = d.z[b].x;
+            }
+            if (lane < kBQ) {
+                const int ia = lane < kBMem ? lane : lane - kBMem;
+                double w = 0.0;
+                if (ia < hb) {
+                    const int64_t o = (int64_t)slot[ia] * M + b;
+                    w = lane < kBMem ? d.Yh[o].x : d.Sh[o].x;
+                }
+                bpost[3 + lane] = w;
+            }
+        }
+        if constexpr (CL > 1) cg::this_cluster().sync(); else __syncthreads();
+        const double* opost = bpost;
+        if constexpr (CL > 1) opost = cg::this_cluster().map_shared_rank(bpost, orank);
+        if (threadIdx.x < 32) {
+            const double gb = opost[0], xb = opost[1], zb = xb - opost[2];
+            double wa = 0.0;  // entry `lane` of w_b (row b of W, variable t)
+            if (lane < kBQ) {
+                wa = lane < kBMem ? opost[3 + lane] : theta * opost[3 + lane];
+                wbs[lane] = wa;
+                cv[lane] += dt * pv[lane];
+            }
+            __syncwarp();
+            double mcl = 0.0, mpl = 0.0, mwl = 0.0;
+            if (lane < kBQ) {
+                mcl = row_dot16(Mm, cv, lane);
+                mpl = row_dot16(Mm, pv, lane);
+                mwl = row_dot16(Mm, wbs, lane);
+            }
+            const double wMc = lanes_sum16(wa * mcl), wMp = lanes_sum16(wa * mpl), wMw = lanes_sum16(wa * mwl);
+            __syncwarp();
+            if (lane < kBQ) pv[lane] += gb * wa;
+            if (lane == 0) {
                 double fp = bc[2], fpp = bc[3];
                 fp = __dsub_rn(__dadd_rn(__dadd_rn(__dadd_rn(fp, __dmul_rn(dt, fpp)), __dmul_rn(gb, gb)),
                                          __dmul_rn(__dmul_rn(theta, gb), zb)),
@@ -502,24 +659,26 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
                                           __dmul_rn(__dmul_rn(2.0, gb), wMp)),
                                 __dmul_rn(__dmul_rn(gb, gb), wMw));
                 if (fpp < 0x1p-52 * fpp0) fpp = 0x1p-52 * fpp0;
-                d.q[b] = make_double2(0.0, d.q[b].y);
-                d.bp[b] = -1.0;  // fixed at its bound
-                reinterpret_cast<double*>(d.xc + b)[0] = xb;
+                if (orank == crank) {  // only the row's own CTA writes it
+                    d.bp[b] = -1.0;    // fixed at its bound
+                    reinterpret_cast<double*>(d.xc + b)[0] = xb;
+                }
                 bc[0] = tmin;
                 bc[1] = -fp / fpp;
                 bc[2] = fp;
                 bc[3] = fpp;
-                }
             }
         }
+        cr.phase ^= 1;
         __syncthreads();
-        if (bflag[1] && rmin != INT_MAX) {
+        if (orank == crank) {
             // the owner's warp rescans the owner's rows, 32 at a time
             const int owner = rmin % kUpd;
             if ((int)(threadIdx.x >> 5) == (owner >> 5)) {
                 double tb = INFINITY;
                 int rb_ = INT_MAX;
-                for (int64_t rl = owner + (int64_t)lane * kUpd; rl < p.m; rl += 32LL * kUpd) {
+                for (int64_t rl = owner + (int64_t)kUpd * (crank + (int64_t)CL * lane); rl < p.m;
+                     rl += 32LL * CL * kUpd) {
                     const double t = d.bp[p.row_base + rl];
                     if (t > 0.0 && t < tb) {
                         tb = t;
@@ -543,7 +702,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     __syncthreads();
     {
         const double told = bc[0];
-        TC_ROWS(p)
+        TC_CROWS(p)
         {
             const int64_t row = p.row_base + rl;
             const double2 z = d.z[row], dv = d.q[row];
@@ -562,7 +721,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
 #pragma unroll
     for (int a = 0; a < kBQ; ++a) wr[a] = 0.0;
     int bound_rows = 0;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
@@ -579,7 +738,7 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
 #pragma unroll
         for (int a = 0; a < kBQ; ++a) wr[a] += wx[a] * rx + wy[a] * ry;
     }
-    block_sums_w<kBQ>(wr, red);
+    cl_sums<CL, kBQ>(wr, red, cr);
     // W'^T W' over every variable, from the kept products (into aug, free after the inversion)
     for (int e = threadIdx.x; e < kBQ * kBQ; e += kUpd) {
         const int a = e / kBQ, b = e % kBQ;
@@ -600,11 +759,11 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         aug[e] = val;
     }
     // less the rows at a bound
-    if (__syncthreads_or(bound_rows)) {
-        gram_chunk<0, 34>(d, p, slot, hb, A, red);
-        gram_chunk<34, 34>(d, p, slot, hb, A, red);
-        gram_chunk<68, 34>(d, p, slot, hb, A, red);
-        gram_chunk<102, 34>(d, p, slot, hb, A, red);
+    if (cl_any<CL>(bound_rows, cr)) {
+        gram_chunk<CL, 0, 34>(d, p, slot, hb, A, red, cr, crank);
+        gram_chunk<CL, 34, 34>(d, p, slot, hb, A, red, cr, crank);
+        gram_chunk<CL, 68, 34>(d, p, slot, hb, A, red, cr, crank);
+        gram_chunk<CL, 102, 34>(d, p, slot, hb, A, red, cr, crank);
     } else if (threadIdx.x == 0) {
         for (int e = 0; e < kBQ * kBQ; ++e) A[e] = 0.0;
     }
@@ -634,32 +793,33 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         if (e < kBQ) Nv[e * ld + kBQ] = row_dot16(Mm, wrs, e);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        // Gauss elimination with partial pivoting on [N | v], one of the kBQ + 1 columns per lane
-        bool ok = true;
-        for (int col = 0; col < kBQ; ++col) {
-            int piv = col;
-            for (int r = col + 1; r < kBQ; ++r)
-                if (fabs(Nv[r * ld + col]) > fabs(Nv[piv * ld + col])) piv = r;
-            if (!(fabs(Nv[piv * ld + col]) > 0.0)) {
-                ok = false;
-                break;
-            }
-            __syncwarp();
-            if (piv != col && lane <= kBQ) {
-                const double t = Nv[col * ld + lane];
-                Nv[col * ld + lane] = Nv[piv * ld + lane];
-                Nv[piv * ld + lane] = t;
-            }
-            __syncwarp();
-            for (int r = col + 1; r < kBQ; ++r) {
-                const double f = __ddiv_rn(Nv[r * ld + col], Nv[col * ld + col]);
-                __syncwarp();
-                if (lane >= col && lane <= kBQ)
-                    Nv[r * ld + lane] = __dsub_rn(Nv[r * ld + lane], __dmul_rn(f, Nv[col * ld + lane]));
-                __syncwarp();
-            }
+    // Gauss elimination with partial pivoting on [N | v], the whole CTA taking part; every entry
+    // sees the same operations in the same order as a one-lane-per-column elimination
+    bool ok = true;
+    for (int col = 0; col < kBQ; ++col) {
+        const int piv = block_pivot(Nv, ld, col, shi);
+        if (piv < 0) {
+            ok = false;
+            break;
         }
+        if (piv != col && threadIdx.x <= kBQ) {
+            const double a = Nv[col * ld + threadIdx.x], b = Nv[piv * ld + threadIdx.x];
+            __syncwarp(0x1ffffu);  // threads 0 .. kBQ
+            Nv[col * ld + threadIdx.x] = b;
+            Nv[piv * ld + threadIdx.x] = a;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x > col && threadIdx.x < kBQ)
+            pv[threadIdx.x] = __ddiv_rn(Nv[threadIdx.x * ld + col], Nv[col * ld + col]);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kBQ * ld; e += kUpd) {
+            const int r = e / ld, c = e % ld;
+            if (r > col && c >= col) Nv[e] = __dsub_rn(Nv[e], __dmul_rn(pv[r], Nv[col * ld + c]));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         if (ok)
             for (int a = kBQ - 1; a >= 0; --a) {
                 // v_a = (rhs_a - sum_{q > a} N_aq v_q) / N_aa, the products on lanes a+1 .. kBQ-1
@@ -673,12 +833,13 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     __syncthreads();
     if (!bflag[0]) {
         set_status(d.st, ST_NONFINITE);
-        if (threadIdx.x == 0) d.active[s] = 0;
+        if (lead && threadIdx.x == 0) d.active[s] = 0;
+        cl_barrier<CL>();
         return;
     }
     double amin = 1.0;
     const double ith = 1.0 / theta, ith2 = ith * ith;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
@@ -702,12 +863,13 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         if (threadIdx.x < w) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + w]);
         __syncthreads();
     }
-    const double astar = sh[0];
+    double astar = sh[0];
     __syncthreads();
+    astar = cl_fold<CL>(astar, false, cr);
 
     // 6. direction xbar - z, descent check, capped step
     double gd[1] = {0.0};
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
@@ -720,14 +882,14 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         d.q[row] = dv;
         gd[0] += gz.x * dv.x + gz.y * dv.y;
     }
-    block_sums(gd, sh);
+    cl_sums<CL, 1>(gd, red, cr);
     const bool reset = gd[0] >= 0.0;
     if (reset) {
         hist = 0;
         head = 0;
     }
     double dmax = 0.0;
-    TC_ROWS(p)
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         double2 dv = d.q[row];
@@ -742,10 +904,10 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         }
         dmax = fmax(dmax, sqrt(dv.x * dv.x + dv.y * dv.y));
     }
-    dmax = block_max(dmax, sh);
+    dmax = cl_fold<CL>(block_max(dmax, sh), true, cr);
     const double alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
-    if (threadIdx.x == 0 && d.ls_alpha) d.ls_alpha[s] = alpha;
-    TC_ROWS(p)
+    if (lead && threadIdx.x == 0 && d.ls_alpha) d.ls_alpha[s] = alpha;
+    TC_CROWS(p)
     {
         const int64_t row = p.row_base + rl;
         const bool pinned = d.flags && d.flags[d.gidx[row]];
@@ -761,10 +923,11 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
         d.xs[row] = split4(xn.x, xn.y);
         if (d.x3) d.x3[row] = split3(xn.x, xn.y);
     }
-    if (threadIdx.x == 0) {
+    if (lead && threadIdx.x == 0) {
         d.steps[s] = k + 1;
         d.rms[s] = rms;
         d.hist[s] = hist;
         d.head[s] = head;
     }
+    cl_barrier<CL>();
 }

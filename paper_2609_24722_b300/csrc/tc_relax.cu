@@ -14,9 +14,13 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "tc_plan.cuh"
 
 namespace tc {
+
+namespace cg = cooperative_groups;
 
 constexpr int kUpd = 256;   // update / reduction CTA size
 constexpr int kMaxMem = 16; // largest L-BFGS memory
@@ -58,7 +62,8 @@ struct RelaxDev {
     int* steps;            // per problem
     int* hist;             // per problem: L-BFGS pairs stored
     int* head;             // per problem: L-BFGS ring position
-    double* rho;           // [S][mem]
+    double* rho;           // [S][kMaxMem]: 1/(s_j.y_j) by ring slot
+    double* gram;          // [S][2][kMaxMem][kMaxMem]: s_a.y_b and y_a.y_b by ring slot (L-BFGS)
     double* rms;           // per problem
     double* delta;         // per problem
     double* energy;        // per problem
@@ -344,6 +349,280 @@ __global__ void __launch_bounds__(kUpd) k_update_gdbb(RelaxDev d, const double2*
 // Sum over the problem's rows of f(row), block-reduced (deterministic).
 #define TC_ROWS(p) for (int64_t rl = threadIdx.x; rl < (p).m; rl += kUpd)
 
+// L-BFGS of one problem with many rows (grid-wide launches, below).  The
+// iteration is the host statement's: pair test and store, stop test, two-loop
+// recursion (Nocedal & Wright, Alg. 7.4) with H0 = gamma I, descent check,
+// max-displacement scaling.  Launched over the grid, each inner product the
+// recursion takes with its running vector would be a launch of its own; here
+// the recursion is evaluated through inner products instead: each such
+// product is expanded into products of the gradient with the stored pairs
+// (s_j.g, y_j.g) and of the stored pairs with each other (s_a.y_b, y_a.y_b,
+// kept per ring slot and computed once, when the newer of the two pairs is
+// stored).  A step then needs one round of reductions over the rows (a pass
+// per four stored pairs, all independent) instead of 2 h + 2 that wait on one
+// another, and the direction is one combination
+// d = c_g g + sum_j (c_s[j] s_j + c_y[j] y_j).  The two forms agree to
+// rounding.  (One CTA per problem, k_update_lbfgs, keeps the plain two-loop
+// recursion: its reductions are cheap within a CTA, and the expanded form's
+// extra float64 products cost more there.)
+
+constexpr int kLbSlotsPerPass = 4;                              // stored pairs per dot pass
+constexpr int kLbVals = 6 + 5 * kLbSlotsPerPass;                // values reduced per pass
+constexpr int kLbPasses = (kMaxMem + kLbSlotsPerPass - 1) / kLbSlotsPerPass;
+constexpr int kLbGram = 2 * kMaxMem * kMaxMem;                  // per problem: s_a.y_b, y_a.y_b by slot
+
+__device__ __forceinline__ int lb_slot(int head, int i, int mem) { return ((head - 1 - i) % mem + mem) % mem; }
+
+// Coefficients of one step of one problem.
+struct LbCoef {
+    double cg;                         // d = cg gz + sum_j cs[j] S_j + cy[j] Y_j (j: ring slot)
+    double cs[kMaxMem], cy[kMaxMem];
+    double rms;
+    int keep, slot;                    // store the new pair in ring slot `slot`
+    int stop;                          // 1: no step (stopped, or measuring)
+    int reset;                         // descent check failed: d = -step0 gz
+    int hist, head;                    // history after this step's store
+};
+
+// The reduced inner products of one step: base[0..5] = gz.gz, s.y, s.s, y.y,
+// s.gz, y.gz of the new pair (s = z - z_prev, y = gz - gz_prev); per stored
+// pair of age i (0 the newest): S_i.gz, Y_i.gz, s.Y_i, S_i.y, y.Y_i.
+struct LbDots {
+    double base[6];
+    double sg[kMaxMem], yg[kMaxMem], sY[kMaxMem], Sy[kMaxMem], yY[kMaxMem];
+};
+
+// One row's share of dot pass `pass`.
+__device__ __forceinline__ void lb_row_dots(const RelaxDev& d, int64_t row, int pass, int k, int hist, int head,
+                                            int mem, double (&acc)[kLbVals])
+{
+    const double2 z = d.z[row], gz = d.q[row];
+    double2 sn = make_double2(0.0, 0.0), yn = make_double2(0.0, 0.0);
+    if (k > 0) {
+        const double2 zo = d.xp[row], go = d.gp[row];
+        sn = make_double2(z.x - zo.x, z.y - zo.y);
+        yn = make_double2(gz.x - go.x, gz.y - go.y);
+    }
+    if (pass == 0) {
+        acc[0] += gz.x * gz.x + gz.y * gz.y;
+        acc[1] += sn.x * yn.x + sn.y * yn.y;
+        acc[2] += sn.x * sn.x + sn.y * sn.y;
+        acc[3] += yn.x * yn.x + yn.y * yn.y;
+        acc[4] += sn.x * gz.x + sn.y * gz.y;
+        acc[5] += yn.x * gz.x + yn.y * gz.y;
+    }
+#pragma unroll
+    for (int t = 0; t < kLbSlotsPerPass; ++t) {
+        const int i = pass * kLbSlotsPerPass + t;
+        if (i >= hist) break;
+        const int j = lb_slot(head, i, mem);
+        const double2 S = d.Sh[(int64_t)j * d.M + row], Y = d.Yh[(int64_t)j * d.M + row];
+        acc[6 + 5 * t + 0] += S.x * gz.x + S.y * gz.y;
+        acc[6 + 5 * t + 1] += Y.x * gz.x + Y.y * gz.y;
+        acc[6 + 5 * t + 2] += sn.x * Y.x + sn.y * Y.y;
+        acc[6 + 5 * t + 3] += S.x * yn.x + S.y * yn.y;
+        acc[6 + 5 * t + 4] += yn.x * Y.x + yn.y * Y.y;
+    }
+}
+
+// Scatter the reduced values of pass `pass` into LbDots.
+__device__ __forceinline__ void lb_take(LbDots& o, const double* v, int pass)
+{
+    if (pass == 0)
+        for (int c = 0; c < 6; ++c) o.base[c] = v[c];
+    for (int t = 0; t < kLbSlotsPerPass; ++t) {
+        const int i = pass * kLbSlotsPerPass + t;
+        if (i >= kMaxMem) break;
+        o.sg[i] = v[6 + 5 * t + 0];
+        o.yg[i] = v[6 + 5 * t + 1];
+        o.sY[i] = v[6 + 5 * t + 2];
+        o.Sy[i] = v[6 + 5 * t + 3];
+        o.yY[i] = v[6 + 5 * t + 4];
+    }
+}
+
+// Problem s's slot products and 1/(s.y) between global memory and a block's
+// shared copy (every thread of the block takes part).
+__device__ __forceinline__ void lb_gram_load(const RelaxDev& d, int s, double* SY, double* YY, double* rho)
+{
+    const double* g = d.gram + (int64_t)s * kLbGram;
+    for (int e = threadIdx.x; e < kMaxMem * kMaxMem; e += blockDim.x) {
+        SY[e] = g[e];
+        YY[e] = g[kMaxMem * kMaxMem + e];
+    }
+    if (threadIdx.x < kMaxMem) rho[threadIdx.x] = d.rho[(int64_t)s * kMaxMem + threadIdx.x];
+}
+
+__device__ __forceinline__ void lb_gram_store(RelaxDev& d, int s, const double* SY, const double* YY, const double* rho)
+{
+    double* g = d.gram + (int64_t)s * kLbGram;
+    for (int e = threadIdx.x; e < kMaxMem * kMaxMem; e += blockDim.x) {
+        g[e] = SY[e];
+        g[kMaxMem * kMaxMem + e] = YY[e];
+    }
+    if (threadIdx.x < kMaxMem) d.rho[(int64_t)s * kMaxMem + threadIdx.x] = rho[threadIdx.x];
+}
+
+// The scalar part of the step (one thread): pair test and store into the
+// slot products, stop test, the recursion on inner products, descent check.
+// SY, YY, rho: shared-memory copies of problem s's s_a.y_b and y_a.y_b by ring
+// slot ([a][b]) and 1/(s_j.y_j) (lb_gram_load / lb_gram_store move them), so
+// the dependent chain of the recursion reads no global memory.  Writes hist,
+// head, rms, active of problem s.
+__device__ void lb_scalars(RelaxDev& d, int s, const Prob& p, const StepParams& sp, const LbDots& t, LbCoef& c,
+                           double* SY, double* YY, double* rho)
+{
+    const int k = d.steps[s], mem = sp.memory;
+    const int hist0 = d.hist[s], head0 = d.head[s];
+    c.rms = sqrt(t.base[0] / (double)max(p.m, 1));
+    c.keep = 0;
+    c.slot = head0;
+    c.stop = 1;
+    c.reset = 0;
+    c.hist = hist0;
+    c.head = head0;
+    if (sp.measure) {
+        d.rms[s] = c.rms;
+        return;
+    }
+    // s_j.gz and y_j.gz by ring slot
+    double sg[kMaxMem], yg[kMaxMem];
+    for (int i = 0; i < hist0; ++i) {
+        const int j = lb_slot(head0, i, mem);
+        sg[j] = t.sg[i];
+        yg[j] = t.yg[i];
+    }
+    int hist = hist0, head = head0;
+    c.keep = k > 0 && t.base[1] > 1e-12 * sqrt(t.base[2]) * sqrt(t.base[3]);
+    if (c.keep) {
+        const int jn = head0;
+        for (int i = 0; i < hist0; ++i) {
+            const int j = lb_slot(head0, i, mem);
+            if (j == jn) continue;  // the oldest pair, overwritten by the new one
+            SY[jn * kMaxMem + j] = t.sY[i];
+            SY[j * kMaxMem + jn] = t.Sy[i];
+            YY[jn * kMaxMem + j] = YY[j * kMaxMem + jn] = t.yY[i];
+        }
+        SY[jn * kMaxMem + jn] = t.base[1];
+        YY[jn * kMaxMem + jn] = t.base[3];
+        rho[jn] = 1.0 / t.base[1];
+        sg[jn] = t.base[4];
+        yg[jn] = t.base[5];
+        head = (head0 + 1) % mem;
+        hist = min(hist0 + 1, mem);
+    }
+    c.hist = hist;
+    c.head = head;
+    d.rms[s] = c.rms;
+    d.hist[s] = hist;
+    d.head[s] = head;
+    if (sp.gtol > 0.0 && c.rms < sp.gtol) {
+        d.active[s] = 0;
+        return;
+    }
+    c.stop = 0;
+    // first loop, newest pair first: alpha_i = rho_i s_i.q_i, q_i = gz - sum_{i' < i} alpha_i' y_i'
+    double al[kMaxMem], be[kMaxMem];
+    int js[kMaxMem];
+    for (int i = 0; i < hist; ++i) {
+        const int j = lb_slot(head, i, mem);
+        js[i] = j;
+        double sq = sg[j];
+        for (int i2 = 0; i2 < i; ++i2) sq -= al[i2] * SY[j * kMaxMem + js[i2]];
+        al[i] = rho[j] * sq;
+    }
+    const double gamma = hist > 0 ? SY[js[0] * kMaxMem + js[0]] / YY[js[0] * kMaxMem + js[0]] : sp.step0;
+    // second loop, oldest pair first: r = gamma q + sum_{older i'} (alpha_i' - beta_i') s_i',
+    // beta_i = rho_i y_i.r
+    for (int i = hist - 1; i >= 0; --i) {
+        const int j = js[i];
+        double yq = yg[j];
+        for (int i2 = 0; i2 < hist; ++i2) yq -= al[i2] * YY[j * kMaxMem + js[i2]];
+        double yr = gamma * yq;
+        for (int i2 = hist - 1; i2 > i; --i2) yr += (al[i2] - be[i2]) * SY[js[i2] * kMaxMem + j];
+        be[i] = rho[j] * yr;
+    }
+    // d = -r = -gamma gz + gamma sum alpha_i y_i - sum (alpha_i - beta_i) s_i
+    for (int j = 0; j < kMaxMem; ++j) c.cs[j] = c.cy[j] = 0.0;
+    c.cg = -gamma;
+    double gd = -gamma * t.base[0];
+    for (int i = 0; i < hist; ++i) {
+        c.cy[js[i]] = gamma * al[i];
+        c.cs[js[i]] = -(al[i] - be[i]);
+        gd += c.cy[js[i]] * yg[js[i]] + c.cs[js[i]] * sg[js[i]];
+    }
+    if (gd >= 0.0) {
+        c.reset = 1;
+        c.hist = c.head = 0;
+        d.hist[s] = 0;
+        d.head[s] = 0;
+        c.cg = -sp.step0;
+        for (int j = 0; j < kMaxMem; ++j) c.cs[j] = c.cy[j] = 0.0;
+    }
+}
+
+// Store the kept pair, keep dE/dz as the previous gradient, and (unless the
+// problem stops) write the direction into q; returns |d| of the row.
+__device__ __forceinline__ double lb_row_dir(RelaxDev& d, int64_t row, int k, const LbCoef& c, int mem)
+{
+    const double2 gz = d.q[row];
+    if (c.keep) {
+        const double2 z = d.z[row], zo = d.xp[row], go = d.gp[row];
+        d.Sh[(int64_t)c.slot * d.M + row] = make_double2(z.x - zo.x, z.y - zo.y);
+        d.Yh[(int64_t)c.slot * d.M + row] = make_double2(gz.x - go.x, gz.y - go.y);
+    }
+    d.gp[row] = gz;
+    if (c.stop) return 0.0;
+    double2 dv = make_double2(c.cg * gz.x, c.cg * gz.y);
+    for (int i = 0; i < c.hist; ++i) {
+        const int j = lb_slot(c.head, i, mem);
+        const double2 S = d.Sh[(int64_t)j * d.M + row], Y = d.Yh[(int64_t)j * d.M + row];
+        dv.x += c.cs[j] * S.x + c.cy[j] * Y.x;
+        dv.y += c.cs[j] * S.y + c.cy[j] * Y.y;
+    }
+    d.q[row] = dv;
+    return sqrt(dv.x * dv.x + dv.y * dv.y);
+}
+
+// The step z <- z + alpha d of one row, then x and its splits.
+__device__ __forceinline__ void lb_row_step(RelaxDev& d, int64_t row, double alpha, const StepParams& sp)
+{
+    const bool pinned = d.flags && d.flags[d.gidx[row]];
+    const double2 z = d.z[row], dv = d.q[row];
+    d.xp[row] = z;
+    if (d.xold) d.xold[row] = d.x[row];
+    const double2 zn = make_double2(z.x + alpha * dv.x, z.y + alpha * dv.y);
+    d.z[row] = zn;
+    const double2 xn = z_to_x(zn, sp.radius, pinned, d.tu);
+    d.x[row] = xn;
+    d.xs[row] = split4(xn.x, xn.y);
+    if (d.x3) d.x3[row] = split3(xn.x, xn.y);
+}
+
+// Deterministic block sums of N doubles per thread: a shuffle tree per warp,
+// then the warps' partials in warp order.
+template <int N> __device__ void block_sums_n(double (&v)[N], double (*red)[N])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[w][i] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double t = red[0][threadIdx.x];
+        for (int q = 1; q < kUpd / 32; ++q) t += red[q][threadIdx.x];
+        red[0][threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = red[0][i];
+    __syncthreads();
+}
+
 // L-BFGS on the wall parameterisation, one CTA per problem.  Same iteration as
 // the host statement: pair test and store, stop test, two-loop recursion
 // (Nocedal & Wright, Alg. 7.4), descent check, max-displacement scaling.
@@ -527,325 +806,213 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
 
 #include "tc_lbfgsb.cuh"
 
-// ------------------------------------------- L-BFGS for large problems ---
-// The same iteration as k_update_lbfgs, for one problem with many rows, as a
-// fixed sequence of grid-wide launches (host loops run to the memory size;
-// launches past the stored history return at once).  Every dot product is
-// written as per-block partials and added in block order by one CTA, so the
-// result does not depend on scheduling.  No launch waits on another CTA.
+// CTAs per problem of the L-BFGS-B update: the largest cluster size of 8, 4, 2
+// that the device can run for this kernel and that keeps all problems in one
+// wave (problems x size <= SMs), else 1.  A problem's float64 sums are added in
+// an order that depends on that size, so its result is deterministic for a
+// given number of problems in the call (and bit for bit the same run to run).
+template <int CL> static bool lbfgsb_cluster_ok()
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kUpd);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_update_lbfgsb<CL>, &cfg);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess && n >= 1;
+}
 
-struct LbScal {
-    double al[kMaxMem];  // two-loop alphas
-    double c;            // current second-loop coefficient
-    double gamma;        // H0 scale
-    double alpha;        // step scale
-    int keep, slot, done, reset;
-};
+// Largest usable cluster size on the current device (queried once per device).
+static int lbfgsb_cluster_max()
+{
+    static int cached[64];
+    static bool known[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (!known[dev]) {
+        cached[dev] = lbfgsb_cluster_ok<8>() ? 8 : lbfgsb_cluster_ok<4>() ? 4 : lbfgsb_cluster_ok<2>() ? 2 : 1;
+        known[dev] = true;
+    }
+    return cached[dev];
+}
+
+static int lbfgsb_cluster_size(int n_problems)
+{
+    int c = lbfgsb_cluster_max();
+    while (c > 1 && (int64_t)n_problems * c > sm_count()) c /= 2;
+    return c;
+}
+
+template <int CL>
+static cudaError_t launch_lbfgsb_cl(const RelaxDev& d, const double2* part_g, const SlotView& v, const StepParams& sp,
+                                    cudaStream_t st)
+{
+    if constexpr (CL == 1) {
+        k_update_lbfgsb<1><<<d.S, kUpd, 0, st>>>(d, part_g, v, sp);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)d.S * CL);
+        cfg.blockDim = dim3(kUpd);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_update_lbfgsb<CL>, d, part_g, v, sp);
+    }
+}
+
+static cudaError_t launch_lbfgsb(const RelaxDev& d, const double2* part_g, const SlotView& v, const StepParams& sp,
+                                 cudaStream_t st)
+{
+    switch (lbfgsb_cluster_size(d.S)) {
+        case 8: return launch_lbfgsb_cl<8>(d, part_g, v, sp, st);
+        case 4: return launch_lbfgsb_cl<4>(d, part_g, v, sp, st);
+        case 2: return launch_lbfgsb_cl<2>(d, part_g, v, sp, st);
+        default: return launch_lbfgsb_cl<1>(d, part_g, v, sp, st);
+    }
+}
+
+// ------------------------------------------- L-BFGS for large problems ---
+// The same step as k_update_lbfgs for one problem with many rows, as a fixed
+// sequence of grid-wide launches: the dot passes (per-block partials), one
+// thread for the scalars (partials added in block order, so the result does
+// not depend on scheduling), the direction (per-block maxima of |d|) and the
+// step.  No launch waits on another CTA.
 
 struct LbArgs {
     int s;
-    double* part;  // [kLargeBlocks][4]
-    LbScal* sc;
+    double* part;  // [kLbPasses][kLargeBlocks][kLbVals]
+    LbCoef* c;
 };
-
-__device__ __forceinline__ int lb_slot(int head, int i, int mem) { return ((head - 1 - i) % mem + mem) % mem; }
-
-// block partial of up to 4 doubles into part[blockIdx.x][0..3]
-__device__ void lb_partial(double (&v)[4], double* part, double* sh)
-{
-    block_sums(v, sh);
-    if (threadIdx.x == 0)
-        for (int c = 0; c < 4; ++c) part[blockIdx.x * 4 + c] = v[c];
-}
-
-__device__ void lb_total(const double* part, double (&t)[4])
-{
-    for (int c = 0; c < 4; ++c) t[c] = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
-        for (int c = 0; c < 4; ++c) t[c] += part[b * 4 + c];
-}
 
 #define TC_GRID_ROWS(p) for (int64_t rl = blockIdx.x * (int64_t)kUpd + threadIdx.x; rl < (p).m; rl += (int64_t)gridDim.x * kUpd)
 
-// 1. dE/dz into q; partials |gz|^2, s.y, s.s, y.y
-__global__ void __launch_bounds__(kUpd) k_lb_grad(RelaxDev d, LbArgs la, const double2* __restrict__ part_g,
-                                                  SlotView v, StepParams sp)
+// Dot pass `pass` (pass 0 also forms dE/dz into q).
+__global__ void __launch_bounds__(kUpd) k_lb_dots(RelaxDev d, LbArgs la, const double2* __restrict__ part_g,
+                                                  SlotView v, StepParams sp, int pass)
 {
-    __shared__ double sh[kUpd];
+    __shared__ double red[kUpd / 32][kLbVals];
     if (!d.active[la.s]) return;
     const Prob p = d.prob[la.s];
-    const int k = d.steps[la.s];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int k = d.steps[la.s], hist0 = sp.measure ? 0 : d.hist[la.s], head0 = d.head[la.s];
+    if (pass > 0 && pass * kLbSlotsPerPass >= hist0) return;
     bool bad = false;
+    double acc[kLbVals];
+#pragma unroll
+    for (int q = 0; q < kLbVals; ++q) acc[q] = 0.0;
     TC_GRID_ROWS(p)
     {
         const int64_t row = p.row_base + rl;
-        const double2 g = sum_g(p, rl, part_g, v);
-        if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
-        const bool pinned = d.flags && d.flags[d.gidx[row]];
-        const double2 z = d.z[row];
-        const double2 gz = grad_z(z, g, sp.radius, pinned, d.tu);
-        d.q[row] = gz;
-        acc[0] += gz.x * gz.x + gz.y * gz.y;
-        if (k > 0) {
-            const double2 zo = d.xp[row], go = d.gp[row];
-            const double sx = z.x - zo.x, sy = z.y - zo.y, yx = gz.x - go.x, yy = gz.y - go.y;
-            acc[1] += sx * yx + sy * yy;
-            acc[2] += sx * sx + sy * sy;
-            acc[3] += yx * yx + yy * yy;
+        if (pass == 0) {
+            const double2 g = sum_g(p, rl, part_g, v);
+            if (!isfinite(g.x) || !isfinite(g.y)) bad = true;
+            const bool pinned = d.flags && d.flags[d.gidx[row]];
+            d.q[row] = grad_z(d.z[row], g, sp.radius, pinned, d.tu);
         }
+        lb_row_dots(d, row, pass, k, hist0, head0, sp.memory, acc);
     }
     if (bad) set_status(d.st, ST_NONFINITE);
-    lb_partial(acc, la.part, sh);
+    block_sums_n<kLbVals>(acc, red);
+    if (threadIdx.x < kLbVals)
+        la.part[((int64_t)pass * kLargeBlocks + blockIdx.x) * kLbVals + threadIdx.x] = red[0][threadIdx.x];
 }
 
-// 2. pair test, history bookkeeping, stop test (one CTA)
-__global__ void k_lb_decide(RelaxDev d, LbArgs la, StepParams sp)
+// The scalars: the partials of every pass added in block order (one column
+// per thread), then the scalar step on thread 0 from shared copies.
+__global__ void __launch_bounds__(kUpd) k_lb_scalars(RelaxDev d, LbArgs la, StepParams sp)
 {
-    if (threadIdx.x != 0) return;
-    LbScal& c = *la.sc;
-    c.done = 1;
-    c.keep = 0;  // a stopped problem stores no pair (k_lb_store runs every step)
-    if (!d.active[la.s]) return;
-    const Prob p = d.prob[la.s];
-    const int k = d.steps[la.s];
-    double t[4];
-    for (int q = 0; q < 4; ++q) t[q] = 0.0;
-    for (int b = 0; b < kLargeBlocks; ++b)
-        for (int q = 0; q < 4; ++q) t[q] += la.part[b * 4 + q];
-    if (sp.measure) {
-        d.rms[la.s] = sqrt(t[0] / (double)max(p.m, 1));
+    __shared__ double tv[kLbPasses][kLbVals];
+    __shared__ double sSY[kMaxMem * kMaxMem], sYY[kMaxMem * kMaxMem], srho[kMaxMem];
+    __shared__ LbDots tot;
+    LbCoef& c = *la.c;
+    if (!d.active[la.s]) {
+        if (threadIdx.x == 0) {
+            c.keep = 0;
+            c.stop = 1;
+            c.hist = -1;  // inactive on entry: the direction and step launches do nothing
+        }
         return;
     }
-    const int mem = sp.memory;
-    int hist = d.hist[la.s], head = d.head[la.s];
-    c.keep = k > 0 && t[1] > 1e-12 * sqrt(t[2]) * sqrt(t[3]);
-    c.slot = head;
-    if (c.keep) {
-        d.rho[(int64_t)la.s * kMaxMem + head] = 1.0 / t[1];
-        head = (head + 1) % mem;
-        hist = min(hist + 1, mem);
-    }
-    const double rms = sqrt(t[0] / (double)max(p.m, 1));
-    d.rms[la.s] = rms;
-    d.hist[la.s] = hist;
-    d.head[la.s] = head;
-    if (sp.gtol > 0.0 && rms < sp.gtol) {
-        d.active[la.s] = 0;
-        return;
-    }
-    c.done = 0;
-}
-
-// 3. store the pair, keep dE/dz
-__global__ void __launch_bounds__(kUpd) k_lb_store(RelaxDev d, LbArgs la)
-{
-    const LbScal& c = *la.sc;
     const Prob p = d.prob[la.s];
-    const int64_t M = d.M;
-    TC_GRID_ROWS(p)
-    {
-        const int64_t row = p.row_base + rl;
-        const double2 gz = d.q[row];
-        if (c.keep) {
-            const double2 z = d.z[row], zo = d.xp[row], go = d.gp[row];
-            d.Sh[(int64_t)c.slot * M + row] = make_double2(z.x - zo.x, z.y - zo.y);
-            d.Yh[(int64_t)c.slot * M + row] = make_double2(gz.x - go.x, gz.y - go.y);
-        }
-        d.gp[row] = gz;
+    const int hist0 = sp.measure ? 0 : d.hist[la.s];
+    const int passes = max(1, (hist0 + kLbSlotsPerPass - 1) / kLbSlotsPerPass);
+    for (int e = threadIdx.x; e < passes * kLbVals; e += blockDim.x) {
+        const int pass = e / kLbVals, q = e % kLbVals;
+        double t = 0.0;
+        for (int b = 0; b < kLargeBlocks; ++b) t += la.part[((int64_t)pass * kLargeBlocks + b) * kLbVals + q];
+        tv[pass][q] = t;
     }
+    lb_gram_load(d, la.s, sSY, sYY, srho);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int pass = 0; pass < passes; ++pass) lb_take(tot, tv[pass], pass);
+        lb_scalars(d, la.s, p, sp, tot, c, sSY, sYY, srho);
+    }
+    __syncthreads();
+    if (!sp.measure) lb_gram_store(d, la.s, sSY, sYY, srho);
 }
 
-// 4. two-loop recursion step.  phase 1, entry i: q -= al[j_{i-1}] y_{j_{i-1}} (i > 0),
-// then partial s_{j_i} . q (i < hist); at i == hist also the gamma partials.
-// phase 2, entry i (counting down from hist - 1): q += c s_{j_{i+1}} (i < hist - 1)
-// or q *= gamma (i == hist - 1), then partial y_{j_i} . q.
-__global__ void __launch_bounds__(kUpd) k_lb_loop(RelaxDev d, LbArgs la, StepParams sp, int phase, int i)
-{
-    __shared__ double sh[kUpd];
-    const LbScal& c = *la.sc;
-    if (c.done) return;
-    const Prob p = d.prob[la.s];
-    const int hist = d.hist[la.s], head = d.head[la.s], mem = sp.memory;
-    const int64_t M = d.M;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (phase == 1) {
-        if (i > hist) return;
-        const int jp = i > 0 ? lb_slot(head, i - 1, mem) : 0;
-        const int jn = i < hist ? lb_slot(head, i, mem) : 0;
-        const int jnew = lb_slot(head, 0, mem);
-        const double a = i > 0 ? c.al[jp] : 0.0;
-        TC_GRID_ROWS(p)
-        {
-            const int64_t row = p.row_base + rl;
-            double2 q = d.q[row];
-            if (i > 0) {
-                const double2 y = d.Yh[(int64_t)jp * M + row];
-                q = make_double2(q.x - a * y.x, q.y - a * y.y);
-                d.q[row] = q;
-            }
-            if (i < hist) {
-                const double2 sv = d.Sh[(int64_t)jn * M + row];
-                acc[0] += sv.x * q.x + sv.y * q.y;
-            } else if (hist > 0) {
-                const double2 sv = d.Sh[(int64_t)jnew * M + row], y = d.Yh[(int64_t)jnew * M + row];
-                acc[1] += sv.x * y.x + sv.y * y.y;
-                acc[2] += y.x * y.x + y.y * y.y;
-            }
-        }
-    } else {
-        if (i >= hist) return;
-        const int jn = lb_slot(head, i, mem);
-        const int jp = i < hist - 1 ? lb_slot(head, i + 1, mem) : 0;
-        TC_GRID_ROWS(p)
-        {
-            const int64_t row = p.row_base + rl;
-            double2 q = d.q[row];
-            if (i == hist - 1) {
-                q = make_double2(q.x * c.gamma, q.y * c.gamma);
-            } else {
-                const double2 sv = d.Sh[(int64_t)jp * M + row];
-                q = make_double2(q.x + c.c * sv.x, q.y + c.c * sv.y);
-            }
-            d.q[row] = q;
-            const double2 y = d.Yh[(int64_t)jn * M + row];
-            acc[0] += y.x * q.x + y.y * q.y;
-        }
-    }
-    lb_partial(acc, la.part, sh);
-}
-
-// 5. scalars after a loop step (one CTA)
-__global__ void k_lb_loop_fin(RelaxDev d, LbArgs la, StepParams sp, int phase, int i)
-{
-    if (threadIdx.x != 0) return;
-    LbScal& c = *la.sc;
-    if (c.done) return;
-    const int hist = d.hist[la.s], head = d.head[la.s], mem = sp.memory;
-    const double* rho = d.rho + (int64_t)la.s * kMaxMem;
-    double t[4];
-    for (int q = 0; q < 4; ++q) t[q] = 0.0;
-    for (int b = 0; b < kLargeBlocks; ++b)
-        for (int q = 0; q < 4; ++q) t[q] += la.part[b * 4 + q];
-    if (phase == 1) {
-        if (i > hist) return;
-        if (i < hist) {
-            const int j = lb_slot(head, i, mem);
-            c.al[j] = rho[j] * t[0];
-        } else {
-            c.gamma = hist > 0 ? t[1] / t[2] : sp.step0;
-        }
-    } else {
-        if (i >= hist) return;
-        const int j = lb_slot(head, i, mem);
-        c.c = c.al[j] - rho[j] * t[0];
-    }
-}
-
-// 6. finish the direction: last second-loop update (or the gamma scaling
-// without history), then partials of gz . q and max |q|
+// Pair store, previous gradient, direction; per-block maximum of |d|.
 __global__ void __launch_bounds__(kUpd) k_lb_dir(RelaxDev d, LbArgs la, StepParams sp)
 {
     __shared__ double sh[kUpd];
-    const LbScal& c = *la.sc;
-    if (c.done) return;
+    const LbCoef& c = *la.c;
+    if (sp.measure || c.hist < 0) return;
     const Prob p = d.prob[la.s];
-    const int hist = d.hist[la.s], head = d.head[la.s], mem = sp.memory;
-    const int64_t M = d.M;
-    const int j0 = lb_slot(head, 0, mem);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int k = d.steps[la.s];
     double mx = 0.0;
-    TC_GRID_ROWS(p)
-    {
-        const int64_t row = p.row_base + rl;
-        double2 q = d.q[row];
-        if (hist > 0) {
-            const double2 sv = d.Sh[(int64_t)j0 * M + row];
-            q = make_double2(q.x + c.c * sv.x, q.y + c.c * sv.y);
-        } else {
-            q = make_double2(q.x * c.gamma, q.y * c.gamma);
-        }
-        d.q[row] = q;  // H gz; the direction is -q
-        const double2 gz = d.gp[row];
-        acc[0] += gz.x * q.x + gz.y * q.y;
-        mx = fmax(mx, sqrt(q.x * q.x + q.y * q.y));
-        acc[2] = fmax(acc[2], sqrt(gz.x * gz.x + gz.y * gz.y));
-    }
-    acc[1] = block_max(mx, sh);
-    acc[2] = block_max(acc[2], sh);
-    acc[0] = block_sum<kUpd>(acc[0], sh);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 4; ++q) la.part[blockIdx.x * 4 + q] = acc[q];
+    TC_GRID_ROWS(p) mx = fmax(mx, lb_row_dir(d, p.row_base + rl, k, c, sp.memory));
+    mx = block_max(mx, sh);
+    if (threadIdx.x == 0) la.part[blockIdx.x] = mx;
 }
 
-// 7. descent check and step scale (one CTA)
-__global__ void k_lb_dir_fin(RelaxDev d, LbArgs la, StepParams sp)
-{
-    if (threadIdx.x != 0) return;
-    LbScal& c = *la.sc;
-    if (c.done) return;
-    double dd = 0.0, qmax = 0.0, gmax = 0.0;
-    for (int b = 0; b < kLargeBlocks; ++b) {
-        dd += la.part[b * 4 + 0];
-        qmax = fmax(qmax, la.part[b * 4 + 1]);
-        gmax = fmax(gmax, la.part[b * 4 + 2]);
-    }
-    // direction -q is a descent direction iff gz . q > 0
-    c.reset = !(dd > 0.0);
-    if (c.reset) {
-        d.hist[la.s] = 0;
-        d.head[la.s] = 0;
-    }
-    const double dmax = c.reset ? sp.step0 * gmax : qmax;
-    c.alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
-    if (d.ls_alpha) d.ls_alpha[la.s] = c.alpha;
-}
-
-// 8. the step z += alpha d, then x and its split
+// The step; every block takes the maximum over the blocks' maxima in block order.
 __global__ void __launch_bounds__(kUpd) k_lb_step(RelaxDev d, LbArgs la, StepParams sp)
 {
-    const LbScal& c = *la.sc;
-    if (c.done) return;
+    const LbCoef& c = *la.c;
+    if (c.hist < 0 || c.stop) return;
     const Prob p = d.prob[la.s];
-    TC_GRID_ROWS(p)
-    {
-        const int64_t row = p.row_base + rl;
-        const bool pinned = d.flags && d.flags[d.gidx[row]];
-        const double2 z = d.z[row], q = d.q[row], gz = d.gp[row];
-        const double2 dv = c.reset ? make_double2(-sp.step0 * gz.x, -sp.step0 * gz.y) : make_double2(-q.x, -q.y);
-        d.xp[row] = z;
-        if (d.xold) {
-            d.xold[row] = d.x[row];
-            d.q[row] = dv;  // the line search moves along dv
-        }
-        const double2 zn = make_double2(z.x + c.alpha * dv.x, z.y + c.alpha * dv.y);
-        d.z[row] = zn;
-        const double2 xn = z_to_x(zn, sp.radius, pinned, d.tu);
-        d.x[row] = xn;
-        d.xs[row] = split4(xn.x, xn.y);
-        if (d.x3) d.x3[row] = split3(xn.x, xn.y);
+    double dmax = 0.0;
+    for (int b = 0; b < kLargeBlocks; ++b) dmax = fmax(dmax, la.part[b]);
+    const double alpha = dmax > sp.maxstep ? sp.maxstep / dmax : 1.0;
+    TC_GRID_ROWS(p) lb_row_step(d, p.row_base + rl, alpha, sp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (d.ls_alpha) d.ls_alpha[la.s] = alpha;
+        d.steps[la.s] = d.steps[la.s] + 1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.steps[la.s] = d.steps[la.s] + 1;
 }
 
-// Launch the sequence for one large problem.
+// Launches of one step of one large problem (measure: the RMS only).
+static int lbfgs_large_launches(const StepParams& sp)
+{
+    return sp.measure ? 2 : (sp.memory + kLbSlotsPerPass - 1) / kLbSlotsPerPass + 3;
+}
+
 static cudaError_t lbfgs_large(RelaxDev& d, LbArgs la, const double2* part_g, SlotView v, const StepParams& sp,
                                cudaStream_t s)
 {
-    k_lb_grad<<<kLargeBlocks, kUpd, 0, s>>>(d, la, part_g, v, sp);
-    k_lb_decide<<<1, 32, 0, s>>>(d, la, sp);
-    k_lb_store<<<kLargeBlocks, kUpd, 0, s>>>(d, la);
-    for (int i = 0; i <= sp.memory; ++i) {
-        k_lb_loop<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp, 1, i);
-        k_lb_loop_fin<<<1, 32, 0, s>>>(d, la, sp, 1, i);
+    const int passes = sp.measure ? 1 : std::max(1, (sp.memory + kLbSlotsPerPass - 1) / kLbSlotsPerPass);
+    for (int pass = 0; pass < passes; ++pass) k_lb_dots<<<kLargeBlocks, kUpd, 0, s>>>(d, la, part_g, v, sp, pass);
+    k_lb_scalars<<<1, kUpd, 0, s>>>(d, la, sp);
+    if (!sp.measure) {
+        k_lb_dir<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp);
+        k_lb_step<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp);
     }
-    for (int i = sp.memory - 1; i >= 0; --i) {
-        k_lb_loop<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp, 2, i);
-        k_lb_loop_fin<<<1, 32, 0, s>>>(d, la, sp, 2, i);
-    }
-    k_lb_dir<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp);
-    k_lb_dir_fin<<<1, 32, 0, s>>>(d, la, sp);
-    k_lb_step<<<kLargeBlocks, kUpd, 0, s>>>(d, la, sp);
     return cudaGetLastError();
 }
 
@@ -1147,7 +1314,7 @@ static_assert(sizeof(tc_relax_profile) == 56, "tc_relax_profile layout");
 struct LargeSet {
     std::vector<int> ids;
     double* part = nullptr;
-    LbScal* sc = nullptr;  // one per entry of ids
+    LbCoef* sc = nullptr;  // one per entry of ids
 };
 
 // The energy-change pass of the line search: float32 difference form in the
@@ -1206,14 +1373,14 @@ static cudaError_t launch_step(RelaxDev& d, const PassArgs& a, const Plan& P, in
     if (e != cudaSuccess) return e;
     if (ev_mid && (e = cudaEventRecord(ev_mid, st)) != cudaSuccess) return e;
     if (sp.opt == TC_OPT_LBFGSB_TU) {
-        k_update_lbfgsb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
-        if (ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, st, launches);
+        e = launch_lbfgsb(d, a.part_g, v, sp, st);
+        if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, st, launches);
     } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
         k_update_lbfgs<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
         for (size_t q = 0; q < large.ids.size(); ++q) {
             LbArgs la{large.ids[q], large.part, large.sc + q};
             if (e == cudaSuccess) e = lbfgs_large(d, la, a.part_g, v, sp, st);
-            launches += 2 * (2 * sp.memory + 1) + 6;
+            launches += lbfgs_large_launches(sp);
         }
         if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, st, launches);
     } else {
@@ -1235,14 +1402,13 @@ static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P,
     StepParams sm = sp;
     sm.measure = 1;
     if (sp.opt == TC_OPT_LBFGSB_TU) {
-        k_update_lbfgsb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
+        launch_lbfgsb(d, a.part_g, v, sm, st);
     } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
         k_update_lbfgs<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
         for (size_t q = 0; q < large.ids.size(); ++q) {
             LbArgs la{large.ids[q], large.part, large.sc + q};
-            k_lb_grad<<<kLargeBlocks, kUpd, 0, st>>>(d, la, a.part_g, v, sm);
-            k_lb_decide<<<1, 32, 0, st>>>(d, la, sm);
-            launches += 2;
+            lbfgs_large(d, la, a.part_g, v, sm, st);
+            launches += lbfgs_large_launches(sm);
         }
     } else {
         k_update_gdbb<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
@@ -1255,7 +1421,9 @@ static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P,
 //  - profiled: directly on s, with an event between each pass and update;
 //  - inside a caller's stream capture: every step joins the caller's graph;
 //  - otherwise: kChunkSteps steps are captured once on a private stream and the
-//    graph is replayed on s; with a stopping tolerance the host checks between
+//    graph is replayed on s (the executable graph comes from a per-device cache
+//    and is updated in place when an earlier call had the same shape, so a
+//    repeated call does not instantiate again); with a stopping tolerance the host checks between
 //    replays whether any problem is still active and stops when none is (the
 //    steps it skips would have been no-ops: every kernel returns at once for an
 //    inactive problem).  A shorter last chunk is launched directly.
@@ -1304,7 +1472,7 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
     for (int k = 0; k < K && e == cudaSuccess; ++k) e = launch_step<KIND>(d, a, P, G, sp, cap, per_chunk, large, ls, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
     if (e == cudaSuccess && (e = e2) != cudaSuccess) where = "cudaStreamEndCapture";
-    if (e == cudaSuccess && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) where = "cudaGraphInstantiate";
+    if (e == cudaSuccess && !(exec = take_graph_exec(graph, &e))) where = "cudaGraphInstantiate";
     int done = 0;
     while (e == cudaSuccess && done + K <= steps) {
         if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
@@ -1331,7 +1499,12 @@ static tc_status run_phase(RelaxDev& d, PassArgs a, const Plan& P, int64_t G, co
     // the executable graph is destroyed only after its launches have finished
     cudaError_t e3 = cudaStreamSynchronize(s);
     if (e == cudaSuccess && (e = e3) != cudaSuccess) where = "step loop execution";
-    if (exec) cudaGraphExecDestroy(exec);
+    // a graph that ran cleanly goes back to the cache: the next call of this shape updates it in
+    // place (cudaGraphExecUpdate) instead of instantiating a new one
+    if (exec && e == cudaSuccess)
+        give_graph_exec(exec);
+    else if (exec)
+        cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     return cuda_status(e, where);
 }
@@ -1414,6 +1587,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int prec = prm->precision;
     const bool lbfgs = prm->optimizer >= TC_OPT_LBFGS;
     const bool boxed = prm->optimizer == TC_OPT_LBFGSB_TU;
+    if (boxed) (void)lbfgsb_cluster_max();  // queried here, outside any stream capture
     const int mem = lbfgs ? prm->memory : 0;
     const int64_t G_bulk = prec == TC_MIXED  ? pass_grid<PASS_MIXED, false, true>(P.W)
                            : prec == TC_F64X ? pass_grid<PASS_F64X, false, true>(P.W)
@@ -1483,12 +1657,13 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         d.head = cv.take<int>(n_sub);
         d.status = cv.take<int>(n_sub);
         d.rho = cv.take<double>((size_t)n_sub * kMaxMem);
+        d.gram = cv.take<double>(lbfgs && !boxed ? (size_t)n_sub * kLbGram : 0);
         d.rms = cv.take<double>(n_sub);
         d.delta = cv.take<double>(n_sub);
         d.energy = cv.take<double>(n_sub);
         snap_split = cv.take<float4>(inst ? 0 : n);
-        large.part = cv.take<double>(lbfgs ? (size_t)kLargeBlocks * 4 : 0);
-        large.sc = cv.take<LbScal>(lbfgs ? large.ids.size() : 0);
+        large.part = cv.take<double>(lbfgs ? (size_t)kLbPasses * kLargeBlocks * kLbVals : 0);
+        large.sc = cv.take<LbCoef>(lbfgs ? large.ids.size() : 0);
         part_e = cv.take<double>(slots * M);
         part_g = cv.take<double2>(slots * M);
         part1 = cv.take<double>(slots1 * max_m);

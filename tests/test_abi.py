@@ -32,8 +32,8 @@ def test_struct_layouts_match_header(lib):
     assert C.sizeof(L.RelaxProfile) == 56
     # tc_zone_params: 4 double, 4 int32; tc_cycle_params: zone, relax, 2 int32
     assert C.sizeof(L.ZoneParams) == 48 and L.ZoneParams.m_min.offset == 32
-    assert C.sizeof(L.CycleParams) == 176 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 144
-    assert L.CycleParams.disjoint.offset == 168
+    assert C.sizeof(L.CycleParams) == 184 and L.CycleParams.relax.offset == 48 and L.CycleParams.batch.offset == 144
+    assert L.CycleParams.disjoint.offset == 168 and L.CycleParams.ramp_total.offset == 176
     assert L.CycleParams.sigma0.offset == 152
 
 

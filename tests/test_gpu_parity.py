@@ -424,3 +424,24 @@ def test_lbfgs_tolerance_stop_then_polish_equals_one_run(n):
     tc.relax_subdomains(pb, world=world, n_steps=k, **kw)
     tc.sync_status()
     np.testing.assert_array_equal(pa.cpu().numpy(), pb.cpu().numpy())
+
+
+def test_repeated_calls_reuse_the_step_graph_with_new_arguments():
+    """The executable step-loop graph is kept across calls and updated in place for a call of the
+    same shape: a call on configuration A, then B, then A again (and a call of another shape in
+    between) gives A's result bit for bit, equal to the directly launched (profiled) loop."""
+    n = 5000
+    kw = dict(world=T(np.array([[0, 2000], [2000, n]], dtype=np.int64)), precision="mixed", optimizer="lbfgs",
+              n_steps=70, memory=8, step0=1e-5, maxstep=0.01, accept=False)
+    a = synth.arcsine_disk(n, 61)
+    b = synth.arcsine_disk(n, 62)
+    outs = []
+    for pos, extra in ((a, {}), (b, {}), (synth.arcsine_disk(3000, 63), {"world": T(np.array([[0, 3000]]))}),
+                       (a, {}), (a, {"profile": True})):
+        p = T(pos.copy())
+        tc.relax_subdomains(p, **{**kw, **extra})
+        tc.sync_status()
+        outs.append(p.cpu().numpy())
+    np.testing.assert_array_equal(outs[3], outs[0])
+    np.testing.assert_array_equal(outs[4], outs[0])
+    assert not np.array_equal(outs[1], outs[0])
