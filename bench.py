@@ -338,6 +338,39 @@ def run_c3_disjoint(pos_np, relax_kw: dict, flush, stream, reps: int = 2, seed: 
             "accepted_subdomains": acc, "skipped_overlap": int((r.status == 2).sum().item())}
 
 
+def run_graph_effect(dev, n: int = 1000, steps: int = 500, reps: int = 3) -> dict:
+    """The step loop as a CUDA graph against direct launches where launches dominate: one N = 1000
+    instance (config C1's size), 500 mixed L-BFGS steps, each step a few microseconds of kernel time.
+    The direct form is the profiled loop (an event between launches), the graph form replays the
+    cached 64-step graph."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2609_24722_b300 as tc
+
+    pos = torch.tensor(synth.arcsine_disk(n, 0), device=dev)
+    world = torch.tensor(np.array([[0, n]], dtype=np.int64), device=dev)
+    kw = dict(world=world, precision="mixed", optimizer="lbfgs", n_steps=steps, memory=8, step0=1e-4, maxstep=0.01,
+              accept=False)
+    out = {}
+    for name, prof in (("graph", False), ("direct", True)):
+        ts = []
+        for _ in range(reps + 1):
+            p = pos.clone()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            tc.relax_subdomains(p, profile=prof, **kw)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[f"{name}_ms"] = statistics.median(ts[1:])
+    tc.sync_status()
+    return {"workload": f"one instance of N={n}, {steps} mixed L-BFGS(8) steps", **out,
+            "us_per_step_graph": 1e3 * out["graph_ms"] / steps, "us_per_step_direct": 1e3 * out["direct_ms"] / steps}
+
+
 def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps: int = 500,
                   polish: int = 20, fp64_steps: int = 10, polish_precision: str = "fp64"):
     """Config C5: 512 independent instances (N_k ~ U{100..5000}, arcsine init each), relaxed in one
@@ -724,6 +757,7 @@ def main():
     ms_f64 = time_allpairs("fp64", 3)
     ms_f64x = time_allpairs("fp64x", 3)
     c5 = run_instances(dev) if not args.no_instances else None
+    graph_effect = run_graph_effect(dev) if not args.no_instances else None
     # config C4: the full relaxation of one N = 1e5 configuration, float64 polish, oracle energy check
     c4 = run_full_relax(dev) if not args.no_instances else None
     if c5 is not None:
@@ -795,6 +829,7 @@ def main():
         "c3_relax_pass_by_precision": c3_pass,
         "c3_disjoint_subdomains": c3_disjoint,
         "instances_c5": c5,
+        "step_graph_vs_direct": graph_effect,
         "full_relax_c4": c4,
         "adaptive_cycle": cyc,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
