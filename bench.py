@@ -750,8 +750,9 @@ def main():
         c3_pass[prec_name] = {"ms_per_pass": ms_p, "pairs_per_s": pr["pass_pairs"] / (ms_p / 1e3)}
     c3_pass["mixed"] = {"ms_per_pass": prof["pass_ms"] / max(prof["n_pass"], 1),
                         "pairs_per_s": prof["pass_pairs"] / (prof["pass_ms"] / max(prof["n_pass"], 1) / 1e3)}
-    # SURVEY Q1's second reading of the subdomain workload: 256 truly disjoint subdomains, m ~ U{200..5000}
-    # scaled by 0.9 N / sum(m), every one relaxed and accepted on its own merit (no overlap skips)
+    # the other reading of the subdomain workload (256 subdomains of m ~ U{200..5000} cannot be disjoint
+    # in N = 1e5): 256 truly disjoint subdomains with m scaled by 0.9 N / sum(m), every one relaxed and
+    # accepted on its own merit (no overlap skips)
     c3_disjoint = run_c3_disjoint(pos_np, relax_kw, flush, stream, reps=2, seed=rank)
     ms_mixed = time_allpairs("mixed", 5)
     ms_f64 = time_allpairs("fp64", 3)

@@ -93,11 +93,12 @@ __device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, 
 // Row partial of one pass: sum of its slots in order (float64, compensated for e).
 struct SlotView {
     int64_t W, G, u_base, stride, row_sub;
+    const int64_t* bounds = nullptr;  // the pass's CTA bounds when it used explicit ones
 };
 
 __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double2* part_g, const SlotView& v)
 {
-    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
+    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G, v.bounds);
     double gx = 0.0, gy = 0.0;
     int64_t o = p.row_base + rl - v.row_sub;
     for (int64_t k = 0; k < c; ++k) {
@@ -110,7 +111,7 @@ __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double
 
 __device__ __forceinline__ double sum_e(const Prob& p, int64_t rl, const double* part_e, const SlotView& v)
 {
-    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
+    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G, v.bounds);
     double hi = 0.0, lo = 0.0;
     int64_t o = p.row_base + rl - v.row_sub;
     for (int64_t k = 0; k < c; ++k) dd_add(hi, lo, part_e[k * v.stride + o]);
@@ -1368,7 +1369,7 @@ static cudaError_t launch_step(RelaxDev& d, const PassArgs& a, const Plan& P, in
                                cudaStream_t st, int& launches, const LargeSet& large, const LsArgs* ls,
                                cudaEvent_t ev_mid)
 {
-    const SlotView v{P.W, G, 0, P.M, 0};
+    const SlotView v{P.W, G, 0, P.M, 0, a.bounds};
     cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
     if (e != cudaSuccess) return e;
     if (ev_mid && (e = cudaEventRecord(ev_mid, st)) != cudaSuccess) return e;
@@ -1396,7 +1397,7 @@ template <int KIND>
 static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P, int64_t G, const StepParams& sp,
                                   cudaStream_t st, int& launches, const LargeSet& large)
 {
-    const SlotView v{P.W, G, 0, P.M, 0};
+    const SlotView v{P.W, G, 0, P.M, 0, a.bounds};
     cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
     if (e != cudaSuccess) return e;
     StepParams sm = sp;
@@ -1599,8 +1600,14 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int64_t G_d = pass_grid<PASS_DELTA, false, false>(P.W);
     const bool ls_on = lbfgs && prm->line_search > 0;
     const int64_t G_dm = pass_grid<PASS_DMIX, false, false>(P.W);
+    // the mixed bulk pass may cut its units by estimated work (row blocks that fit in the half
+    // path of the launch shape weigh half)
+    const std::vector<int64_t> wbounds =
+        prec == TC_MIXED ? plan_weighted_bounds(P.prob, P.W, G_bulk, mixed_half_rows()) : std::vector<int64_t>();
     int64_t slots = 1;
     for (int64_t G : {G_bulk, G_f64, G_e, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
+    if (!wbounds.empty())
+        slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_bulk, wbounds.data()));
     // single-problem passes of the sequential accept
     int64_t slots1 = 1;
     std::vector<int64_t> G1(n_sub);
@@ -1622,6 +1629,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
 
     Carver c;
     fx3* snap3 = nullptr;
+    int64_t* bounds_d = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
         probd = cv.take<Prob>(n_sub);
@@ -1667,6 +1675,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         part_e = cv.take<double>(slots * M);
         part_g = cv.take<double2>(slots * M);
         part1 = cv.take<double>(slots1 * max_m);
+        bounds_d = cv.take<int64_t>(wbounds.size());
     };
     RelaxDev d{};
     Prob* probd;
@@ -1695,6 +1704,8 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     if (prof) cudaEventRecord(ev_a, s);
     e = cudaMemcpyAsync(probd, P.prob.data(), sizeof(Prob) * n_sub, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(wbd, wbeg.data(), 8 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !wbounds.empty())
+        e = cudaMemcpyAsync(bounds_d, wbounds.data(), 8 * wbounds.size(), cudaMemcpyHostToDevice, s);
     // per-problem state: active = ok = 1, counters zero
     std::vector<int> ones(n_sub, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
@@ -1769,9 +1780,11 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     ls_f64.G = G_d;
     tc_status rs;
     if (prec == TC_MIXED) {
-        a.rows = d.xs;
-        a.snap = snap_split;
-        rs = run_phase<PASS_MIXED>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
+        PassArgs ab = a;
+        ab.rows = d.xs;
+        ab.snap = snap_split;
+        ab.bounds = wbounds.empty() ? nullptr : bounds_d;
+        rs = run_phase<PASS_MIXED>(d, ab, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
     } else if (prec == TC_F64X) {
         a.rows = d.x3;
         a.snap = snap3;
