@@ -49,19 +49,49 @@ __device__ __forceinline__ double breakpoint(double z, double g, double lo, doub
     return INFINITY;
 }
 
-// Deterministic block sums of N doubles per thread: a shuffle tree per warp,
-// then the warps' partials in warp order.
+// Warp partials of values v[OFF .. OFF + N) (N <= 32) into red[warp][OFF + i]:
+// a shuffle tree per value that halves the live values at each level
+// (recursive halving).  At offset o a lane keeps one half of its live values,
+// sends the other half to lane ^ o and adds what it receives, so the warp
+// spends about one add per value instead of five.  Every value still meets the
+// other lanes' partials in the pairs and order of a shfl_down tree (an add of
+// two doubles is commutative), so each partial is bit for bit that tree's.
+// Value i ends in lane i << (5 - log2 NP), NP = N rounded up to a power of two.
+template <int N, int OFF, int M> __device__ __forceinline__ void warp_sums(const double (&v)[M], double (*red)[kRed])
+{
+    static_assert(N >= 1 && N <= 32 && OFF + N <= M, "warp_sums range");
+    constexpr int NP = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
+    constexpr int SH = NP == 1 ? 5 : NP == 2 ? 4 : NP == 4 ? 3 : NP == 8 ? 2 : NP == 16 ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    double x[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) x[i] = i < N ? v[OFF + i] : 0.0;
+#pragma unroll
+    for (int o = 16, c = NP; o > 0; o >>= 1) {
+        if (c > 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < NP / 2; ++k)
+                if (k < c / 2) {
+                    const double keep = up ? x[k + c / 2] : x[k], send = up ? x[k] : x[k + c / 2];
+                    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            c /= 2;
+        } else {
+            x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+        }
+    }
+    const int i = lane >> SH;
+    if ((lane & ((1 << SH) - 1)) == 0 && i < N) red[threadIdx.x >> 5][OFF + i] = x[0];
+}
+
+// Deterministic block sums of N doubles per thread: warp partials (warp_sums,
+// 32 values at a time), then the warps' partials in warp order.
 template <int N> __device__ void block_sums_w(double (&v)[N], double (*red)[kRed])
 {
     static_assert(N <= kRed, "reduction too wide");
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        double x = v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[w][i] = x;
-    }
+    warp_sums<(N < 32 ? N : 32), 0>(v, red);
+    if constexpr (N > 32) warp_sums<N - 32, 32>(v, red);
     __syncthreads();
     if (threadIdx.x < N) {
         double t = red[0][threadIdx.x];
@@ -110,53 +140,58 @@ __device__ void block_argmin(double& t, int& r, double* sht, int* shr)
 
 // Row of the largest |a[r * ld + col]| over rows col .. kBQ-1, the first such
 // row on ties (as a search that keeps the first maximum), or -1 if that value
-// is 0; computed by warp 0 and returned to every thread.
-__device__ int block_pivot(const double* a, int ld, int col, int* sh_piv)
+// is 0; every lane of the calling warp gets it.  For doubles that are not
+// negative the order of their bit patterns as integers is their numeric order,
+// so the search compares integers (a NaN entry counts as 0 and is never taken).
+__device__ __forceinline__ int warp_pivot(const double* a, int ld, int col)
 {
-    if (threadIdx.x < 32) {
-        const int r0 = threadIdx.x;
-        double v = (r0 >= col && r0 < kBQ) ? fabs(a[r0 * ld + col]) : -1.0;
-        int r = r0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
-            if (v2 > v || (v2 == v && r2 < r)) {
-                v = v2;
-                r = r2;
-            }
-        }
-        if (threadIdx.x == 0) *sh_piv = v > 0.0 ? r : -1;
+    const int r0 = threadIdx.x & 31;
+    unsigned long long key = 0ull;
+    if (r0 >= col && r0 < kBQ) {
+        const double v = a[r0 * ld + col];
+        key = v == v ? (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull : 0ull;
     }
-    __syncthreads();
-    const int piv = *sh_piv;
-    __syncthreads();
-    return piv;
+    int r = r0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+        if (k2 > key || (k2 == key && r2 < r)) {
+            key = k2;
+            r = r2;
+        }
+    }
+    return key > 0ull ? r : -1;
 }
 
 // [K | I] -> [I | K^{-1}] by Gauss-Jordan elimination with partial pivoting,
 // the whole CTA taking part (two of the 16 x 32 entries per thread).  Every
 // entry sees the same operations in the same order as a one-lane-per-column
-// elimination.  False (for every thread) if a pivot is 0.
+// elimination.  Per column, warp 0 finds the pivot, swaps and divides the
+// pivot row and records the column for the elimination (one CTA barrier), then
+// every thread eliminates (a second barrier).  False (for every thread) if a
+// pivot is 0.
 __device__ bool block_gauss_jordan(double* aug, double* fcol, int* sh_piv)
 {
     constexpr int ld = 2 * kBQ;
     static_assert(ld == 32 && kBQ * ld == 2 * kUpd, "two entries per thread");
     const int t = threadIdx.x;
     for (int col = 0; col < kBQ; ++col) {
-        const int piv = block_pivot(aug, ld, col, sh_piv);
-        if (piv < 0) return false;
-        if (t < ld) {
-            // swap rows col and piv, then divide the pivot row by the pivot
-            const double pv = aug[piv * ld + col];
-            const double a = aug[col * ld + t], b = aug[piv * ld + t];
-            __syncwarp();
-            if (piv != col) aug[piv * ld + t] = a;
-            aug[col * ld + t] = __ddiv_rn(b, pv);
+        if (t < 32) {
+            const int piv = warp_pivot(aug, ld, col);
+            if (t == 0) *sh_piv = piv;
+            if (piv >= 0) {
+                const double pv = aug[piv * ld + col];
+                const double a = aug[col * ld + t], b = aug[piv * ld + t];
+                // column col of every other row once the rows are swapped
+                if (t < kBQ) fcol[t] = t == piv ? aug[col * ld + col] : aug[t * ld + col];
+                __syncwarp();
+                if (piv != col) aug[piv * ld + t] = a;
+                aug[col * ld + t] = __ddiv_rn(b, pv);
+            }
         }
         __syncthreads();
-        if (t < kBQ) fcol[t] = aug[t * ld + col];
-        __syncthreads();
+        if (*sh_piv < 0) return false;
 #pragma unroll
         for (int e = t; e < kBQ * ld; e += kUpd) {
             const int r = e / ld, c = e % ld;
@@ -795,23 +830,36 @@ __global__ void __launch_bounds__(kUpd, 1) k_update_lbfgsb(RelaxDev d, const dou
     __syncthreads();
     // Gauss elimination with partial pivoting on [N | v], the whole CTA taking part; every entry
     // sees the same operations in the same order as a one-lane-per-column elimination
+    // per column, warp 0 finds the pivot, swaps the rows and forms the multipliers (one CTA
+    // barrier), then the CTA eliminates (a second barrier)
     bool ok = true;
     for (int col = 0; col < kBQ; ++col) {
-        const int piv = block_pivot(Nv, ld, col, shi);
-        if (piv < 0) {
+        if (threadIdx.x < 32) {
+            const int piv = warp_pivot(Nv, ld, col);
+            if (threadIdx.x == 0) shi[0] = piv;
+            if (piv >= 0) {
+                if (piv != col) {
+                    double a = 0.0, b = 0.0;
+                    if (threadIdx.x <= kBQ) {
+                        a = Nv[col * ld + threadIdx.x];
+                        b = Nv[piv * ld + threadIdx.x];
+                    }
+                    __syncwarp();
+                    if (threadIdx.x <= kBQ) {
+                        Nv[col * ld + threadIdx.x] = b;
+                        Nv[piv * ld + threadIdx.x] = a;
+                    }
+                    __syncwarp();
+                }
+                if ((int)threadIdx.x > col && threadIdx.x < kBQ)
+                    pv[threadIdx.x] = __ddiv_rn(Nv[threadIdx.x * ld + col], Nv[col * ld + col]);
+            }
+        }
+        __syncthreads();
+        if (shi[0] < 0) {
             ok = false;
             break;
         }
-        if (piv != col && threadIdx.x <= kBQ) {
-            const double a = Nv[col * ld + threadIdx.x], b = Nv[piv * ld + threadIdx.x];
-            __syncwarp(0x1ffffu);  // threads 0 .. kBQ
-            Nv[col * ld + threadIdx.x] = b;
-            Nv[piv * ld + threadIdx.x] = a;
-        }
-        __syncthreads();
-        if ((int)threadIdx.x > col && threadIdx.x < kBQ)
-            pv[threadIdx.x] = __ddiv_rn(Nv[threadIdx.x * ld + col], Nv[col * ld + col]);
-        __syncthreads();
         for (int e = threadIdx.x; e < kBQ * ld; e += kUpd) {
             const int r = e / ld, c = e % ld;
             if (r > col && c >= col) Nv[e] = __dsub_rn(Nv[e], __dmul_rn(pv[r], Nv[col * ld + c]));

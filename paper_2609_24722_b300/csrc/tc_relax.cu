@@ -29,6 +29,14 @@ constexpr int kMaxMem = 16; // largest L-BFGS memory
 // always runs one CTA per problem.
 constexpr int kLargeRows = 16384;
 constexpr int kLargeBlocks = 296;  // CTAs of the grid-wide update launches
+// Resident CTAs per SM of the queued one-CTA L-BFGS update (used when there
+// are more problems than such CTAs).
+#ifndef TC_UPD_PER_SM
+#define TC_UPD_PER_SM 2
+#endif
+constexpr int kUpdPerSm = TC_UPD_PER_SM;
+// Byte offset, in the workspace's counter area, of the update queue's ticket counter.
+constexpr size_t kUpdCtrOff = 64;
 
 struct RelaxDev {
     const Prob* prob;
@@ -75,6 +83,10 @@ struct RelaxDev {
     double2* xc;           // per row: generalized Cauchy point (L-BFGS-B)
     double* bsmall;        // per problem: s.y and s.s of the stored pairs by slot, theta (L-BFGS-B)
     int* any_active;       // one int: some problem still steps (early stop between graph replays)
+    const int32_t* upd_order;  // nullable: problems of the queued L-BFGS update, largest first
+    int upd_n;                 // entries of upd_order
+    int upd_ctas;              // CTAs of the queued update launch
+    unsigned* upd_ctr;         // its ticket counter (zero between launches)
 };
 
 __device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, int64_t row)
@@ -627,12 +639,9 @@ template <int N> __device__ void block_sums_n(double (&v)[N], double (*red)[N])
 // L-BFGS on the wall parameterisation, one CTA per problem.  Same iteration as
 // the host statement: pair test and store, stop test, two-loop recursion
 // (Nocedal & Wright, Alg. 7.4), descent check, max-displacement scaling.
-__global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
-                                                        StepParams sp)
+__device__ void lbfgs_one(const RelaxDev& d, const double2* __restrict__ part_g, const SlotView& v,
+                          const StepParams& sp, const int s, double* sh, double* al)
 {
-    __shared__ double sh[kUpd];
-    __shared__ double al[kMaxMem];
-    const int s = blockIdx.x;
     if (!d.active[s]) return;
     const Prob p = d.prob[s];
     if (p.m > kLargeRows) return;  // updated by the grid-wide sequence below
@@ -802,6 +811,36 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
         d.rms[s] = rms;
         d.hist[s] = hist;
         d.head[s] = head;
+    }
+}
+
+// One CTA per problem (d.upd_order null), or persistent CTAs that take the
+// problems of d.upd_order (largest first) from a queue: a ticket counter that
+// the CTA drawing the last ticket of the launch sets back to zero.  Each
+// problem is stepped by one CTA either way, with the same sums in the same
+// order, so the schedule never changes a result.
+__global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
+                                                        StepParams sp)
+{
+    __shared__ double sh[kUpd];
+    __shared__ double al[kMaxMem];
+    __shared__ unsigned ticket;
+    if (!d.upd_order) {
+        lbfgs_one(d, part_g, v, sp, blockIdx.x, sh, al);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) ticket = atomicAdd(d.upd_ctr, 1u);
+        __syncthreads();
+        const unsigned t = ticket;
+        __syncthreads();
+        if (t >= (unsigned)d.upd_n) {
+            // every CTA draws exactly one ticket >= upd_n; the last of them is drawn last
+            if (threadIdx.x == 0 && t == (unsigned)d.upd_n + gridDim.x - 1) *d.upd_ctr = 0u;
+            return;
+        }
+        lbfgs_one(d, part_g, v, sp, d.upd_order[t], sh, al);
+        __syncthreads();
     }
 }
 
@@ -1377,7 +1416,7 @@ static cudaError_t launch_step(RelaxDev& d, const PassArgs& a, const Plan& P, in
         e = launch_lbfgsb(d, a.part_g, v, sp, st);
         if (e == cudaSuccess && ls && sp.line_search > 0) e = line_search(d, *ls, P, sp, st, launches);
     } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
-        k_update_lbfgs<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
+        k_update_lbfgs<<<d.upd_order ? d.upd_ctas : d.S, kUpd, 0, st>>>(d, a.part_g, v, sp);
         for (size_t q = 0; q < large.ids.size(); ++q) {
             LbArgs la{large.ids[q], large.part, large.sc + q};
             if (e == cudaSuccess) e = lbfgs_large(d, la, a.part_g, v, sp, st);
@@ -1405,7 +1444,7 @@ static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P,
     if (sp.opt == TC_OPT_LBFGSB_TU) {
         launch_lbfgsb(d, a.part_g, v, sm, st);
     } else if (sp.opt == TC_OPT_LBFGS || sp.opt == TC_OPT_LBFGS_TU) {
-        k_update_lbfgs<<<d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
+        k_update_lbfgs<<<d.upd_order ? d.upd_ctas : d.S, kUpd, 0, st>>>(d, a.part_g, v, sm);
         for (size_t q = 0; q < large.ids.size(); ++q) {
             LbArgs la{large.ids[q], large.part, large.sc + q};
             lbfgs_large(d, la, a.part_g, v, sm, st);
@@ -1627,9 +1666,21 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         for (int32_t k = 0; k < n_sub; ++k)
             if (P.prob[k].m > kLargeRows) large.ids.push_back(k);
 
+    // more one-CTA L-BFGS problems than resident update CTAs: persistent CTAs take them largest
+    // first from a queue, so the float64 work of the big problems spreads over the SMs
+    std::vector<int32_t> upd_order;
+    const int upd_ctas = kUpdPerSm * sm_count();
+    if (lbfgs && !boxed && n_sub > upd_ctas) {
+        for (int32_t k = 0; k < n_sub; ++k)
+            if (P.prob[k].m <= kLargeRows) upd_order.push_back(k);
+        std::stable_sort(upd_order.begin(), upd_order.end(),
+                         [&](int32_t a_, int32_t b_) { return P.prob[a_].m > P.prob[b_].m; });
+    }
+
     Carver c;
     fx3* snap3 = nullptr;
     int64_t* bounds_d = nullptr;
+    int32_t* upd_order_d = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
         probd = cv.take<Prob>(n_sub);
@@ -1676,6 +1727,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         part_g = cv.take<double2>(slots * M);
         part1 = cv.take<double>(slots1 * max_m);
         bounds_d = cv.take<int64_t>(wbounds.size());
+        upd_order_d = cv.take<int32_t>(upd_order.size());
     };
     RelaxDev d{};
     Prob* probd;
@@ -1699,6 +1751,12 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     d.st = st;
     d.tu = prm->optimizer == TC_OPT_LBFGS_TU || boxed ? 1 : 0;
     d.boxed = boxed ? 1 : 0;
+    if (!upd_order.empty()) {
+        d.upd_order = upd_order_d;
+        d.upd_n = (int)upd_order.size();
+        d.upd_ctas = upd_ctas;
+        d.upd_ctr = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kUpdCtrOff);
+    }
 
     cudaError_t e = cudaSuccess;
     if (prof) cudaEventRecord(ev_a, s);
@@ -1706,6 +1764,10 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     if (e == cudaSuccess) e = cudaMemcpyAsync(wbd, wbeg.data(), 8 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !wbounds.empty())
         e = cudaMemcpyAsync(bounds_d, wbounds.data(), 8 * wbounds.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !upd_order.empty())
+        e = cudaMemcpyAsync(upd_order_d, upd_order.data(), 4 * upd_order.size(), cudaMemcpyHostToDevice, s);
+    // the queue's counter starts every call at zero, whatever an earlier failed call left
+    if (e == cudaSuccess && d.upd_ctr) e = cudaMemsetAsync(d.upd_ctr, 0, sizeof(unsigned), s);
     // per-problem state: active = ok = 1, counters zero
     std::vector<int> ones(n_sub, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s);

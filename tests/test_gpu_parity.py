@@ -279,6 +279,30 @@ def test_lbfgs_instances_fp64_match_oracle():
         assert abs(r.energy[k].item() - oracle.energy(xo)) <= 1e-12 * oracle.energy(xo)
 
 
+def test_lbfgs_many_instances_queued_update_matches_oracle():
+    """More instances than resident update CTAs: persistent CTAs take the instances, largest first,
+    from a queue.  Every instance must still take every step and follow the oracle's iteration."""
+    rng = np.random.default_rng(5)
+    sizes = rng.integers(8, 81, 700)
+    parts = [synth.arcsine_disk(int(m), 1000 + k) for k, m in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    world = np.stack([off[:-1], off[1:]], 1).astype(np.int64)
+    pos = np.concatenate(parts)
+    iters = 12
+    for rep in range(2):  # the second call reuses the queue counter the first left at zero
+        p = T(pos.copy())
+        r = tc.relax_subdomains(p, world=T(world), precision="fp64", optimizer="lbfgs", n_steps=iters, memory=8,
+                                step0=1e-4, maxstep=0.02, accept=False, want_energy=True)
+        tc.sync_status()
+        assert (r.steps.cpu().numpy() == iters).all()
+        x = p.cpu().numpy()
+        for k in sorted({0, 699, int(np.argmax(sizes)), int(np.argmin(sizes)), 350}):
+            b, e = off[k], off[k + 1]
+            xo, it, rms = oracle.lbfgs(pos[b:e], memory=8, max_iter=iters, gtol=0.0, step0=1e-4, maxstep=0.02)
+            assert np.abs(x[b:e] - xo).max() <= 1e-9
+            assert abs(r.energy[k].item() - oracle.energy(xo)) <= 1e-12 * oracle.energy(xo)
+
+
 def test_lbfgs_large_instance_grid_update_matches_oracle():
     """An instance above 16384 charges takes the grid-wide L-BFGS update; it must follow the oracle."""
     n = 17000
