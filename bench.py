@@ -652,7 +652,8 @@ def main():
         _lib.check(_lib.lib().tc_set_pass_config(_lib.TC_MIXED, args.config), "tc_set_pass_config")
         tuned = {"best": args.config, "shapes": []}
     else:
-        tuned = autotune.tune(n=N, nsub=64, reps=2, seed=rank, cache=None)
+        # on the timed workload's own shape: N charges, N_SUB subdomains of m ~ U{200..5000}
+        tuned = autotune.tune(n=N, nsub=N_SUB, reps=3, seed=rank, cache=None)
 
     pos_np, idx_np, off_np = make_inputs(rank)
     pos0 = torch.tensor(pos_np, device=dev)
