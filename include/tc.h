@@ -65,8 +65,10 @@ typedef enum {
 
 /* Launch shapes of the pair passes (tuning; the paper has no counterpart).
  * Every shape computes the same sums in the same order: a row block of 512
- * charges against tiles of 256 sources; shapes differ in CTA size and rows
- * per thread.  tc_pass_config_count(prec) shapes exist (0 .. count-1);
+ * charges against tiles of 256 sources, the units (row block x tile) cut into
+ * ranges whose number depends on the work and the SM count only (the mixed
+ * passes take the ranges from a queue); shapes differ in CTA size, rows per
+ * thread and CTAs per SM.  tc_pass_config_count(prec) shapes exist (0 .. count-1);
  * tc_set_pass_config selects one for every later call in this process
  * (TC_ERR_INVALID_ARG for an unknown shape); the default is 0.  An autotuner
  * (paper_2609_24722_b300/autotune.py) times the shapes and picks one. */

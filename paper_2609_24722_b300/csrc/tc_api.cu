@@ -13,10 +13,6 @@ namespace tc {
 
 int g_mixed_config = 0;
 
-// Shapes 3 and 4 (4 rows per thread, 128 threads) and 5 (8 rows, 64 threads)
-// skip the second half of a row block's row pairs in far tiles when its rows
-// all lie in its first 256; shapes 0, 1, 2 (2 rows per thread) cannot.
-int mixed_half_rows() { return g_mixed_config >= 3 ? kRB / 2 : 0; }
 
 namespace {
 

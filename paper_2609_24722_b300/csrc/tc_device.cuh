@@ -283,7 +283,13 @@ struct PassArgs {
     const int* active;  // nullable; problems with active[s] == 0 are skipped
     double* part_e;     // [slots x M] row partial energies (or energy changes)
     double2* part_g;    // [slots x M] row partial gradients (nullable)
-    const int64_t* bounds;  // nullable: the CTAs' unit ranges (the mixed pass only), else the equal split
+    const int64_t* bounds;  // nullable: the ranges' units (the mixed pass only), else the equal split
+    // nullable (the mixed pass only): the launch's G ranges are taken in order from this ticket
+    // counter (zero between launches) by `ctas` persistent CTAs instead of one range per CTA;
+    // `ranges` is set to G at the launch
+    unsigned* ticket;
+    int64_t ctas;
+    int64_t ranges;
 };
 
 }  // namespace tc

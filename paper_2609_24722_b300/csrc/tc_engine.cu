@@ -156,6 +156,9 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
         G = want_g ? pass_grid<PASS_F64X, true, true>(P.W) : pass_grid<PASS_F64X, true, false>(P.W);
     else
         G = want_g ? pass_grid<PASS_F64, true, true>(P.W) : pass_grid<PASS_F64, true, false>(P.W);
+    // the mixed pass: ranges from a queue (mixed_ranges), the same for every launch shape
+    const int64_t ctas = G;
+    if (prec == TC_MIXED) G = mixed_ranges(P.W);
     P.G = G;
     P.slots = plan_slots(P.prob, 0, 1, 0, P.W, G);
     const int64_t nb = (n + 255) / 256;
@@ -194,6 +197,9 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
         k_split<<<cb, 256, 0, s>>>(pos2, n, split, st);
         a.rows = split;
         a.snap = split;
+        a.ticket = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kPassCtrOff);
+        a.ctas = ctas;
+        if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "set-up");
         e = want_g ? launch_pass<PASS_MIXED, true, true>(a, G, 0, 0, s)
                    : launch_pass<PASS_MIXED, true, false>(a, G, 0, 0, s);
     } else if (prec == TC_F64X) {

@@ -203,11 +203,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
     __shared__ Prob sprob;
     __shared__ int sprob_s;
 
+    __shared__ unsigned sticket;
+
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t G = gridDim.x;
-    const int64_t k = blockIdx.x;
-    int64_t u = a.bounds ? a.bounds[k] : sk_begin(a.W, G, k);
-    const int64_t u_end = a.bounds ? a.bounds[k + 1] : sk_begin(a.W, G, k + 1);
+    // ranges: one per CTA, or (a.ticket) a.ranges of them taken in order from the ticket counter;
+    // a range's slots depend on the range alone, so no result depends on which CTA takes it
+    const int64_t G = a.ticket ? a.ranges : gridDim.x;
+    int64_t k = blockIdx.x;
 
     MixedRows<R> rs;
     unsigned valid = 0;  // bit c: this thread's c-th staged source is a real charge
@@ -254,6 +256,20 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
         bx = warp_box(bx);
         if (lane == 0) swbox[b][warp] = bx;
     };
+    for (;;) {
+    if (a.ticket) {
+        if (tid == 0) sticket = atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        k = sticket;
+        __syncthreads();
+        if (k >= G) {
+            // every CTA draws exactly one ticket >= G; the last of them is drawn last
+            if (tid == 0 && k == G + gridDim.x - 1) *a.ticket = 0u;
+            break;
+        }
+    }
+    int64_t u = a.bounds ? a.bounds[k] : sk_begin(a.W, G, k);
+    const int64_t u_end = a.bounds ? a.bounds[k + 1] : sk_begin(a.W, G, k + 1);
     while (u < u_end) {
         if (tid == 0) {
             const int s = a.prob ? find_prob(a.prob, a.S, u_base + u) : 0;
@@ -335,6 +351,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
         }
         u += t1 - t0;
         __syncthreads();  // every thread is done with sprob before the next segment rewrites it
+    }
+    if (!a.ticket) break;
     }
 }
 

@@ -58,19 +58,15 @@ inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last
     return best;
 }
 
-// Rows of a row block that the far tiles of the current mixed launch shape
-// still compute when the block's rows all lie in its first half (0: the shape
-// always computes all kRB rows); see the half path of k_pass_mixed.
-int mixed_half_rows();
-
-// CTA bounds for the mixed pass that equalise estimated work instead of unit
+// Range bounds for the mixed pass that equalise estimated work instead of unit
 // counts: a unit of a row block whose rows fit in `half_rows` weighs 3, any
-// other unit 5 (its far tiles, the great majority, compute half the row pairs
-// but load every source; 3 : 5 timed best of 1 : 2, 3 : 5 and equal weights on
-// 256 subdomains at N = 1e5).  CTA k starts at the first unit whose cumulative
-// weight reaches ceil(k Wt / G).
-// Empty (no bounds) unless half_rows > 0, some block qualifies, and every CTA
-// gets at least one unit (W >= 4 G).
+// other unit 5 (the far tiles, the great majority, of the 4- and 8-row launch
+// shapes compute half the row pairs of such a block but load every source;
+// 3 : 5 timed best of 1 : 2, 3 : 5 and equal weights on 256 subdomains at
+// N = 1e5).  The weights do not depend on the launch shape, so neither do the
+// ranges.  Range k starts at the first unit whose cumulative weight reaches
+// ceil(k Wt / G).  Empty (no bounds) unless half_rows > 0, some block
+// qualifies, and every range gets at least one unit (W >= 4 G).
 inline std::vector<int64_t> plan_weighted_bounds(const std::vector<Prob>& ps, int64_t W, int64_t G, int half_rows)
 {
     std::vector<int64_t> b;
@@ -107,6 +103,21 @@ inline std::vector<int64_t> plan_weighted_bounds(const std::vector<Prob>& ps, in
     for (int64_t q = 1; q <= G; ++q)
         if (b[q] <= b[q - 1]) return {};  // an empty range: keep the equal split
     return b;
+}
+
+// Ranges of a mixed pass whose persistent CTAs take them from a queue
+// (PassArgs::ticket): about kDynPerSm per SM, each of at least kDynMinUnits
+// units, and never fewer than min(W, 4 SMs).  The count depends on the work
+// and the SM count only, not on the launch shape, so every shape computes the
+// same per-range sums; the queue keeps the SMs busy when units differ in cost
+// (near tiles, partial row blocks).
+constexpr int kDynPerSm = 64;
+constexpr int64_t kDynMinUnits = 16;
+constexpr size_t kPassCtrOff = 96;  // the queue's ticket counter in the workspace counter area
+inline int64_t mixed_ranges(int64_t W)
+{
+    const int64_t sm = sm_count();
+    return std::max<int64_t>(1, std::max(std::min<int64_t>(W, 4 * sm), std::min<int64_t>(kDynPerSm * sm, W / kDynMinUnits)));
 }
 
 template <class K> inline int64_t grid_for(K kernel, int64_t W)
@@ -221,7 +232,13 @@ inline cudaError_t launch_pass(const PassArgs& a, int64_t G, int64_t u_base, int
     if (a.W <= 0) return cudaSuccess;
     int threads = 0;
     auto fn = pass_kernel<KIND, WANT_E, WANT_G>(&threads);
-    fn<<<(unsigned)G, threads, 0, s>>>(a, u_base, row_sub);
+    if (KIND == PASS_MIXED && a.ticket) {
+        PassArgs b = a;
+        b.ranges = G;
+        fn<<<(unsigned)std::min<int64_t>(a.ctas, G), threads, 0, s>>>(b, u_base, row_sub);
+    } else {
+        fn<<<(unsigned)G, threads, 0, s>>>(a, u_base, row_sub);
+    }
     return cudaGetLastError();
 }
 

@@ -1639,14 +1639,16 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int64_t G_d = pass_grid<PASS_DELTA, false, false>(P.W);
     const bool ls_on = lbfgs && prm->line_search > 0;
     const int64_t G_dm = pass_grid<PASS_DMIX, false, false>(P.W);
-    // the mixed bulk pass may cut its units by estimated work (row blocks that fit in the half
-    // path of the launch shape weigh half)
+    // the mixed bulk pass: its persistent CTAs take ranges from a queue (mixed_ranges), so units of
+    // uneven cost (tiles that turn near as subdomains spread) stay balanced over the SMs; the ranges
+    // are cut by estimated work (units of row blocks whose rows fit in their first half weigh less)
+    const int64_t G_rng = prec == TC_MIXED ? mixed_ranges(P.W) : G_bulk;
     const std::vector<int64_t> wbounds =
-        prec == TC_MIXED ? plan_weighted_bounds(P.prob, P.W, G_bulk, mixed_half_rows()) : std::vector<int64_t>();
+        prec == TC_MIXED ? plan_weighted_bounds(P.prob, P.W, G_rng, kRB / 2) : std::vector<int64_t>();
     int64_t slots = 1;
-    for (int64_t G : {G_bulk, G_f64, G_e, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
+    for (int64_t G : {G_rng, G_f64, G_e, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
     if (!wbounds.empty())
-        slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_bulk, wbounds.data()));
+        slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_rng, wbounds.data()));
     // single-problem passes of the sequential accept
     int64_t slots1 = 1;
     std::vector<int64_t> G1(n_sub);
@@ -1766,8 +1768,10 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         e = cudaMemcpyAsync(bounds_d, wbounds.data(), 8 * wbounds.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !upd_order.empty())
         e = cudaMemcpyAsync(upd_order_d, upd_order.data(), 4 * upd_order.size(), cudaMemcpyHostToDevice, s);
-    // the queue's counter starts every call at zero, whatever an earlier failed call left
+    // the queues' counters start every call at zero, whatever an earlier failed call left
     if (e == cudaSuccess && d.upd_ctr) e = cudaMemsetAsync(d.upd_ctr, 0, sizeof(unsigned), s);
+    unsigned* pass_ctr = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kPassCtrOff);
+    if (e == cudaSuccess && prec == TC_MIXED) e = cudaMemsetAsync(pass_ctr, 0, sizeof(unsigned), s);
     // per-problem state: active = ok = 1, counters zero
     std::vector<int> ones(n_sub, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
@@ -1846,7 +1850,9 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         ab.rows = d.xs;
         ab.snap = snap_split;
         ab.bounds = wbounds.empty() ? nullptr : bounds_d;
-        rs = run_phase<PASS_MIXED>(d, ab, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
+        ab.ticket = pass_ctr;
+        ab.ctas = G_bulk;
+        rs = run_phase<PASS_MIXED>(d, ab, P, G_rng, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
     } else if (prec == TC_F64X) {
         a.rows = d.x3;
         a.snap = snap3;
