@@ -198,7 +198,7 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
         a.rows = split;
         a.snap = split;
         a.ticket = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kPassCtrOff);
-        a.ctas = ctas;
+        a.ctas = mixed_ctas(G, ctas);
         if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "set-up");
         e = want_g ? launch_pass<PASS_MIXED, true, true>(a, G, 0, 0, s)
                    : launch_pass<PASS_MIXED, true, false>(a, G, 0, 0, s);

@@ -106,18 +106,28 @@ inline std::vector<int64_t> plan_weighted_bounds(const std::vector<Prob>& ps, in
 }
 
 // Ranges of a mixed pass whose persistent CTAs take them from a queue
-// (PassArgs::ticket): about kDynPerSm per SM, each of at least kDynMinUnits
-// units, and never fewer than min(W, 4 SMs).  The count depends on the work
-// and the SM count only, not on the launch shape, so every shape computes the
-// same per-range sums; the queue keeps the SMs busy when units differ in cost
-// (near tiles, partial row blocks).
-constexpr int kDynPerSm = 64;
+// (PassArgs::ticket).  The count depends on the work and the SM count only, not
+// on the launch shape, so every shape computes the same per-range sums; the
+// queue keeps the SMs busy when units differ in cost (near tiles, partial row
+// blocks).  It is k x 12 SMs ranges (k = 1 .. 5, ranges of at least
+// kDynMinUnits units where the work allows), so that 3, 4, 5 or 6 resident
+// CTAs per SM take them in whole rounds (mixed_ctas); below 12 SMs units, one
+// range per unit.
 constexpr int64_t kDynMinUnits = 16;
 constexpr size_t kPassCtrOff = 96;  // the queue's ticket counter in the workspace counter area
 inline int64_t mixed_ranges(int64_t W)
 {
-    const int64_t sm = sm_count();
-    return std::max<int64_t>(1, std::max(std::min<int64_t>(W, 4 * sm), std::min<int64_t>(kDynPerSm * sm, W / kDynMinUnits)));
+    const int64_t r0 = 12 * (int64_t)sm_count();
+    if (W <= r0) return std::max<int64_t>(1, W);
+    return std::min<int64_t>(5, std::max<int64_t>(1, W / (kDynMinUnits * r0))) * r0;
+}
+
+// CTAs for `ranges` ranges when at most `ctas_max` are resident: as few rounds
+// of the queue as ctas_max allows, with the ranges spread evenly over them.
+inline int64_t mixed_ctas(int64_t ranges, int64_t ctas_max)
+{
+    const int64_t rounds = (ranges + ctas_max - 1) / ctas_max;
+    return (ranges + rounds - 1) / rounds;
 }
 
 template <class K> inline int64_t grid_for(K kernel, int64_t W)

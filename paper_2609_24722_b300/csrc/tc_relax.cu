@@ -1851,7 +1851,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         ab.snap = snap_split;
         ab.bounds = wbounds.empty() ? nullptr : bounds_d;
         ab.ticket = pass_ctr;
-        ab.ctas = G_bulk;
+        ab.ctas = mixed_ctas(G_rng, G_bulk);
         rs = run_phase<PASS_MIXED>(d, ab, P, G_rng, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
     } else if (prec == TC_F64X) {
         a.rows = d.x3;
