@@ -127,29 +127,6 @@ __host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t W, int64
     return (G * (u + 1) + W - 1) / W - 1;
 }
 
-// A pass may instead cut its units at explicit bounds: CTA k takes units
-// [bounds[k], bounds[k+1]) (bounds[0] = 0, bounds[G] = W, every range non-empty),
-// chosen on the host so that the CTAs get equal estimated work rather than
-// equal unit counts.  The owner of unit u is then the largest k with
-// bounds[k] <= u.
-__host__ __device__ __forceinline__ int64_t bounds_owner(const int64_t* b, int64_t G, int64_t u)
-{
-    int64_t lo = 0, hi = G - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (b[mid] <= u)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-__host__ __device__ __forceinline__ int64_t pass_owner(const int64_t* b, int64_t u, int64_t W, int64_t G)
-{
-    return b ? bounds_owner(b, G, u) : sk_owner(u, W, G);
-}
-
 // One problem of a pass: rows [row_base, row_base + m) of the row arrays move;
 // sources are the snapshot range [snap_b, snap_e) of the configuration (with
 // the problem's own charges masked by mask words [mask_off, ...)) followed by
@@ -283,7 +260,6 @@ struct PassArgs {
     const int* active;  // nullable; problems with active[s] == 0 are skipped
     double* part_e;     // [slots x M] row partial energies (or energy changes)
     double2* part_g;    // [slots x M] row partial gradients (nullable)
-    const int64_t* bounds;  // nullable: the ranges' units (the mixed pass only), else the equal split
     // nullable (the mixed pass only): the launch's G ranges are taken in order from this ticket
     // counter (zero between launches) by `ctas` persistent CTAs instead of one range per CTA;
     // `ranges` is set to G at the launch

@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
             break;
         }
     }
-    int64_t u = a.bounds ? a.bounds[k] : sk_begin(a.W, G, k);
-    const int64_t u_end = a.bounds ? a.bounds[k + 1] : sk_begin(a.W, G, k + 1);
+    int64_t u = sk_begin(a.W, G, k);
+    const int64_t u_end = sk_begin(a.W, G, k + 1);
     while (u < u_end) {
         if (tid == 0) {
             const int s = a.prob ? find_prob(a.prob, a.S, u_base + u) : 0;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
                 if (t + 1 < t1) stage(buf ^ 1);
                 __syncthreads();
             }
-            const int64_t slot = k - pass_owner(a.bounds, sprob.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
+            const int64_t slot = k - sk_owner(sprob.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int64_t rl = rl0 + (int64_t)r * THREADS;

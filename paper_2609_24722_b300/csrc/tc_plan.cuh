@@ -40,10 +40,10 @@ inline void plan_units(Plan& P)
     P.W = u;
 }
 
-// Largest number of CTAs that touch one row block, for G CTAs over units
-// [u_base, u_base + W) of problems `ps`.
+// Largest number of ranges that touch one row block, for G equal ranges over
+// units [u_base, u_base + W) of problems `ps` (the slots a pass needs per row).
 inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last, int64_t u_base, int64_t W,
-                          int64_t G, const int64_t* bounds = nullptr)
+                          int64_t G)
 {
     int64_t best = 1;
     for (size_t s = first; s < last; ++s) {
@@ -51,58 +51,11 @@ inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last
         int64_t n_t = p.n_t_snap + p.n_t_priv;
         for (int64_t rb = 0; rb < p.n_rb; ++rb) {
             int64_t U0 = p.unit_off + rb * n_t - u_base;
-            int64_t c = pass_owner(bounds, U0 + n_t - 1, W, G) - pass_owner(bounds, U0, W, G) + 1;
+            int64_t c = sk_owner(U0 + n_t - 1, W, G) - sk_owner(U0, W, G) + 1;
             best = std::max(best, c);
         }
     }
     return best;
-}
-
-// Range bounds for the mixed pass that equalise estimated work instead of unit
-// counts: a unit of a row block whose rows fit in `half_rows` weighs 3, any
-// other unit 5 (the far tiles, the great majority, of the 4- and 8-row launch
-// shapes compute half the row pairs of such a block but load every source;
-// 3 : 5 timed best of 1 : 2, 3 : 5 and equal weights on 256 subdomains at
-// N = 1e5).  The weights do not depend on the launch shape, so neither do the
-// ranges.  Range k starts at the first unit whose cumulative weight reaches
-// ceil(k Wt / G).  Empty (no bounds) unless half_rows > 0, some block
-// qualifies, and every range gets at least one unit (W >= 4 G).
-inline std::vector<int64_t> plan_weighted_bounds(const std::vector<Prob>& ps, int64_t W, int64_t G, int half_rows)
-{
-    std::vector<int64_t> b;
-    if (half_rows <= 0 || G < 2 || W < 4 * G) return b;
-    int64_t wt = 0;
-    bool any = false;
-    for (const Prob& p : ps) {
-        const int64_t n_t = p.n_t_snap + p.n_t_priv;
-        for (int64_t rb = 0; rb < p.n_rb; ++rb) {
-            const bool light = (int64_t)p.m - rb * kRB <= half_rows;
-            any = any || light;
-            wt += n_t * (light ? 3 : 5);
-        }
-    }
-    if (!any) return b;
-    b.assign(G + 1, W);
-    b[0] = 0;
-    int64_t k = 1, cum = 0;
-    for (const Prob& p : ps) {
-        const int64_t n_t = p.n_t_snap + p.n_t_priv;
-        for (int64_t rb = 0; rb < p.n_rb && k < G; ++rb) {
-            const int64_t w = (int64_t)p.m - rb * kRB <= half_rows ? 3 : 5;
-            const int64_t u0 = p.unit_off + rb * n_t;
-            // CTA k's target weight ceil(k wt / G) falls in this block's units [cum, cum + n_t w)
-            while (k < G) {
-                const int64_t target = (k * wt + G - 1) / G;
-                if (target >= cum + n_t * w) break;
-                b[k] = u0 + (target > cum ? (target - cum + w - 1) / w : 0);
-                ++k;
-            }
-            cum += n_t * w;
-        }
-    }
-    for (int64_t q = 1; q <= G; ++q)
-        if (b[q] <= b[q - 1]) return {};  // an empty range: keep the equal split
-    return b;
 }
 
 // Ranges of a mixed pass whose persistent CTAs take them from a queue
@@ -165,12 +118,11 @@ template <int THREADS> __device__ double block_sum(double v, double* sh)
 }
 
 // Number of slots holding partials of row block rb of problem p.
-__device__ __forceinline__ int64_t slot_count(const Prob& p, int rb, int64_t u_base, int64_t W, int64_t G,
-                                              const int64_t* bounds = nullptr)
+__device__ __forceinline__ int64_t slot_count(const Prob& p, int rb, int64_t u_base, int64_t W, int64_t G)
 {
     int64_t n_t = p.n_t_snap + p.n_t_priv;
     int64_t U0 = p.unit_off + rb * n_t - u_base;
-    return pass_owner(bounds, U0 + n_t - 1, W, G) - pass_owner(bounds, U0, W, G) + 1;
+    return sk_owner(U0 + n_t - 1, W, G) - sk_owner(U0, W, G) + 1;
 }
 
 __device__ __forceinline__ double2 project1(double2 p, double radius, bool pinned)

@@ -37,6 +37,9 @@ constexpr int kLargeBlocks = 296;  // CTAs of the grid-wide update launches
 constexpr int kUpdPerSm = TC_UPD_PER_SM;
 // Byte offset, in the workspace's counter area, of the update queue's ticket counter.
 constexpr size_t kUpdCtrOff = 64;
+// Gradient passes with more slots per row than this are summed by k_sum_slots
+// (every SM) before the update kernels read them.
+constexpr int64_t kPreReduceSlots = 16;
 
 struct RelaxDev {
     const Prob* prob;
@@ -51,6 +54,7 @@ struct RelaxDev {
     float4* xs;            // per row: hi/lo split of x
     fx3* x3;               // per row: three-part split of x (float64-grade float32 pass), nullable
     double2* g;            // per row: reduced dE/dx
+    double2* g_red;        // per row: the pass's slots summed (k_sum_slots), nullable
     double2* xp;           // per row: previous x (BB) / previous z (L-BFGS)
     double2* gp;           // per row: previous g (BB) / current dE/dz (L-BFGS)
     double2* z;            // per row: L-BFGS variable
@@ -105,12 +109,13 @@ __device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, 
 // Row partial of one pass: sum of its slots in order (float64, compensated for e).
 struct SlotView {
     int64_t W, G, u_base, stride, row_sub;
-    const int64_t* bounds = nullptr;  // the pass's CTA bounds when it used explicit ones
+    const double2* red = nullptr;     // nullable: the rows' gradients already summed (k_sum_slots)
 };
 
 __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double2* part_g, const SlotView& v)
 {
-    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G, v.bounds);
+    if (v.red) return v.red[p.row_base + rl - v.row_sub];
+    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
     double gx = 0.0, gy = 0.0;
     int64_t o = p.row_base + rl - v.row_sub;
     for (int64_t k = 0; k < c; ++k) {
@@ -123,7 +128,7 @@ __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double
 
 __device__ __forceinline__ double sum_e(const Prob& p, int64_t rl, const double* part_e, const SlotView& v)
 {
-    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G, v.bounds);
+    int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
     double hi = 0.0, lo = 0.0;
     int64_t o = p.row_base + rl - v.row_sub;
     for (int64_t k = 0; k < c; ++k) dd_add(hi, lo, part_e[k * v.stride + o]);
@@ -297,7 +302,19 @@ struct StepParams {
     double step0, alpha_min, alpha_max, maxstep, gtol, radius;
     int measure;  // 1: only record the RMS stationarity of the current rows (no step)
     int line_search = 0;  // L-BFGS: at most this many Armijo halvings per step (0: none)
+    int pre_reduce = 0;   // host: sum the pass's slots over all SMs first (k_sum_slots)
 };
+
+// Each row's gradient partials summed in slot order (sum_g) into d.g_red, over
+// every SM, for passes with many slots per row: the update kernels, which run
+// on few CTAs, then read one value per row.  The sums are those sum_g forms.
+__global__ void k_sum_slots(RelaxDev d, const double2* __restrict__ part_g, SlotView v)
+{
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < d.M; rr += (int64_t)gridDim.x * blockDim.x) {
+        const Prob p = d.prob[find_row_prob(d.prob, d.S, rr)];
+        d.g_red[rr] = sum_g(p, rr - p.row_base, part_g, v);
+    }
+}
 
 // Projected gradient descent (fixed or Barzilai-Borwein step), one CTA per problem.
 __global__ void __launch_bounds__(kUpd) k_update_gdbb(RelaxDev d, const double2* __restrict__ part_g, SlotView v,
@@ -1408,9 +1425,15 @@ static cudaError_t launch_step(RelaxDev& d, const PassArgs& a, const Plan& P, in
                                cudaStream_t st, int& launches, const LargeSet& large, const LsArgs* ls,
                                cudaEvent_t ev_mid)
 {
-    const SlotView v{P.W, G, 0, P.M, 0, a.bounds};
+    SlotView v{P.W, G, 0, P.M, 0};
     cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
     if (e != cudaSuccess) return e;
+    if (sp.pre_reduce && a.W > 0) {
+        k_sum_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.M + 255) / 256, 8L * sm_count())), 256, 0, st>>>(
+            d, a.part_g, v);
+        v.red = d.g_red;
+        ++launches;
+    }
     if (ev_mid && (e = cudaEventRecord(ev_mid, st)) != cudaSuccess) return e;
     if (sp.opt == TC_OPT_LBFGSB_TU) {
         e = launch_lbfgsb(d, a.part_g, v, sp, st);
@@ -1436,9 +1459,15 @@ template <int KIND>
 static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P, int64_t G, const StepParams& sp,
                                   cudaStream_t st, int& launches, const LargeSet& large)
 {
-    const SlotView v{P.W, G, 0, P.M, 0, a.bounds};
+    SlotView v{P.W, G, 0, P.M, 0};
     cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
     if (e != cudaSuccess) return e;
+    if (sp.pre_reduce && a.W > 0) {
+        k_sum_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.M + 255) / 256, 8L * sm_count())), 256, 0, st>>>(
+            d, a.part_g, v);
+        v.red = d.g_red;
+        ++launches;
+    }
     StepParams sm = sp;
     sm.measure = 1;
     if (sp.opt == TC_OPT_LBFGSB_TU) {
@@ -1639,16 +1668,15 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int64_t G_d = pass_grid<PASS_DELTA, false, false>(P.W);
     const bool ls_on = lbfgs && prm->line_search > 0;
     const int64_t G_dm = pass_grid<PASS_DMIX, false, false>(P.W);
-    // the mixed bulk pass: its persistent CTAs take ranges from a queue (mixed_ranges), so units of
-    // uneven cost (tiles that turn near as subdomains spread) stay balanced over the SMs; the ranges
-    // are cut by estimated work (units of row blocks whose rows fit in their first half weigh less)
+    // the mixed bulk pass: its persistent CTAs take equal ranges from a queue (mixed_ranges), so
+    // units of uneven cost (tiles that turn near as subdomains spread, partial row blocks) stay
+    // balanced over the SMs
     const int64_t G_rng = prec == TC_MIXED ? mixed_ranges(P.W) : G_bulk;
-    const std::vector<int64_t> wbounds =
-        prec == TC_MIXED ? plan_weighted_bounds(P.prob, P.W, G_rng, kRB / 2) : std::vector<int64_t>();
     int64_t slots = 1;
     for (int64_t G : {G_rng, G_f64, G_e, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
-    if (!wbounds.empty())
-        slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_rng, wbounds.data()));
+    // phases whose gradient passes leave many slots per row sum them over every SM before the update
+    const bool pre_bulk = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_rng) > kPreReduceSlots;
+    const bool pre_polish = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_f64) > kPreReduceSlots;
     // single-problem passes of the sequential accept
     int64_t slots1 = 1;
     std::vector<int64_t> G1(n_sub);
@@ -1681,7 +1709,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
 
     Carver c;
     fx3* snap3 = nullptr;
-    int64_t* bounds_d = nullptr;
     int32_t* upd_order_d = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
@@ -1693,6 +1720,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         d.x3 = use_x ? cv.take<fx3>(M) : nullptr;
         snap3 = cv.take<fx3>(use_x && !inst ? n : 0);
         d.g = cv.take<double2>(M);
+        d.g_red = cv.take<double2>(pre_bulk || pre_polish ? M : 0);
         d.xp = cv.take<double2>(M);
         d.gp = cv.take<double2>(M);
         d.z = cv.take<double2>(lbfgs ? M : 0);
@@ -1728,7 +1756,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         part_e = cv.take<double>(slots * M);
         part_g = cv.take<double2>(slots * M);
         part1 = cv.take<double>(slots1 * max_m);
-        bounds_d = cv.take<int64_t>(wbounds.size());
         upd_order_d = cv.take<int32_t>(upd_order.size());
     };
     RelaxDev d{};
@@ -1764,8 +1791,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     if (prof) cudaEventRecord(ev_a, s);
     e = cudaMemcpyAsync(probd, P.prob.data(), sizeof(Prob) * n_sub, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(wbd, wbeg.data(), 8 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !wbounds.empty())
-        e = cudaMemcpyAsync(bounds_d, wbounds.data(), 8 * wbounds.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !upd_order.empty())
         e = cudaMemcpyAsync(upd_order_d, upd_order.data(), 4 * upd_order.size(), cudaMemcpyHostToDevice, s);
     // the queues' counters start every call at zero, whatever an earlier failed call left
@@ -1828,6 +1853,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     a.part_g = part_g;
     StepParams sp{prm->optimizer, mem, prm->step0, prm->alpha_min, prm->alpha_max, prm->maxstep, prm->gtol, prm->radius, 0};
     sp.line_search = ls_on ? prm->line_search : 0;
+    sp.pre_reduce = pre_bulk ? 1 : 0;
     // energy-change passes of the line search: float32 difference form in the mixed phase,
     // float64 pair differences otherwise (rows: rows8 / rows4; snapshot as the relaxation's)
     LsArgs ls_mixed, ls_f64;
@@ -1849,7 +1875,6 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         PassArgs ab = a;
         ab.rows = d.xs;
         ab.snap = snap_split;
-        ab.bounds = wbounds.empty() ? nullptr : bounds_d;
         ab.ticket = pass_ctr;
         ab.ctas = mixed_ctas(G_rng, G_bulk);
         rs = run_phase<PASS_MIXED>(d, ab, P, G_rng, sp, prm->n_steps, s, prof, launches, large, &ls_mixed);
@@ -1868,6 +1893,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         if (cudaError_t e_ = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s); e_ != cudaSuccess) return cuda_fail(e_, "cudaMemcpyAsync");
         StepParams sp2 = sp;
         sp2.gtol = prm->polish_gtol;
+        sp2.pre_reduce = pre_polish ? 1 : 0;
         if (polish_x) {
             a.rows = d.x3;
             a.snap = snap3;
