@@ -260,12 +260,21 @@ struct PassArgs {
     const int* active;  // nullable; problems with active[s] == 0 are skipped
     double* part_e;     // [slots x M] row partial energies (or energy changes)
     double2* part_g;    // [slots x M] row partial gradients (nullable)
-    // nullable (the mixed pass only): the launch's G ranges are taken in order from this ticket
-    // counter (zero between launches) by `ctas` persistent CTAs instead of one range per CTA;
-    // `ranges` is set to G at the launch
+    // nullable (the mixed and float64 passes): the launch's G ranges are taken in order from this
+    // ticket counter (zero between launches) by `ctas` persistent CTAs instead of one range per
+    // CTA; `ranges` is set to G at the launch
     unsigned* ticket;
     int64_t ctas;
     int64_t ranges;
+    // float64 pass, problems without snapshot tiles (all pairs of a world): 1 = each unordered pair
+    // once.  Row block rb covers the problem's own tiles 2 rb and 2 rb + 1; units of earlier tiles
+    // do nothing, those two tiles are computed as usual (every ordered pair, rows only), and a
+    // later tile t adds each pair's terms to the row and to the source: the source sums of unit
+    // (rb, t) go to col_e / col_g[rb * col_stride + row - row_sub] for the rows of tile t.
+    int sym;
+    double* col_e;
+    double2* col_g;
+    int64_t col_stride;
 };
 
 }  // namespace tc

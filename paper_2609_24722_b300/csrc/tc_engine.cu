@@ -52,11 +52,14 @@ __global__ void k_check(const double2* __restrict__ pos, int64_t n, int* st)
     }
 }
 
-// Finish of the all-pairs pass: per row, add the slots in order; write grad
-// and local energies; the last block adds the block energies in order.
+// Finish of the all-pairs pass: per row, add the slots in order, then (after a
+// symmetric float64 pass, col_e non-null) the source sums that row blocks
+// rb < t / 2 left for the row's tile t, in order of rb; write grad and local
+// energies; the last block adds the block energies in order.
 template <bool WANT_G>
 __global__ void k_finish_allpairs(Prob p, int64_t W, int64_t G, const double* __restrict__ part_e,
-                                  const double2* __restrict__ part_g, double2* __restrict__ grad,
+                                  const double2* __restrict__ part_g, const double* __restrict__ col_e,
+                                  const double2* __restrict__ col_g, double2* __restrict__ grad,
                                   double* __restrict__ local_e, double* __restrict__ block_e,
                                   unsigned* __restrict__ counter, double* __restrict__ energy, int* st)
 {
@@ -76,6 +79,17 @@ __global__ void k_finish_allpairs(Prob p, int64_t W, int64_t G, const double* __
                 double2 q = part_g[s * n + i];
                 gx += q.x;
                 gy += q.y;
+            }
+        }
+        if (col_e) {
+            const int64_t nb = i / kT / 2;
+            for (int64_t b = 0; b < nb; ++b) {
+                dd_add(eh, el, col_e[b * n + i]);
+                if (WANT_G) {
+                    const double2 q = col_g[b * n + i];
+                    gx += q.x;
+                    gy += q.y;
+                }
             }
         }
         e = eh + el;
@@ -156,12 +170,16 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
         G = want_g ? pass_grid<PASS_F64X, true, true>(P.W) : pass_grid<PASS_F64X, true, false>(P.W);
     else
         G = want_g ? pass_grid<PASS_F64, true, true>(P.W) : pass_grid<PASS_F64, true, false>(P.W);
-    // the mixed pass: ranges from a queue (mixed_ranges), the same for every launch shape
+    // the mixed and float64 passes: ranges from a queue (mixed_ranges), the same for every launch
+    // shape; the float64 pass takes each unordered pair once when its source sums (24 bytes per
+    // charge and row block) fit 2 GiB
     const int64_t ctas = G;
-    if (prec == TC_MIXED) G = mixed_ranges(P.W);
+    const bool sym = prec == TC_FP64 && (int64_t)P.prob[0].n_rb * n * 24 <= (int64_t(2) << 30);
+    if (prec == TC_MIXED || sym) G = mixed_ranges(P.W);
     P.G = G;
     P.slots = plan_slots(P.prob, 0, 1, 0, P.W, G);
     const int64_t nb = (n + 255) / 256;
+    const int64_t ncol = sym ? (int64_t)P.prob[0].n_rb * n : 0;
 
     Carver c;
     c.take<float4>(prec == TC_MIXED ? n : 0);
@@ -169,6 +187,8 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
     c.take<double>(P.slots * n);
     c.take<double2>(want_g ? P.slots * n : 0);
     c.take<double>(nb);
+    c.take<double>(ncol);
+    c.take<double2>(want_g ? ncol : 0);
     void* ws = workspace(s, c.off, &err);
     if (!ws) return err;
     c.base = static_cast<char*>(ws);
@@ -178,6 +198,8 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
     double* part_e = c.take<double>(P.slots * n);
     double2* part_g = c.take<double2>(want_g ? P.slots * n : 0);
     double* block_e = c.take<double>(nb);
+    double* col_e = sym ? c.take<double>(ncol) : nullptr;
+    double2* col_g = sym && want_g ? c.take<double2>(ncol) : nullptr;
     unsigned* counter = reinterpret_cast<unsigned*>(ws);
 
     PassArgs a{};
@@ -212,17 +234,27 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
         k_check<<<cb, 256, 0, s>>>(pos2, n, st);
         a.rows = pos2;
         a.snap = pos2;
+        if (sym) {
+            a.sym = 1;
+            a.col_e = col_e;
+            a.col_g = col_g;
+            a.col_stride = n;
+            a.ticket = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kPassCtrOff);
+            a.ctas = mixed_ctas(G, want_g ? pass_grid<PASS_F64, true, true, true>(P.W)
+                                          : pass_grid<PASS_F64, true, false, true>(P.W));
+            if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "set-up");
+        }
         e = want_g ? launch_pass<PASS_F64, true, true>(a, G, 0, 0, s)
                    : launch_pass<PASS_F64, true, false>(a, G, 0, 0, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "set-up");
     if (want_g)
-        k_finish_allpairs<true><<<(unsigned)nb, 256, 0, s>>>(P.prob[0], P.W, G, part_e, part_g,
+        k_finish_allpairs<true><<<(unsigned)nb, 256, 0, s>>>(P.prob[0], P.W, G, part_e, part_g, col_e, col_g,
                                                              reinterpret_cast<double2*>(grad), local_e, block_e,
                                                              counter, energy, st);
     else
-        k_finish_allpairs<false><<<(unsigned)nb, 256, 0, s>>>(P.prob[0], P.W, G, part_e, nullptr, nullptr, local_e,
-                                                              block_e, counter, energy, st);
+        k_finish_allpairs<false><<<(unsigned)nb, 256, 0, s>>>(P.prob[0], P.W, G, part_e, nullptr, col_e, nullptr,
+                                                              nullptr, local_e, block_e, counter, energy, st);
     return cuda_status(cudaGetLastError());
 }
 

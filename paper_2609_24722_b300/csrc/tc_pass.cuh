@@ -64,6 +64,56 @@ template <int R> struct RowState<PASS_F64, R> {
         }
     }
 
+    // One chunk of 32 sources that lie after the row block, each unordered pair
+    // once: lane l pairs its rows with source (l + k) mod 32 at step k, adds the
+    // terms to its rows (as tile()) and the opposite gradient and the same
+    // 1/r to the source's sums (ax, ay, ae), and then takes lane l + 1's source
+    // sums, which belong to its next source.  After the 32 steps lane l holds
+    // the sums of source l of the chunk (over this warp's rows).  et collects
+    // the rows' 1/r sums of the tile.
+    template <bool WANT_E, bool WANT_G>
+    __device__ __forceinline__ void chunk_sym(const double2* __restrict__ s, double& ax, double& ay, double& ae,
+                                              double (&et)[R])
+    {
+        const int lane = threadIdx.x & 31;
+        const int next = (lane + 1) & 31;
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const double2 q = s[(lane + k) & 31];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const double dx = x[r] - q.x;
+                const double dy = y[r] - q.y;
+                const double r2 = fma(dx, dx, dy * dy);
+                const double inv = rsqrt64(r2);
+                if (WANT_E) {
+                    et[r] += inv;
+                    ae += inv;
+                }
+                if (WANT_G) {
+                    const double inv3 = inv * inv * inv;
+                    gx[r] = fma(-dx, inv3, gx[r]);
+                    gy[r] = fma(-dy, inv3, gy[r]);
+                    ax = fma(dx, inv3, ax);
+                    ay = fma(dy, inv3, ay);
+                }
+            }
+            if (WANT_G) {
+                ax = __shfl_sync(0xffffffffu, ax, next);
+                ay = __shfl_sync(0xffffffffu, ay, next);
+            }
+            if (WANT_E) ae = __shfl_sync(0xffffffffu, ae, next);
+        }
+    }
+
+    template <bool WANT_E> __device__ __forceinline__ void add_energy(const double (&et)[R], double escale)
+    {
+        if (WANT_E) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) dd_add(eh[r], el[r], et[r] * escale);
+        }
+    }
+
     __device__ double e(int r) const { return eh[r] + el[r]; }
     __device__ double2 g(int r) const { return make_double2(gx[r], gy[r]); }
 };
@@ -343,37 +393,61 @@ __device__ __forceinline__ typename SrcT<KIND>::type load_src(const PassArgs& a,
 }
 
 // The pass.  Grid: persistent CTAs (any count); each takes units
-// [u_base + b_k, u_base + b_{k+1}) of the W units starting at u_base.
-// Row partials go to part_e/part_g[slot * M + row - row_sub].
-template <int KIND, int R, int THREADS, bool WANT_E, bool WANT_G>
+// [u_base + b_k, u_base + b_{k+1}) of the W units starting at u_base, or (a.ticket)
+// the ranges k drawn from the ticket counter.  Row partials go to
+// part_e/part_g[slot * M + row - row_sub]; with a.sym (float64), source sums of
+// the later tiles go to col_e/col_g (PassArgs).
+template <int KIND, int R, int THREADS, bool WANT_E, bool WANT_G, bool SYM = false>
 __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, int64_t row_sub)
 {
     constexpr int T = THREADS;
     constexpr int RB = THREADS * R;
+    constexpr int NW = THREADS / 32;
     using src_t = typename SrcT<KIND>::type;  // rows use the same entry type as sources
     __shared__ src_t tile[2][T];
+    constexpr bool SYM_OK = SYM && KIND == PASS_F64 && RB == 2 * T;
+    __shared__ double csum[SYM_OK ? 3 : 1][SYM_OK ? NW : 1][32];  // per warp: a chunk's source sums
+    __shared__ unsigned sticket;
 
-    const int tid = threadIdx.x;
-    const int64_t G = gridDim.x;
-    const int64_t k = blockIdx.x;
-    int64_t u = sk_begin(a.W, G, k);
-    const int64_t u_end = sk_begin(a.W, G, k + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t G = a.ticket ? a.ranges : gridDim.x;
+    int64_t k = blockIdx.x;
 
     RowState<KIND, R> rs;
+    for (;;) {
+    if (a.ticket) {
+        if (tid == 0) sticket = atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        k = sticket;
+        __syncthreads();
+        if (k >= G) {
+            // every CTA draws exactly one ticket >= G; the last of them is drawn last
+            if (tid == 0 && k == G + gridDim.x - 1) *a.ticket = 0u;
+            break;
+        }
+    }
+    int64_t u = sk_begin(a.W, G, k);
+    const int64_t u_end = sk_begin(a.W, G, k + 1);
     while (u < u_end) {
         const int s = a.prob ? find_prob(a.prob, a.S, u_base + u) : 0;
         const Prob p = a.prob ? a.prob[s] : a.single;
         const int n_t = p.n_t_snap + p.n_t_priv;
         const int64_t local = u_base + u - p.unit_off;
         const int rb = (int)(local / n_t);
-        const int t0 = (int)(local % n_t);
-        const int t1 = (int)min((int64_t)n_t, (int64_t)t0 + (u_end - u));
+        const int t1 = (int)min((int64_t)n_t, (int64_t)(local % n_t) + (u_end - u));
+        const int tu = (int)(local % n_t);  // the segment's first unit
+        // symmetric float64 pass: the tiles before the row block's own ones do nothing
+        const bool sym = SYM_OK && a.sym;
+        const int t0 = sym ? max(tu, 2 * rb) : tu;
         const bool act = (a.active == nullptr) || (a.active[s] != 0);
         if (act) {
             const int64_t rl0 = (int64_t)rb * RB + tid;
             rs.load(static_cast<const src_t*>(a.rows), p.row_base, rl0, THREADS, p.m);
-            src_t pre = load_src<KIND, T>(a, p, t0, tid);
-            tile[0][tid] = pre;
+            src_t pre{};
+            if (t0 < t1) {
+                pre = load_src<KIND, T>(a, p, t0, tid);
+                tile[0][tid] = pre;
+            }
             __syncthreads();
             for (int t = t0; t < t1; ++t) {
                 const int buf = (t - t0) & 1;
@@ -393,6 +467,42 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
                         rs.template tile<T, true, true>(tile[buf], jself, (sc_t)sc);
                     else
                         rs.template tile<T, false, true>(tile[buf], jself, (sc_t)sc);
+                } else if constexpr (SYM_OK) {
+                    if (sym && tp >= 2 * rb + 2) {
+                        // a later tile: each pair once, the source sums per chunk of 32 sources
+                        double et[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) et[r] = 0.0;
+                        for (int c = 0; c < T / 32; ++c) {
+                            double ax = 0.0, ay = 0.0, ae = 0.0;
+                            rs.template chunk_sym<WANT_E, WANT_G>(tile[buf] + c * 32, ax, ay, ae, et);
+                            csum[0][warp][lane] = ax;
+                            csum[1][warp][lane] = ay;
+                            csum[2][warp][lane] = ae;
+                            __syncthreads();
+                            if (tid < 32) {
+                                double sx = 0.0, sy = 0.0, se = 0.0;
+#pragma unroll
+                                for (int w = 0; w < NW; ++w) {
+                                    sx += csum[0][w][tid];
+                                    sy += csum[1][w][tid];
+                                    se += csum[2][w][tid];
+                                }
+                                const int64_t j = (int64_t)tp * T + c * 32 + tid;
+                                if (j < p.m) {
+                                    const int64_t o = (int64_t)rb * a.col_stride + p.row_base + j - row_sub;
+                                    if (WANT_E) a.col_e[o] = se * sc;
+                                    if (WANT_G) a.col_g[o] = make_double2(sx, sy);
+                                }
+                            }
+                            __syncthreads();
+                        }
+                        rs.template add_energy<WANT_E>(et, sc);
+                    } else if (self) {
+                        rs.template tile<T, true, WANT_E, WANT_G>(tile[buf], jself, sc);
+                    } else {
+                        rs.template tile<T, false, WANT_E, WANT_G>(tile[buf], jself, sc);
+                    }
                 } else {
                     if (self)
                         rs.template tile<T, true, WANT_E, WANT_G>(tile[buf], jself, (float)sc);
@@ -417,7 +527,10 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
                 }
             }
         }
-        u += t1 - t0;
+        u += t1 - tu;
+        __syncthreads();  // the next segment's first tile overwrites tile[0]
+    }
+    if (!a.ticket) break;
     }
 }
 

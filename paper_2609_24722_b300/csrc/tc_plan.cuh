@@ -178,13 +178,14 @@ template <bool WANT_E, bool WANT_G> struct MixedShape {
     }
 };
 
-template <int KIND, bool WANT_E, bool WANT_G> inline auto pass_kernel(int* threads)
+// SYM: the float64 kernel with the symmetric (PassArgs::sym) path compiled in.
+template <int KIND, bool WANT_E, bool WANT_G, bool SYM = false> inline auto pass_kernel(int* threads)
 {
     if constexpr (KIND == PASS_MIXED) {
         return MixedShape<WANT_E, WANT_G>::kernel(g_mixed_config, threads);
     } else {
         *threads = kThreads;
-        return k_pass<KIND, kR, kThreads, WANT_E, WANT_G>;
+        return k_pass<KIND, kR, kThreads, WANT_E, WANT_G, SYM && KIND == PASS_F64>;
     }
 }
 
@@ -194,7 +195,8 @@ inline cudaError_t launch_pass(const PassArgs& a, int64_t G, int64_t u_base, int
     if (a.W <= 0) return cudaSuccess;
     int threads = 0;
     auto fn = pass_kernel<KIND, WANT_E, WANT_G>(&threads);
-    if (KIND == PASS_MIXED && a.ticket) {
+    if (KIND == PASS_F64 && a.sym) fn = pass_kernel<KIND, WANT_E, WANT_G, true>(&threads);
+    if ((KIND == PASS_MIXED || KIND == PASS_F64) && a.ticket) {
         PassArgs b = a;
         b.ranges = G;
         fn<<<(unsigned)std::min<int64_t>(a.ctas, G), threads, 0, s>>>(b, u_base, row_sub);
@@ -204,10 +206,10 @@ inline cudaError_t launch_pass(const PassArgs& a, int64_t G, int64_t u_base, int
     return cudaGetLastError();
 }
 
-template <int KIND, bool WANT_E, bool WANT_G> inline int64_t pass_grid(int64_t W)
+template <int KIND, bool WANT_E, bool WANT_G, bool SYM = false> inline int64_t pass_grid(int64_t W)
 {
     int threads = 0;
-    auto fn = pass_kernel<KIND, WANT_E, WANT_G>(&threads);
+    auto fn = pass_kernel<KIND, WANT_E, WANT_G, SYM>(&threads);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess || occ < 1) {
         cudaGetLastError();

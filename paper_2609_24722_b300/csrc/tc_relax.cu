@@ -40,6 +40,9 @@ constexpr size_t kUpdCtrOff = 64;
 // Gradient passes with more slots per row than this are summed by k_sum_slots
 // (every SM) before the update kernels read them.
 constexpr int64_t kPreReduceSlots = 16;
+// Instances take their float64 passes symmetric (each unordered pair once,
+// PassArgs::sym) when the source sums, 24 bytes per row and row block, fit this.
+constexpr int64_t kSymBytes = int64_t(2) << 30;
 
 struct RelaxDev {
     const Prob* prob;
@@ -106,10 +109,15 @@ __device__ __forceinline__ int find_row_prob(const Prob* __restrict__ P, int S, 
     return lo;
 }
 
-// Row partial of one pass: sum of its slots in order (float64, compensated for e).
+// Row partial of one pass: sum of its slots in order (float64, compensated for e),
+// then, after a symmetric float64 pass, the source sums that the earlier row
+// blocks rb < t / 2 left for the row's tile t, in order of rb.
 struct SlotView {
     int64_t W, G, u_base, stride, row_sub;
     const double2* red = nullptr;     // nullable: the rows' gradients already summed (k_sum_slots)
+    const double2* colg = nullptr;    // nullable: source sums of a symmetric pass (PassArgs::col_g)
+    const double* cole = nullptr;     // nullable: the same for 1/r (PassArgs::col_e)
+    int64_t col_stride = 0;
 };
 
 __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double2* part_g, const SlotView& v)
@@ -123,6 +131,14 @@ __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double
         gx += q.x;
         gy += q.y;
     }
+    if (v.colg) {
+        const int64_t nb = rl / kT / 2;
+        for (int64_t b = 0; b < nb; ++b) {
+            const double2 q = v.colg[b * v.col_stride + o];
+            gx += q.x;
+            gy += q.y;
+        }
+    }
     return make_double2(gx, gy);
 }
 
@@ -132,7 +148,23 @@ __device__ __forceinline__ double sum_e(const Prob& p, int64_t rl, const double*
     double hi = 0.0, lo = 0.0;
     int64_t o = p.row_base + rl - v.row_sub;
     for (int64_t k = 0; k < c; ++k) dd_add(hi, lo, part_e[k * v.stride + o]);
+    if (v.cole) {
+        const int64_t nb = rl / kT / 2;
+        for (int64_t b = 0; b < nb; ++b) dd_add(hi, lo, v.cole[b * v.col_stride + o]);
+    }
     return hi + lo;
+}
+
+// The reduction view of a gradient/energy pass launched with `a` over G ranges.
+__host__ inline SlotView pass_view(const PassArgs& a, int64_t W, int64_t G, int64_t M)
+{
+    SlotView v{W, G, 0, M, 0};
+    if (a.sym) {
+        v.colg = a.col_g;
+        v.cole = a.col_e;
+        v.col_stride = a.col_stride;
+    }
+    return v;
 }
 
 // Deterministic block reductions of several doubles at once.
@@ -1425,7 +1457,7 @@ static cudaError_t launch_step(RelaxDev& d, const PassArgs& a, const Plan& P, in
                                cudaStream_t st, int& launches, const LargeSet& large, const LsArgs* ls,
                                cudaEvent_t ev_mid)
 {
-    SlotView v{P.W, G, 0, P.M, 0};
+    SlotView v = pass_view(a, P.W, G, P.M);
     cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
     if (e != cudaSuccess) return e;
     if (sp.pre_reduce && a.W > 0) {
@@ -1459,7 +1491,7 @@ template <int KIND>
 static cudaError_t launch_measure(RelaxDev& d, const PassArgs& a, const Plan& P, int64_t G, const StepParams& sp,
                                   cudaStream_t st, int& launches, const LargeSet& large)
 {
-    SlotView v{P.W, G, 0, P.M, 0};
+    SlotView v = pass_view(a, P.W, G, P.M);
     cudaError_t e = launch_pass<KIND, false, true>(a, G, 0, 0, st);
     if (e != cudaSuccess) return e;
     if (sp.pre_reduce && a.W > 0) {
@@ -1671,12 +1703,19 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     // the mixed bulk pass: its persistent CTAs take equal ranges from a queue (mixed_ranges), so
     // units of uneven cost (tiles that turn near as subdomains spread, partial row blocks) stay
     // balanced over the SMs
-    const int64_t G_rng = prec == TC_MIXED ? mixed_ranges(P.W) : G_bulk;
+    // instances: the float64 passes take each unordered pair once and their ranges from the queue
+    int64_t rb_max = 0;
+    for (const Prob& p : P.prob) rb_max = std::max<int64_t>(rb_max, p.n_rb);
+    const bool sym = inst && rb_max * P.M * 24 <= kSymBytes;
+    const int64_t G_sym = sym ? mixed_ranges(P.W) : 0;
+    const int64_t G_rng = prec == TC_MIXED ? mixed_ranges(P.W) : (sym && prec == TC_FP64 ? G_sym : G_bulk);
+    const int64_t G_pol = sym && !polish_x ? G_sym : G_f64;
+    const int64_t G_en = sym ? G_sym : G_e;
     int64_t slots = 1;
-    for (int64_t G : {G_rng, G_f64, G_e, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
+    for (int64_t G : {G_rng, G_pol, G_en, G_d, G_dm}) slots = std::max(slots, plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G));
     // phases whose gradient passes leave many slots per row sum them over every SM before the update
     const bool pre_bulk = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_rng) > kPreReduceSlots;
-    const bool pre_polish = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_f64) > kPreReduceSlots;
+    const bool pre_polish = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_pol) > kPreReduceSlots;
     // single-problem passes of the sequential accept
     int64_t slots1 = 1;
     std::vector<int64_t> G1(n_sub);
@@ -1710,6 +1749,8 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     Carver c;
     fx3* snap3 = nullptr;
     int32_t* upd_order_d = nullptr;
+    double2* col_g = nullptr;
+    double* col_e = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
         probd = cv.take<Prob>(n_sub);
@@ -1721,6 +1762,8 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         snap3 = cv.take<fx3>(use_x && !inst ? n : 0);
         d.g = cv.take<double2>(M);
         d.g_red = cv.take<double2>(pre_bulk || pre_polish ? M : 0);
+        col_g = cv.take<double2>(sym ? (size_t)(rb_max * M) : 0);
+        col_e = cv.take<double>(sym ? (size_t)(rb_max * M) : 0);
         d.xp = cv.take<double2>(M);
         d.gp = cv.take<double2>(M);
         d.z = cv.take<double2>(lbfgs ? M : 0);
@@ -1796,7 +1839,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     // the queues' counters start every call at zero, whatever an earlier failed call left
     if (e == cudaSuccess && d.upd_ctr) e = cudaMemsetAsync(d.upd_ctr, 0, sizeof(unsigned), s);
     unsigned* pass_ctr = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kPassCtrOff);
-    if (e == cudaSuccess && prec == TC_MIXED) e = cudaMemsetAsync(pass_ctr, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pass_ctr, 0, sizeof(unsigned), s);
     // per-problem state: active = ok = 1, counters zero
     std::vector<int> ones(n_sub, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.active, ones.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, s);
@@ -1870,6 +1913,21 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     ls_f64.a.active = d.ls_active;
     ls_f64.a.part_g = nullptr;
     ls_f64.G = G_d;
+    // the float64 passes' arguments (symmetric and queued for instances), for up to ctas_max CTAs
+    auto f64args = [&](int64_t ctas_max) {
+        PassArgs x = a;
+        x.rows = d.x;
+        x.snap = pos;
+        if (sym) {
+            x.sym = 1;
+            x.col_g = col_g;
+            x.col_e = col_e;
+            x.col_stride = M;
+            x.ticket = pass_ctr;
+            x.ctas = mixed_ctas(G_sym, ctas_max);
+        }
+        return x;
+    };
     tc_status rs;
     if (prec == TC_MIXED) {
         PassArgs ab = a;
@@ -1883,9 +1941,8 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         a.snap = snap3;
         rs = run_phase<PASS_F64X>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_f64);
     } else {
-        a.rows = d.x;
-        a.snap = pos;
-        rs = run_phase<PASS_F64>(d, a, P, G_bulk, sp, prm->n_steps, s, prof, launches, large, &ls_f64);
+        rs = run_phase<PASS_F64>(d, f64args(sym ? pass_grid<PASS_F64, false, true, true>(P.W) : G_bulk), P, G_rng, sp,
+                                 prm->n_steps, s, prof, launches, large, &ls_f64);
     }
     if (rs != TC_OK) return rs;
     if (prm->polish_steps > 0) {
@@ -1899,9 +1956,8 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
             a.snap = snap3;
             rs = run_phase<PASS_F64X>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large, &ls_f64);
         } else {
-            a.rows = d.x;
-            a.snap = pos;
-            rs = run_phase<PASS_F64>(d, a, P, G_f64, sp2, prm->polish_steps, s, prof, launches, large, &ls_f64);
+            rs = run_phase<PASS_F64>(d, f64args(sym ? pass_grid<PASS_F64, false, true, true>(P.W) : G_f64), P, G_pol,
+                                     sp2, prm->polish_steps, s, prof, launches, large, &ls_f64);
         }
         if (rs != TC_OK) return rs;
     }
@@ -1909,10 +1965,9 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     if (prof) cudaEventRecord(ev_c, s);
     if (prm->want_energy) {
         // float64 E_sub of the relaxed rows against the entry configuration
-        a.rows = d.x;
-        a.snap = pos;
-        if ((e = launch_pass<PASS_F64, true, false>(a, G_e, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
-        SlotView v{P.W, G_e, 0, M, 0};
+        const PassArgs ae = f64args(sym ? pass_grid<PASS_F64, true, false, true>(P.W) : G_e);
+        if ((e = launch_pass<PASS_F64, true, false>(ae, G_en, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+        const SlotView v = pass_view(ae, P.W, G_en, M);
         k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, d.energy, nullptr);
         launches += (P.W > 0 ? 1 : 0) + 1;
     }
