@@ -175,7 +175,8 @@ tc_status allpairs(const double* pos, int64_t n, tc_precision prec, double* grad
     // charge and row block) fit 2 GiB
     const int64_t ctas = G;
     const bool sym = prec == TC_FP64 && (int64_t)P.prob[0].n_rb * n * 24 <= (int64_t(2) << 30);
-    if (prec == TC_MIXED || sym) G = mixed_ranges(P.W);
+    if (prec == TC_MIXED) G = mixed_ranges(P.W);
+    if (sym) G = sym_ranges(P.W);
     P.G = G;
     P.slots = plan_slots(P.prob, 0, 1, 0, P.W, G);
     const int64_t nb = (n + 255) / 256;

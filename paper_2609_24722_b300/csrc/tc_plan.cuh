@@ -68,12 +68,17 @@ inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last
 // range per unit.
 constexpr int64_t kDynMinUnits = 16;
 constexpr size_t kPassCtrOff = 96;  // the queue's ticket counter in the workspace counter area
-inline int64_t mixed_ranges(int64_t W)
+inline int64_t mixed_ranges(int64_t W, int64_t min_units = kDynMinUnits, int64_t kmax = 5)
 {
     const int64_t r0 = 12 * (int64_t)sm_count();
     if (W <= r0) return std::max<int64_t>(1, W);
-    return std::min<int64_t>(5, std::max<int64_t>(1, W / (kDynMinUnits * r0))) * r0;
+    return std::min<int64_t>(kmax, std::max<int64_t>(1, W / (min_units * r0))) * r0;
 }
+
+// Ranges of the symmetric float64 pass: a unit there is ~1 ms of one CTA's
+// float64 pipe and the units of the lower triangle cost nothing, so ranges of
+// about 2 units (up to 20 x 12 SMs of them) keep the queue's tail short.
+inline int64_t sym_ranges(int64_t W) { return mixed_ranges(W, 2, 20); }
 
 // CTAs for `ranges` ranges when at most `ctas_max` are resident: as few rounds
 // of the queue as ctas_max allows, with the ranges spread evenly over them.

@@ -1707,7 +1707,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     int64_t rb_max = 0;
     for (const Prob& p : P.prob) rb_max = std::max<int64_t>(rb_max, p.n_rb);
     const bool sym = inst && rb_max * P.M * 24 <= kSymBytes;
-    const int64_t G_sym = sym ? mixed_ranges(P.W) : 0;
+    const int64_t G_sym = sym ? sym_ranges(P.W) : 0;
     const int64_t G_rng = prec == TC_MIXED ? mixed_ranges(P.W) : (sym && prec == TC_FP64 ? G_sym : G_bulk);
     const int64_t G_pol = sym && !polish_x ? G_sym : G_f64;
     const int64_t G_en = sym ? G_sym : G_e;
