@@ -895,13 +895,23 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
 
 #include "tc_lbfgsb.cuh"
 
-// CTAs per problem of the L-BFGS-B update: the largest cluster size of 8, 4, 2
-// that the device can run for this kernel and that keeps all problems in one
-// wave (problems x size <= SMs), else 1.  A problem's float64 sums are added in
-// an order that depends on that size, so its result is deterministic for a
-// given number of problems in the call (and bit for bit the same run to run).
+// CTAs per problem of the L-BFGS-B update: the largest cluster size of 16
+// (a non-portable size, where the device allows it), 8, 4, 2 that the device
+// can run for this kernel and that keeps all problems in one wave
+// (problems x size <= SMs), else 1.  A problem's float64 sums are added in an
+// order that depends on that size, so its result is deterministic for a given
+// number of problems in the call (and bit for bit the same run to run).
+#ifndef TC_LB_CLMAX
+#define TC_LB_CLMAX 16
+#endif
 template <int CL> static bool lbfgsb_cluster_ok()
 {
+    if (CL > TC_LB_CLMAX) return false;
+    if (CL > 8 && cudaFuncSetAttribute(k_update_lbfgsb<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(kUpd);
@@ -929,7 +939,11 @@ static int lbfgsb_cluster_max()
         return 1;
     }
     if (!known[dev]) {
-        cached[dev] = lbfgsb_cluster_ok<8>() ? 8 : lbfgsb_cluster_ok<4>() ? 4 : lbfgsb_cluster_ok<2>() ? 2 : 1;
+        cached[dev] = lbfgsb_cluster_ok<16>() ? 16
+                      : lbfgsb_cluster_ok<8>() ? 8
+                      : lbfgsb_cluster_ok<4>() ? 4
+                      : lbfgsb_cluster_ok<2>() ? 2
+                                               : 1;
         known[dev] = true;
     }
     return cached[dev];
@@ -969,6 +983,7 @@ static cudaError_t launch_lbfgsb(const RelaxDev& d, const double2* part_g, const
                                  cudaStream_t st)
 {
     switch (lbfgsb_cluster_size(d.S)) {
+        case 16: return launch_lbfgsb_cl<16>(d, part_g, v, sp, st);
         case 8: return launch_lbfgsb_cl<8>(d, part_g, v, sp, st);
         case 4: return launch_lbfgsb_cl<4>(d, part_g, v, sp, st);
         case 2: return launch_lbfgsb_cl<2>(d, part_g, v, sp, st);
