@@ -62,13 +62,13 @@ inline int64_t plan_slots(const std::vector<Prob>& ps, size_t first, size_t last
 // (PassArgs::ticket).  The count depends on the work and the SM count only, not
 // on the launch shape, so every shape computes the same per-range sums; the
 // queue keeps the SMs busy when units differ in cost (near tiles, partial row
-// blocks).  It is k x 12 SMs ranges (k = 1 .. 10, ranges of at least
+// blocks).  It is k x 12 SMs ranges (k = 1 .. 5, ranges of at least
 // kDynMinUnits units where the work allows), so that 3, 4, 5 or 6 resident
 // CTAs per SM take them in whole rounds (mixed_ctas); below 12 SMs units, one
 // range per unit.
 constexpr int64_t kDynMinUnits = 16;
 constexpr size_t kPassCtrOff = 96;  // the queue's ticket counter in the workspace counter area
-inline int64_t mixed_ranges(int64_t W, int64_t min_units = kDynMinUnits, int64_t kmax = 10)
+inline int64_t mixed_ranges(int64_t W, int64_t min_units = kDynMinUnits, int64_t kmax = 5)
 {
     const int64_t r0 = 12 * (int64_t)sm_count();
     if (W <= r0) return std::max<int64_t>(1, W);
