@@ -282,6 +282,47 @@ def test_lbfgs_instances_fp64_match_oracle():
         assert abs(r.energy[k].item() - oracle.energy(xo)) <= 1e-12 * oracle.energy(xo)
 
 
+def test_lbfgs_instances_across_row_blocks_match_oracle():
+    """Instances that straddle the 512-row blocks take their float64 passes with each unordered pair
+    once (row blocks against their later tiles, source sums rotated along the lanes): the L-BFGS
+    iterates and the float64 energies must still follow the oracle."""
+    sizes = [511, 512, 513, 1100, 1600]
+    pos = np.concatenate([synth.arcsine_disk(m, 300 + m) for m in sizes])
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    world = np.stack([off[:-1], off[1:]], 1).astype(np.int64)
+    p = T(pos.copy())
+    iters = 8
+    r = tc.relax_subdomains(p, world=T(world), precision="fp64", optimizer="lbfgs", n_steps=iters, memory=8,
+                            step0=1e-5, maxstep=0.01, accept=False, want_energy=True)
+    tc.sync_status()
+    x = p.cpu().numpy()
+    for k in range(len(sizes)):
+        b, e = off[k], off[k + 1]
+        xo, it, rms = oracle.lbfgs(pos[b:e], memory=8, max_iter=iters, gtol=0.0, step0=1e-5, maxstep=0.01)
+        assert np.abs(x[b:e] - xo).max() <= 1e-9
+        assert abs(r.energy[k].item() - oracle.energy(xo)) <= 1e-12 * oracle.energy(xo)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_queued_passes_are_deterministic(prec):
+    """The mixed and the symmetric float64 passes take their unit ranges from a queue, so which CTA
+    computes which range changes from run to run; the sums do not."""
+    n = 30000
+    pos = synth.arcsine_disk(n, 8)
+    pos = np.ascontiguousarray(pos[synth.zorder(pos)])
+    p = T(pos)
+    runs = []
+    for _ in range(3):
+        g, e = tc.grad(p, prec, with_energy=True)
+        _, loc = tc.local_energy(p, prec)
+        tc.sync_status()
+        runs.append((g.cpu().numpy(), e.item(), loc.cpu().numpy()))
+    for g, e, loc in runs[1:]:
+        np.testing.assert_array_equal(g, runs[0][0])
+        assert e == runs[0][1]
+        np.testing.assert_array_equal(loc, runs[0][2])
+
+
 def test_lbfgs_many_instances_queued_update_matches_oracle():
     """More instances than resident update CTAs: persistent CTAs take the instances, largest first,
     from a queue.  Every instance must still take every step and follow the oracle's iteration."""
