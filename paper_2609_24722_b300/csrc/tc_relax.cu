@@ -251,11 +251,15 @@ __device__ __forceinline__ double2 grad_z(double2 z, double2 g, double radius, b
     }
     double rho = sqrt(z.x * z.x + z.y * z.y);
     if (rho == 0.0) return pinned ? make_double2(0.0, 0.0) : make_double2(radius * g.x, radius * g.y);
-    double ux = z.x / rho, uy = z.y / rho;
+    // one reciprocal and one sincos: the float64 pipe is this update's limit
+    const double ri = 1.0 / rho;
+    double ux = z.x * ri, uy = z.y * ri;
     double gr = g.x * ux + g.y * uy;
     double tx = g.x - gr * ux, ty = g.y - gr * uy;
-    if (pinned) return make_double2(tx / rho, ty / rho);
-    double a = sin(rho) / rho, c = cos(rho);
+    if (pinned) return make_double2(tx * ri, ty * ri);
+    double sn, c;
+    sincos(rho, &sn, &c);
+    const double a = sn * ri;
     return make_double2(radius * (a * tx + c * gr * ux), radius * (a * ty + c * gr * uy));
 }
 
