@@ -905,12 +905,8 @@ __global__ void __launch_bounds__(kUpd) k_update_lbfgs(RelaxDev d, const double2
 // (problems x size <= SMs), else 1.  A problem's float64 sums are added in an
 // order that depends on that size, so its result is deterministic for a given
 // number of problems in the call (and bit for bit the same run to run).
-#ifndef TC_LB_CLMAX
-#define TC_LB_CLMAX 16
-#endif
 template <int CL> static bool lbfgsb_cluster_ok()
 {
-    if (CL > TC_LB_CLMAX) return false;
     if (CL > 8 && cudaFuncSetAttribute(k_update_lbfgsb<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                       cudaSuccess) {
         cudaGetLastError();
