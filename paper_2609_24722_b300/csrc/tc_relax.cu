@@ -26,7 +26,7 @@ constexpr int kUpd = 256;   // update / reduction CTA size
 constexpr int kMaxMem = 16; // largest L-BFGS memory
 // Problems with more rows than this take the L-BFGS update (smooth map or
 // (t, u)) as a sequence of grid-wide launches instead of one CTA; L-BFGS-B
-// always runs one CTA per problem.
+// steps every problem on one CTA or one thread-block cluster (launch_lbfgsb).
 constexpr int kLargeRows = 16384;
 constexpr int kLargeBlocks = 296;  // CTAs of the grid-wide update launches
 // Resident CTAs per SM of the queued one-CTA L-BFGS update (used when there
