@@ -1,4 +1,4 @@
-// tc_lbfgsb.cuh -- the L-BFGS-B update (one CTA per problem).  Included by
+// tc_lbfgsb.cuh -- the L-BFGS-B update (one CTA or cluster per problem).  Included by
 // tc_relax.cu inside namespace tc, after the relaxation state (RelaxDev,
 // SlotView, the (t, u) map and the block reductions) it uses.
 #pragma once

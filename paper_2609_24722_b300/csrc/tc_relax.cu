@@ -686,7 +686,8 @@ template <int N> __device__ void block_sums_n(double (&v)[N], double (*red)[N])
     __syncthreads();
 }
 
-// L-BFGS on the wall parameterisation, one CTA per problem.  Same iteration as
+// L-BFGS on the wall parameterisation, one CTA per problem (or a queue of problems
+// taken by persistent CTAs, k_update_lbfgs).  Same iteration as
 // the host statement: pair test and store, stop test, two-loop recursion
 // (Nocedal & Wright, Alg. 7.4), descent check, max-displacement scaling.
 __device__ void lbfgs_one(const RelaxDev& d, const double2* __restrict__ part_g, const SlotView& v,
@@ -1742,7 +1743,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     const int64_t M = P.M;
     const int64_t taken_words = (n + 31) / 32;
     LargeSet large;
-    // L-BFGS-B steps every problem with one CTA, whatever its size
+    // L-BFGS-B steps every problem on one CTA or cluster (launch_lbfgsb), whatever its size
     if (lbfgs && !boxed)
         for (int32_t k = 0; k < n_sub; ++k)
             if (P.prob[k].m > kLargeRows) large.ids.push_back(k);
