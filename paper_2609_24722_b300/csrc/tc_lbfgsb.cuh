@@ -5,8 +5,9 @@
 
 // ------------------------------------------------------------ L-BFGS-B ---
 // L-BFGS-B (Byrd, Lu, Nocedal & Zhu 1995), the optimiser of Sec. II C step 4,
-// on the (t, u) variables of Sec. II D with the box t in [0, pi/2], one CTA per
-// problem of any size (its time grows with the problem's rows).  A pinned
+// on the (t, u) variables of Sec. II D with the box t in [0, pi/2], one CTA or
+// one cluster of CTAs per problem of any size (its time grows with the
+// problem's rows per CTA).  A pinned
 // charge's variables are (u, 0): u unbounded, the second fixed at 0.
 //
 // Compact representation B = theta I - W M W^T, M = K^{-1},
