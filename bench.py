@@ -87,7 +87,7 @@ def run_case(args):
     if args.case == "full-relax":
         # the C4 workload with longer budgets than the bench line's entry: mixed steps past the 1e-4
         # tolerance, then float64-grade (fp64x) and float64 polishes
-        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=200)), flush=True)
+        print(json.dumps(run_full_relax(dev, n=args.n, max_polish=1000, polish_chunk=100)), flush=True)
         print(json.dumps(run_full_relax(dev, n=args.n, extra_mixed=20000, max_polish=2000,
                                         polish_precision="fp64x")), flush=True)
         return
@@ -456,13 +456,15 @@ def run_instances(dev, seed: int = 3, n_inst: int = 512, rounds: int = 4, steps:
 
 def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_polish: int = 100,
                    polish_precision: str = "fp64", line_search: int = 0, extra_mixed: int = 0,
-                   oracle_check: bool = True) -> dict:
+                   oracle_check: bool = True, polish_chunk: int = 0) -> dict:
     """Config C4: one configuration of N charges (arcsine init, Hilbert order) relaxed by mixed-precision
     L-BFGS(8) on the wall map until the RMS of dE/dz falls below 1e-4 x the initial mean force F_ref
     (then `extra_mixed` more mixed steps), then float64 L-BFGS (or the float64-grade fp64x pass) towards
     1e-8 F_ref, stopping there or at max_polish steps.  The returned configuration's float64 energy,
     computed by the library in the polish call, is compared with the oracle's evaluation of the same
-    configuration (one half of the sum of its rows' 1/r sums, rows split over every host thread)."""
+    configuration (one half of the sum of its rows' 1/r sums, rows split over every host thread).
+    polish_chunk > 0 runs the polish as calls of that many steps (each restarts L-BFGS) and records
+    the RMS and float64 energy after each in `polish_trace`."""
     import numpy as np
     import torch
 
@@ -492,8 +494,21 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
     e_mid = tc.energy(p, "fp64").item()
     torch.cuda.synchronize()
     t1b = time.perf_counter()
-    r2 = tc.relax_subdomains(p, precision=polish_precision, n_steps=max_polish, gtol=1e-8 * f_ref, want_energy=True,
-                             **kw)
+    trace = []
+    if polish_chunk > 0:
+        done = 0
+        while done < max_polish:
+            r2 = tc.relax_subdomains(p, precision=polish_precision, n_steps=min(polish_chunk, max_polish - done),
+                                     gtol=1e-8 * f_ref, want_energy=True, **kw)
+            done += int(r2.steps[0])
+            trace.append([done, r2.rms[0].item(), r2.energy[0].item()])
+            if r2.rms[0].item() < 1e-8 * f_ref or int(r2.steps[0]) == 0:
+                break
+        r2_steps = done
+    else:
+        r2 = tc.relax_subdomains(p, precision=polish_precision, n_steps=max_polish, gtol=1e-8 * f_ref,
+                                 want_energy=True, **kw)
+        r2_steps = int(r2.steps[0])
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     tc.sync_status()
@@ -504,10 +519,12 @@ def run_full_relax(dev, n: int = N, seed: int = 0, max_mixed: int = 20000, max_p
            "polish_stopped_by": "tolerance" if r2.rms[0].item() < 1e-8 * f_ref else "step cap",
            "mixed_steps": steps1, "mixed_rms": r1.rms[0].item(), "mixed_time_s": t1 - t0,
            "energy_after_mixed": e_mid,
-           "polish_steps": int(r2.steps[0]), "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1b,
-           "polish_ms_per_step": 1e3 * (t2 - t1b) / max(int(r2.steps[0]), 1),
+           "polish_steps": r2_steps, "polish_rms": r2.rms[0].item(), "polish_time_s": t2 - t1b,
+           "polish_ms_per_step": 1e3 * (t2 - t1b) / max(r2_steps, 1),
            "relax_time_s": (t1 - t0) + (t2 - t1b), "mean_force_initial": f_ref, "tolerance_polish": 1e-8 * f_ref,
            "energy_initial": e0, "energy_final": e, "E_over_N2": e / n ** 2, "pi_over_4": math.pi / 4}
+    if trace:
+        out["polish_trace"] = trace  # [steps so far, RMS dE/dz, float64 energy] after each call
     if oracle_check:
         x = p.cpu().numpy()
         t3 = time.perf_counter()
