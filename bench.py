@@ -43,7 +43,7 @@ LOCAL_PREC = "fp64"  # the total energy needs 12+ digits: float64
 # dram__bytes_write.sum of k_pass_mixed launches 6..8 in one ncu capture of
 # `python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-instances --config 3`; the capture
 # must be retaken, or this set to None, whenever that kernel changes.
-RELAX_PASS_DRAM_BYTES = 36.5e6
+RELAX_PASS_DRAM_BYTES = 36.3e6
 METRIC = "Coulomb pair-interactions/s (E+grad) at N=1e5, mixed vs FP64; relax time"
 UNIT = "pair-interactions/s"
 WORKLOAD = ("adaptive-cycle step at N=1e5: fp64 local energies of all charges + 256 subdomains "
@@ -670,7 +670,8 @@ def main():
         tuned = {"best": args.config, "shapes": []}
     else:
         # on the timed workload's own shape: N charges, N_SUB subdomains of m ~ U{200..5000}
-        tuned = autotune.tune(n=N, nsub=N_SUB, reps=3, seed=rank, cache=None)
+        # (11 passes per shape: the shapes' pass times differ by well under 1 %)
+        tuned = autotune.tune(n=N, nsub=N_SUB, reps=10, seed=rank, cache=None)
 
     pos_np, idx_np, off_np = make_inputs(rank)
     pos0 = torch.tensor(pos_np, device=dev)
@@ -848,6 +849,7 @@ def main():
                                               "energy_and_gradient": 0},
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replica x{world}",
                    "pass_shape": tuned["best"]},
+        "pass_shape_ms": {str(r["config"]): round(r["relax_pass_ms"], 4) for r in tuned["shapes"]},
         "relax_time_s": ms_step / 1e3,
         "breakdown_ms": {"relax_pass": prof["pass_ms"], "relax_update": prof["update_ms"],
                          "relax_loop": prof["relax_ms"], "accept": prof["accept_ms"], "setup": prof["setup_ms"]},

@@ -441,8 +441,14 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
         const int t0 = sym ? max(tu, 2 * rb) : tu;
         const bool act = (a.active == nullptr) || (a.active[s] != 0);
         if (act) {
+            // A partial last row block gives its rows to the first rstride
+            // threads (rstride a multiple of 32, rows tid + r * rstride), so
+            // whole warps hold no row and skip the pair arithmetic.
+            const int m_blk = (int)min((int64_t)RB, (int64_t)p.m - (int64_t)rb * RB);
+            const int rstride = min(THREADS, (((m_blk + R - 1) / R) + 31) & ~31);
+            const bool holds = tid < rstride;
             const int64_t rl0 = (int64_t)rb * RB + tid;
-            rs.load(static_cast<const src_t*>(a.rows), p.row_base, rl0, THREADS, p.m);
+            rs.load(static_cast<const src_t*>(a.rows), p.row_base, rl0, rstride, holds ? p.m : 0);
             src_t pre{};
             if (t0 < t1) {
                 pre = load_src<KIND, T>(a, p, t0, tid);
@@ -457,11 +463,12 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
                 const bool self = own && (rb * RB < tp * T + T) && (tp * T < rb * RB + RB);
                 int jself[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) jself[r] = (int)(rl0 + r * THREADS) - tp * T;
+                for (int r = 0; r < R; ++r) jself[r] = (int)(rl0 + r * rstride) - tp * T;
                 const double sc = own ? 0.5 : 1.0;
                 if constexpr (KIND == PASS_DELTA || KIND == PASS_DMIX) {
                     using sc_t = typename std::conditional<KIND == PASS_DELTA, double, float>::type;
-                    if (!own)
+                    if (!holds) {
+                    } else if (!own)
                         rs.template tile<T, false, false>(tile[buf], jself, (sc_t)sc);
                     else if (self)
                         rs.template tile<T, true, true>(tile[buf], jself, (sc_t)sc);
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
                         for (int r = 0; r < R; ++r) et[r] = 0.0;
                         for (int c = 0; c < T / 32; ++c) {
                             double ax = 0.0, ay = 0.0, ae = 0.0;
-                            rs.template chunk_sym<WANT_E, WANT_G>(tile[buf] + c * 32, ax, ay, ae, et);
+                            if (holds) rs.template chunk_sym<WANT_E, WANT_G>(tile[buf] + c * 32, ax, ay, ae, et);
                             csum[0][warp][lane] = ax;
                             csum[1][warp][lane] = ay;
                             csum[2][warp][lane] = ae;
@@ -498,13 +505,15 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
                             __syncthreads();
                         }
                         rs.template add_energy<WANT_E>(et, sc);
+                    } else if (!holds) {
                     } else if (self) {
                         rs.template tile<T, true, WANT_E, WANT_G>(tile[buf], jself, sc);
                     } else {
                         rs.template tile<T, false, WANT_E, WANT_G>(tile[buf], jself, sc);
                     }
                 } else {
-                    if (self)
+                    if (!holds) {
+                    } else if (self)
                         rs.template tile<T, true, WANT_E, WANT_G>(tile[buf], jself, (float)sc);
                     else
                         rs.template tile<T, false, WANT_E, WANT_G>(tile[buf], jself, (float)sc);
@@ -515,8 +524,8 @@ __global__ void __launch_bounds__(THREADS) k_pass(PassArgs a, int64_t u_base, in
             const int64_t slot = k - sk_owner(p.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int64_t rl = rl0 + (int64_t)r * THREADS;
-                if (rl < p.m) {
+                const int64_t rl = rl0 + (int64_t)r * rstride;
+                if (holds && rl < p.m) {
                     const int64_t o = slot * a.M + p.row_base + rl - row_sub;
                     if (WANT_E || KIND == PASS_DELTA || KIND == PASS_DMIX) a.part_e[o] = rs.e(r);
                     if constexpr (KIND == PASS_DMIX) {

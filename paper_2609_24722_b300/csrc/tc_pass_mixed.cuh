@@ -35,19 +35,20 @@ template <int R> struct MixedRows {
     static_assert(R % 2 == 0, "rows come in pairs");
     static constexpr int P = R / 2;
 
-    // Loads rows rl0 + r*stride (r < R); rows past m sit far away.  The pairs go
-    // to lo2[4P][stride] (x lo, y lo, x hi, y hi pairs), accumulators
+    // Loads rows rl0 + r*rstride (r < R) when `holds`; rows past m, and every
+    // row of a thread that holds none, sit far away.  The pairs go to
+    // lo2[4P][stride] (x lo, y lo, x hi, y hi pairs), accumulators
     // acc[6R][stride] are zeroed.  Returns the box (xmin, ymin, xmax, ymax) of
     // the valid rows.
-    __device__ float4 load(const float4* rows, int64_t base, int64_t rl0, int stride, int m, float2* lo2, float* acc,
-                           int tid)
+    __device__ float4 load(const float4* rows, int64_t base, int64_t rl0, int rstride, bool holds, int m,
+                           float2* lo2, float* acc, int stride, int tid)
     {
         float4 box = make_float4(3.0e38f, 3.0e38f, -3.0e38f, -3.0e38f);
         float4 q[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t rl = rl0 + (int64_t)r * stride;
-            const bool ok = rl < m;
+            const int64_t rl = rl0 + (int64_t)r * rstride;
+            const bool ok = holds && rl < m;
             q[r] = ok ? rows[base + rl] : make_float4(kFarRow32, kFarRow32, 0.f, 0.f);
             if (ok) {
                 box.x = fminf(box.x, q[r].x);
@@ -70,14 +71,15 @@ template <int R> struct MixedRows {
 
     // One tile of T sources.  hi[j] = (-x_hi, -x_hi, -y_hi, -y_hi), lo[j] the
     // same for the lo parts.  The tile sums (sum dx r^-3 = -grad, sum 1/r) are
-    // folded into the shared accumulators acc[6R][stride] with TwoSum.
-    // Only the first PA pairs are computed: the caller passes PA < P when every
-    // row of the later pairs lies past the end of the problem (a partial last
-    // row block), so the CTA skips them together.
+    // folded into the shared accumulators acc[6R][stride] with TwoSum.  Row r
+    // of the thread is source jself0 + r * rstride of a tile holding its own
+    // charges (SELF).  Only the first PA pairs are computed: the caller passes
+    // PA < P when every row of the later pairs lies past the end of the
+    // problem (a partial last row block), so the CTA skips them together.
     template <int T, bool NEAR, bool SELF, bool WANT_E, bool WANT_G, int PA = P>
     __device__ __forceinline__ void tile(const float4* __restrict__ hi, const float4* __restrict__ lo,
                                          const float2* lo2, float* acc, int stride, int tid, int jself0,
-                                         float escale)
+                                         int rstride, float escale)
     {
         static_assert(PA >= 1 && PA <= P, "active pairs");
         float2 et[PA], gxt[PA], gyt[PA], xl[PA], yl[PA], xh[PA], yh[PA];
@@ -112,9 +114,8 @@ template <int R> struct MixedRows {
                 const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
                 float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
                 if (SELF) {
-                    // row r of this thread is source jself0 + r * stride of this tile
-                    inv.x = (j == jself0 + (2 * p) * stride) ? 0.f : inv.x;
-                    inv.y = (j == jself0 + (2 * p + 1) * stride) ? 0.f : inv.y;
+                    inv.x = (j == jself0 + (2 * p) * rstride) ? 0.f : inv.x;
+                    inv.y = (j == jself0 + (2 * p + 1) * rstride) ? 0.f : inv.y;
                 }
                 if (WANT_E) et[p] = __fadd2_rn(et[p], inv);
                 if (WANT_G) {
@@ -284,9 +285,21 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
         const int t1 = (int)min((int64_t)n_t, (int64_t)t0 + (u_end - u));
         const bool act = (a.active == nullptr) || (a.active[sprob_s] != 0);
         if (act) {
+            // A partial last row block: when its rows fit in the first PH
+            // pairs of every thread (rows tid + r * THREADS), all warps compute
+            // those pairs only (`half`); otherwise its rows go to the first
+            // rstride threads (rstride a multiple of 32, rows tid + r * rstride)
+            // and whole warps that hold no row skip the tile arithmetic.
+            // Halving every warp's work keeps the SM's schedulers evenly loaded,
+            // which idle warps do not.
+            constexpr int PH = P >= 2 ? P / 2 : P;
+            const int m_blk = (int)min((int64_t)RB, (int64_t)sprob.m - (int64_t)rb * RB);
+            const bool half = P >= 2 && m_blk <= 2 * PH * THREADS;
+            const int rstride = half ? THREADS : min(THREADS, (((m_blk + R - 1) / R) + 31) & ~31);
+            const bool holds = tid < rstride;
             const int64_t rl0 = (int64_t)rb * RB + tid;
-            float4 rbox = warp_box(rs.load(static_cast<const float4*>(a.rows), sprob.row_base, rl0, THREADS, sprob.m,
-                                           slo2, sacc, tid));
+            float4 rbox = warp_box(rs.load(static_cast<const float4*>(a.rows), sprob.row_base, rl0, rstride, holds,
+                                           sprob.m, slo2, sacc, THREADS, tid));
             if (lane == 0) srbox[warp] = rbox;
             fetch(t0);
             stage(0);
@@ -309,28 +322,26 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
                 // memory base is a compile-time address and every source load
                 // uses an immediate offset
                 const int kind = self ? 2 : (boxes_far(rb4, tbox) ? 0 : 1);
-                // far tiles of a row block whose rows all lie in its first half
-                // skip the second half's pairs (CTA-uniform)
-                constexpr int PH = P >= 2 ? P / 2 : P;
-                const bool half = P >= 2 && (int64_t)rb * RB + 2 * PH * THREADS >= sprob.m;
-                if (buf == 0) {
-                    if (kind == 0 && half)
-                        rs.template tile<T, false, false, WANT_E, WANT_G, PH>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
-                    else if (kind == 0)
-                        rs.template tile<T, false, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
-                    else if (kind == 1)
-                        rs.template tile<T, true, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
-                    else
-                        rs.template tile<T, true, true, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, sc);
-                } else {
-                    if (kind == 0 && half)
-                        rs.template tile<T, false, false, WANT_E, WANT_G, PH>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
-                    else if (kind == 0)
-                        rs.template tile<T, false, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
-                    else if (kind == 1)
-                        rs.template tile<T, true, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
-                    else
-                        rs.template tile<T, true, true, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, sc);
+                if (holds) {
+                    if (buf == 0) {
+                        if (kind == 0 && half)
+                            rs.template tile<T, false, false, WANT_E, WANT_G, PH>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                        else if (kind == 0)
+                            rs.template tile<T, false, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                        else if (kind == 1)
+                            rs.template tile<T, true, false, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                        else
+                            rs.template tile<T, true, true, WANT_E, WANT_G>(shi[0], slo[0], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                    } else {
+                        if (kind == 0 && half)
+                            rs.template tile<T, false, false, WANT_E, WANT_G, PH>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                        else if (kind == 0)
+                            rs.template tile<T, false, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                        else if (kind == 1)
+                            rs.template tile<T, true, false, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                        else
+                            rs.template tile<T, true, true, WANT_E, WANT_G>(shi[1], slo[1], slo2, sacc, THREADS, tid, jself0, rstride, sc);
+                    }
                 }
                 if (t + 1 < t1) stage(buf ^ 1);
                 __syncthreads();
@@ -338,8 +349,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pass_mixed(PassArgs a, int64_
             const int64_t slot = k - sk_owner(sprob.unit_off + (int64_t)rb * n_t - u_base, a.W, G);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int64_t rl = rl0 + (int64_t)r * THREADS;
-                if (rl < sprob.m) {
+                const int64_t rl = rl0 + (int64_t)r * rstride;
+                if (holds && rl < sprob.m) {
                     const int64_t o = slot * a.M + sprob.row_base + rl - row_sub;
                     const float* ac = sacc + tid;
                     if (WANT_E) a.part_e[o] = (double)ac[(6 * r + 0) * THREADS] + (double)ac[(6 * r + 1) * THREADS];
