@@ -260,9 +260,9 @@ struct PassArgs {
     const int* active;  // nullable; problems with active[s] == 0 are skipped
     double* part_e;     // [slots x M] row partial energies (or energy changes)
     double2* part_g;    // [slots x M] row partial gradients (nullable)
-    // nullable (the mixed and float64 passes): the launch's G ranges are taken in order from this
-    // ticket counter (zero between launches) by `ctas` persistent CTAs instead of one range per
-    // CTA; `ranges` is set to G at the launch
+    // nullable: the launch's G ranges are taken in order from this ticket counter (zero between
+    // launches) by `ctas` persistent CTAs instead of one range per CTA; `ranges` is set to G at
+    // the launch
     unsigned* ticket;
     int64_t ctas;
     int64_t ranges;

@@ -201,7 +201,7 @@ inline cudaError_t launch_pass(const PassArgs& a, int64_t G, int64_t u_base, int
     int threads = 0;
     auto fn = pass_kernel<KIND, WANT_E, WANT_G>(&threads);
     if (KIND == PASS_F64 && a.sym) fn = pass_kernel<KIND, WANT_E, WANT_G, true>(&threads);
-    if ((KIND == PASS_MIXED || KIND == PASS_F64) && a.ticket) {
+    if (a.ticket) {
         PassArgs b = a;
         b.ranges = G;
         fn<<<(unsigned)std::min<int64_t>(a.ctas, G), threads, 0, s>>>(b, u_base, row_sub);

@@ -115,6 +115,7 @@ struct SlotView {
     const double2* colg = nullptr;    // nullable: source sums of a symmetric pass (PassArgs::col_g)
     const double* cole = nullptr;     // nullable: the same for 1/r (PassArgs::col_e)
     int64_t col_stride = 0;
+    const double* rede = nullptr;     // nullable: the rows' energy partials already summed (k_sum_slots_e)
 };
 
 __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double2* part_g, const SlotView& v)
@@ -141,6 +142,7 @@ __device__ __forceinline__ double2 sum_g(const Prob& p, int64_t rl, const double
 
 __device__ __forceinline__ double sum_e(const Prob& p, int64_t rl, const double* part_e, const SlotView& v)
 {
+    if (v.rede) return v.rede[p.row_base + rl - v.row_sub];
     int64_t c = slot_count(p, (int)(rl / kRB), v.u_base, v.W, v.G);
     double hi = 0.0, lo = 0.0;
     int64_t o = p.row_base + rl - v.row_sub;
@@ -347,6 +349,17 @@ __global__ void k_sum_slots(RelaxDev d, const double2* __restrict__ part_g, Slot
         const Prob p = d.prob[find_row_prob(d.prob, d.S, rr)];
         d.g_red[rr] = sum_g(p, rr - p.row_base, part_g, v);
     }
+}
+
+// The energy partials of problem s's rows summed in slot order (sum_e) into
+// red[row - v.row_sub], one row per thread: the sequential accept's one-CTA
+// kernel then reads one value per row.  Skipped when the problem is not active.
+__global__ void k_sum_slots_e(RelaxDev d, int s, const double* __restrict__ part_e, SlotView v, double* red)
+{
+    if (!d.ok[s]) return;
+    const Prob p = d.prob[s];
+    const int64_t rl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (rl < p.m) red[p.row_base + rl - v.row_sub] = sum_e(p, rl, part_e, v);
 }
 
 // Projected gradient descent (fixed or Barzilai-Borwein step), one CTA per problem.
@@ -1729,17 +1742,22 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     // phases whose gradient passes leave many slots per row sum them over every SM before the update
     const bool pre_bulk = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_rng) > kPreReduceSlots;
     const bool pre_polish = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_pol) > kPreReduceSlots;
-    // single-problem passes of the sequential accept
+    // single-problem passes of the sequential accept: R1[k] ranges of about two units, taken from
+    // the queue by C1[k] persistent CTAs, so the cheap units of a partial last row block do not
+    // leave SMs idle while others finish whole row blocks; with many slots per row, the rows'
+    // partials are summed over every SM (k_sum_slots_e) before the one-CTA accept kernel
     int64_t slots1 = 1;
-    std::vector<int64_t> G1(n_sub);
+    std::vector<int64_t> R1(n_sub), C1(n_sub);
     if (!inst && prm->accept) {
         for (int32_t k = 0; k < n_sub; ++k) {
             const Prob& p = P.prob[k];
             int64_t Wk = (int64_t)p.n_rb * (p.n_t_snap + p.n_t_priv);
-            G1[k] = std::max<int64_t>(1, std::min<int64_t>(G_d, Wk));
-            slots1 = std::max(slots1, plan_slots(P.prob, k, k + 1, p.unit_off, Wk, G1[k]));
+            R1[k] = std::max<int64_t>(1, sym_ranges(Wk));
+            C1[k] = mixed_ctas(R1[k], std::min<int64_t>(G_d, R1[k]));
+            slots1 = std::max(slots1, plan_slots(P.prob, k, k + 1, p.unit_off, Wk, R1[k]));
         }
     }
+    const bool pre_accept = slots1 > kPreReduceSlots;
     const int64_t M = P.M;
     const int64_t taken_words = (n + 31) / 32;
     LargeSet large;
@@ -1764,6 +1782,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     int32_t* upd_order_d = nullptr;
     double2* col_g = nullptr;
     double* col_e = nullptr;
+    double* acc_red = nullptr;
     auto layout = [&](Carver& cv, RelaxDev& d, Prob*& probd, int64_t*& wbd, float4*& snap_split, double*& part_e,
                       double2*& part_g, double*& part1) {
         probd = cv.take<Prob>(n_sub);
@@ -1812,6 +1831,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
         part_e = cv.take<double>(slots * M);
         part_g = cv.take<double2>(slots * M);
         part1 = cv.take<double>(slots1 * max_m);
+        acc_red = cv.take<double>(pre_accept ? max_m : 0);
         upd_order_d = cv.take<int32_t>(upd_order.size());
     };
     RelaxDev d{};
@@ -2003,9 +2023,16 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
                 PassArgs ak = a;
                 ak.W = (int64_t)p.n_rb * (p.n_t_snap + p.n_t_priv);
                 ak.M = std::max<int64_t>(p.m, 1);
-                if ((e = launch_pass<PASS_DELTA, false, false>(ak, G1[k], p.unit_off, p.row_base, s)) != cudaSuccess)
+                ak.ticket = pass_ctr;
+                ak.ctas = C1[k];
+                if ((e = launch_pass<PASS_DELTA, false, false>(ak, R1[k], p.unit_off, p.row_base, s)) != cudaSuccess)
                     return cuda_fail(e, "accept pass launch");
-                SlotView v{ak.W, G1[k], p.unit_off, ak.M, p.row_base};
+                SlotView v{ak.W, R1[k], p.unit_off, ak.M, p.row_base};
+                if (pre_accept && p.m > 0) {
+                    k_sum_slots_e<<<(unsigned)((p.m + 255) / 256), 256, 0, s>>>(d, k, part1, v, acc_red);
+                    v.rede = acc_red;
+                    ++launches;
+                }
                 k_accept_apply<<<1, kUpd, 0, s>>>(d, k, part1, v);
                 launches += (ak.W > 0 ? 1 : 0) + 1;
             }
