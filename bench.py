@@ -670,8 +670,9 @@ def main():
         tuned = {"best": args.config, "shapes": []}
     else:
         # on the timed workload's own shape: N charges, N_SUB subdomains of m ~ U{200..5000}
-        # (11 passes per shape: the shapes' pass times differ by well under 1 %)
-        tuned = autotune.tune(n=N, nsub=N_SUB, reps=10, seed=rank, cache=None)
+        # over the timed workload's RELAX_STEPS passes per shape: the shapes' pass times differ by
+        # well under 1 %, and their order changes as the zones spread over the steps
+        tuned = autotune.tune(n=N, nsub=N_SUB, reps=RELAX_STEPS - 1, seed=rank, cache=None)
 
     pos_np, idx_np, off_np = make_inputs(rank)
     pos0 = torch.tensor(pos_np, device=dev)
