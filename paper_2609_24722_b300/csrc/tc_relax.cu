@@ -1742,7 +1742,7 @@ tc_status relax(double* pos, int64_t n, const int32_t* idx, const int64_t* offse
     // phases whose gradient passes leave many slots per row sum them over every SM before the update
     const bool pre_bulk = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_rng) > kPreReduceSlots;
     const bool pre_polish = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G_pol) > kPreReduceSlots;
-    // single-problem passes of the sequential accept: R1[k] ranges of about two units, taken from
+    // single-problem passes of the sequential accept: R1[k] ranges of one to two units, taken from
     // the queue by C1[k] persistent CTAs, so the cheap units of a partial last row block do not
     // leave SMs idle while others finish whole row blocks; with many slots per row, the rows'
     // partials are summed over every SM (k_sum_slots_e) before the one-CTA accept kernel
