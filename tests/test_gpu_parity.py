@@ -239,10 +239,14 @@ def test_gd_instance_matches_oracle_trajectory():
         assert int(r.steps[0]) == 20 and int(r.status[0]) == 1
 
 
-def test_bb_subdomains_and_sequential_accept_vs_oracle():
-    n = 2500
+@pytest.mark.parametrize("n,m_lo,m_hi", [(2500, 30, 200), (6000, 100, 700)], ids=["n2500", "n6000"])
+def test_bb_subdomains_and_sequential_accept_vs_oracle(n, m_lo, m_hi):
+    """Float64 BB relaxation of overlapping subdomains and the sequential accept against the oracle.
+    At n = 6000 the subdomains (296-610 charges) end in partial row blocks of 20-426 rows, which the
+    float64 passes run on fewer whole warps, and each accept pass leaves 26-27 slots per row (one
+    range per unit), which are summed over every SM before the accept kernel reads them."""
     pos = synth.lattice_disk(n, 7, 0.05)
-    subs = synth.subdomains(pos, 5, 30, 200, 8)
+    subs = synth.subdomains(pos, 5, m_lo, m_hi, 8)
     idx, off = synth.to_csr(subs)
     eta = 1e-4 / n
     steps = 15
