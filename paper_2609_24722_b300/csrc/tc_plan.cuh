@@ -88,17 +88,6 @@ inline int64_t mixed_ctas(int64_t ranges, int64_t ctas_max)
     return (ranges + rounds - 1) / rounds;
 }
 
-template <class K> inline int64_t grid_for(K kernel, int64_t W)
-{
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        occ = 1;
-    }
-    int64_t g = (int64_t)sm_count() * occ;
-    return std::max<int64_t>(1, std::min<int64_t>(g, W));
-}
-
 // ------------------------------------------------------- small kernels ---
 
 __device__ __forceinline__ bool inside(double x, double y)
