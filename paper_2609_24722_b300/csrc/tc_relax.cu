@@ -2100,7 +2100,10 @@ static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, con
     if (P.M > 0 && (!idx || !new_active)) return TC_ERR_INVALID_ARG;
     plan_units(P);
     const int64_t G = mixed ? pass_grid<PASS_DMIX, false, false>(P.W) : pass_grid<PASS_DELTA, false, false>(P.W);
-    const int64_t slots = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, G);
+    // float64: the persistent CTAs take ranges of a few units from the queue (sym_ranges), so the
+    // cheap units of partial last row blocks leave no SM idle while others finish whole blocks
+    const int64_t R = mixed ? G : sym_ranges(P.W);
+    const int64_t slots = plan_slots(P.prob, 0, P.prob.size(), 0, P.W, R);
     const int64_t M = P.M;
     Carver c;
     f8* rows8 = nullptr;
@@ -2159,12 +2162,15 @@ static tc_status delta_all(const double* pos, int64_t n, const int32_t* idx, con
     a.active = nullptr;
     a.part_e = part_e;
     a.part_g = part_b;
-    SlotView v{P.W, G, 0, a.M, 0};
+    SlotView v{P.W, R, 0, a.M, 0};
     if (mixed) {
         if ((e = launch_pass<PASS_DMIX, false, false>(a, G, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
         k_dmix_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, part_b, v, delta, bound);
     } else {
-        if ((e = launch_pass<PASS_DELTA, false, false>(a, G, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
+        a.ticket = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kPassCtrOff);
+        a.ctas = mixed_ctas(R, G);
+        if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "set-up");
+        if ((e = launch_pass<PASS_DELTA, false, false>(a, R, 0, 0, s)) != cudaSuccess) return cuda_fail(e, "launch");
         k_problem_sums<<<n_sub, kUpd, 0, s>>>(d, part_e, v, delta, nullptr);
     }
     return cuda_status(cudaGetLastError());
